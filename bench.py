@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Throughput of the implicit r-z PIC/MC timestep on one GB300 (arXiv:1001.2969).
+
+A step is one whole implicit timestep of the production-size reactor
+(R 20 cm, L 2.5 cm, 129 x 513 nodes, 1e7 electrons + 1e7 Ar+, 300 V at
+13.56 MHz, dt = T_rf/200): deposit -> multigrid solve -> E -> fused particle
+pass (gather, push, MC, split, push, deposit) -> cell sort.  The metric is
+particle-steps per second, mixed FP32/FP64 path, with the plain FP64 path
+reported beside it.  Inputs (the particle state, 880 MB mixed) are larger
+than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun each rank runs its own reactor (independent replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s and ms/step at 20M particles (mixed vs FP64); % of HBM peak"
+UNIT = "particle-steps/s"
+WORKLOAD = ("c2 production reactor: R 20 cm, L 2.5 cm, 129x513 nodes, 1e7 e- + 1e7 Ar+, "
+            "n0 5e15 m^-3, argon 4 Pa 300 K, 300 V at 13.56 MHz, dt = T_rf/200, seed 1")
+# algorithmic bytes of the particle pass per particle: the state read once and
+# written once (mixed: cell 4 + offsets 8 + v 12 + a 8 + w 4 + id 8 = 44 B)
+BYTES_PER_PARTICLE = {"mixed": 88, "fp64": 152}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip() for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            c = [x.strip() for x in r.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1].split()[0]))
+                mx.append(float(c[2].split()[0]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if c[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic(prec):
+    """DRAM bytes per particle of the particle pass from the committed ncu summary."""
+    p = os.path.join(ROOT, "profiles", f"k_step_{prec}_c2.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("dram_bytes_per_particle:"):
+            try:
+                return float(line.split(":")[1])
+            except ValueError:
+                return None
+    return None
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1001_2969_gb300 import build
+    from paper_1001_2969_gb300 import pic
+
+    build()
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    results = {}
+    for prec in (args.precision, "fp64") if args.fp64_steps > 0 else (args.precision,):
+        steps = args.steps if prec == args.precision else args.fp64_steps
+        cfg = W.config(args.config, precision=prec, seed=1 + rank)
+        h = pic.pic_init(cfg, stream=stream.cuda_stream)
+        pic.pic_step(h, args.warmup)
+        n0 = pic.pic_get_counts(h)["n_alive"].sum()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks(dev) if prec == args.precision else None
+        if clocks:
+            clocks.start()
+        pic.pic_timings(h, reset=True)
+        pic.pic_profile(h, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = pic.pic_step(h, steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ck = clocks.stop() if clocks else None
+        pic.pic_profile(h, False)
+        tm = pic.pic_timings(h, reset=True)
+        ms = ev0.elapsed_time(ev1)
+        n1 = pic.pic_get_counts(h)["n_alive"].sum()
+        psteps = 0.5 * (n0 + n1) * steps
+        res = dict(ms=ms, psteps=psteps, n0=int(n0), n1=int(n1), timings=tm, clocks=ck, status=st)
+        if prec == args.precision:
+            # end to end through the public API with host buffers: per step the z = L
+            # boundary row goes host -> device from pinned memory and the time-averaged
+            # grids come back device -> host
+            phiL = torch.zeros(cfg["nr"], dtype=torch.float64, pin_memory=True)
+            nz, nr = cfg["nz"], cfg["nr"]
+            outs = [torch.zeros(nz * nr, dtype=torch.float64, pin_memory=True) for _ in range(5)]
+            import ctypes as C
+
+            mo = pic.pic_moments_out(*[C.cast(o.data_ptr(), C.POINTER(C.c_double)) for o in outs],
+                                     None, None, None, 0, 0)
+            e_steps = max(1, min(steps, args.e2e_steps))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e_steps):
+                pic.lib().pic_set_boundary(h.ptr, phiL.data_ptr(), 0)
+                pic.pic_step(h, 1)
+                pic.pic_moments_into(h, mo)
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            n2 = pic.pic_get_counts(h)["n_alive"].sum()
+            res["e2e"] = dict(seconds=e2e_s, psteps=0.5 * (n1 + n2) * e_steps, steps=e_steps,
+                              h2d=nr * 8, d2h=5 * nz * nr * 8)
+        pic.pic_destroy(h)
+        del h
+        torch.cuda.empty_cache()
+        results[prec] = res
+    return results
+
+
+def cpu_baseline(cfg_name, n_per_species, steps):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+    import workloads as W
+    from oracle import Oracle
+
+    cfg = W.scaled(W.config(cfg_name), n_per_species)
+    o = Oracle(cfg)
+    o.load()
+    o.step(1)  # first step outside the timing (warm caches)
+    n0 = o.count(0) + o.count(1)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    n1 = o.count(0) + o.count(1)
+    ps = 0.5 * (n0 + n1) * steps
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cfg_name} mesh and load with {n_per_species} particles per species "
+                      f"(1/{int(W.config(cfg_name)['species'][0]['n_init'] / n_per_species)} of the "
+                      f"workload), {steps} steps after one warm-up step, single thread",
+            "ms_per_step": 1e3 * dt / steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        warm = max(args.warmup, 0)
+        import workloads as W
+        from oracle import Oracle
+
+        cfg = W.scaled(W.config(args.config), args.cpu_sample)
+        o = Oracle(cfg)
+        o.load()
+        o.step(warm)
+        n0 = o.count(0) + o.count(1)
+        t0 = time.perf_counter()
+        o.step(args.steps)
+        dt = time.perf_counter() - t0
+        n1 = o.count(0) + o.count(1)
+        v = 0.5 * (n0 + n1) * args.steps / dt
+        sample = (f"{args.config} mesh and load with {args.cpu_sample} particles per species, "
+                  f"{args.steps} timed steps after {warm} warm-up steps, single thread")
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * dt / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "sample": sample},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    res = run_gpu(args, rank, world)
+    main_r = res[args.precision]
+    # whole job: units all ranks processed / the slowest rank's time
+    if world > 1:
+        t = torch.tensor([main_r["ms"], main_r["psteps"]], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[0:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(mx[1:2], op=torch.distributed.ReduceOp.SUM)
+        ms_max, psteps_sum = float(mx[0]), float(mx[1])
+    else:
+        ms_max, psteps_sum = main_r["ms"], main_r["psteps"]
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+    value = psteps_sum / (ms_max * 1e-3)
+    peak, peak_kind = _peaks()
+    tm = main_r["timings"]
+    k_ms = tm["particle_e_ms"] + tm["particle_i_ms"]
+    k_bytes = BYTES_PER_PARTICLE[args.precision] * main_r["psteps"]
+    achieved = k_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
+    tb = _traffic(args.precision)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision,
+                   "particles_per_rank": main_r["n0"],
+                   "l2": "no flush: particle state (880 MB mixed) is larger than L2 (129 MB)",
+                   "parallelism": f"{world} independent reactor replica(s), one per GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_step (fused particle pass, both species)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_particle": BYTES_PER_PARTICLE[args.precision],
+                     "traffic": tb * main_r["psteps"] / (2 * args.steps) if tb else None,
+                     "kernel_ms_per_step": k_ms / args.steps},
+        "phases_ms_per_step": {k[:-3]: v / args.steps for k, v in tm.items() if k.endswith("_ms")},
+        "gpu_launches": tm["launches"],
+        "clocks": main_r["clocks"],
+    }
+    if "fp64" in res and args.precision != "fp64":
+        r = res["fp64"]
+        t64 = r["timings"]
+        k64 = t64["particle_e_ms"] + t64["particle_i_ms"]
+        line["fp64"] = {"value": r["psteps"] / (r["ms"] * 1e-3), "unit": UNIT,
+                        "ms_per_step": r["ms"] / args.fp64_steps, "steps": args.fp64_steps,
+                        "particle_pass_ms_per_step": k64 / args.fp64_steps,
+                        "solve_ms_per_step": t64["solve_ms"] / args.fp64_steps}
+    e = main_r["e2e"]
+    line["e2e"] = {"value": e["psteps"] / e["seconds"], "unit": UNIT,
+                   "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"],
+                   "steps": e["steps"]}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_sample, args.cpu_steps)
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,262 @@
+/*
+ * pic.h -- C ABI of the GB300 implicit electrostatic PIC/MC timestep in
+ * axisymmetric r-z geometry (Wang, Jiang & Wang, "Implicit and
+ * electrostatic Particle-in-cell/Monte Carlo model in two-dimensional and
+ * axisymmetric geometry I: analysis of numerical techniques",
+ * arXiv:1001.2969).
+ *
+ * One handle holds one reactor: an r-z mesh, two species (electrons and
+ * one ion species), their particles resident in GPU memory, the fields and
+ * the multigrid workspace.  Every entry point returns a pic_status and
+ * never aborts the process; pic_last_error() gives a one-line reason.
+ * Grids are FP64, row-major [i][j] with i the z node (0..nz-1) and j the
+ * r node (0..nr-1).  Units are SI (volts, metres, seconds, kilograms,
+ * coulombs); energies in cross-section tables are in eV.
+ *
+ * Threading: a handle may be used from one host thread at a time.  All
+ * device work of a handle is issued on the stream given in the config
+ * (the legacy default stream when NULL).
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pic_status {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,           /* invalid argument or configuration          */
+    PIC_ERR_CAPACITY = 2,      /* particle or births capacity exceeded        */
+    PIC_ERR_CUDA = 3,          /* a CUDA runtime call failed                  */
+    PIC_ERR_NOT_CONVERGED = 4, /* multigrid hit mg_max_cycles (non-fatal)    */
+    PIC_ERR_NUMERIC = 5,       /* NaN/Inf in the particle state               */
+    PIC_ERR_TIMEOUT = 6,       /* a bounded device wait gave up              */
+    PIC_ERR_STATE = 7          /* call not valid in the handle's state        */
+} pic_status;
+
+enum { PIC_FP64 = 0, PIC_MIXED = 1 };
+enum { PIC_WEIGHT_ZR2 = 0, PIC_WEIGHT_ZR = 1 };
+enum { PIC_CHI_MAX = 0, PIC_CHI_MEAN = 1 };
+enum { PIC_SCATTER_VS = 0, PIC_SCATTER_ISOTROPIC = 1 };
+enum { PIC_XS_ELASTIC = 0, PIC_XS_EXCITE = 1, PIC_XS_IONIZE = 2, PIC_XS_CX = 3 };
+
+#define PIC_MAX_CH 4
+
+/* Counter slots returned by pic_moments (int64). */
+#define PIC_C_COLL 0    /* [s*4+ch] real collisions of species s, channel ch */
+#define PIC_C_CAND 8    /* [s] null-collision candidates                      */
+#define PIC_C_NUOVER 10 /* [s] particles whose nu exceeded nu_max             */
+#define PIC_C_BIRTHS 12 /* [s] particles born (ionisation and splitting)      */
+#define PIC_C_SPLITS 14 /* [s] parents split                                  */
+#define PIC_C_ABS 16    /* [s*3+wall] absorbed at z=0, z=L, r=R               */
+#define PIC_C_MGCYC 22  /* multigrid V-cycles, summed over steps              */
+#define PIC_C_STEPS 23  /* steps taken                                        */
+#define PIC_NCOUNT 24
+
+/* Mesh: uniform node-centred r-z mesh, z in [0, L], r in [0, R] (Sec. 2.4,
+ * Sec. 3.2).  nz must be 2^k + 1 (z-semi-coarsening, Sec. 2.5), nr >= 3. */
+typedef struct pic_mesh {
+    double R, L;
+    int32_t nz, nr;
+} pic_mesh;
+
+/* Species [0] electrons, [1] ions: charge, mass, initial density n0
+ * (m^-3), temperature (eV), initial macro-particle count and capacity. */
+typedef struct pic_species {
+    double q, m, n0, T_eV;
+    int64_t n_init, capacity;
+} pic_species;
+
+/* Cross sections (Sec. 2.6): sigma_m2[ch * n_e + k] at E_k = k E_max/(n_e-1),
+ * linearly interpolated, 1/E above E_max.  Electron channels may be
+ * ELASTIC, EXCITE, IONIZE; the ion channel is CX (charge exchange).
+ * B_eV is the ionisation energy-sharing parameter. */
+typedef struct pic_xsec {
+    int32_t n_e;
+    double E_max_eV;
+    int32_t n_ch;
+    const double *sigma_m2;
+    const double *threshold_eV;
+    const int32_t *kind;
+    double B_eV;
+} pic_xsec;
+
+/* rf source on the z = 0 electrode: V(t) = sum_k amp_k sin(2 pi f_k t + ph_k)
+ * (Sec. 3 benchmark: 200 sin(w t) at 13.56 MHz). */
+typedef struct pic_rf {
+    int32_t n;
+    const double *amp_V, *freq_Hz, *phase_rad;
+} pic_rf;
+
+/* Background gas (Sec. 2.6): pressure, temperature, atom mass. */
+typedef struct pic_gas {
+    double p_Pa, T_K, m_gas;
+} pic_gas;
+
+/* Device memory hooks.  alloc returns 256-byte aligned device memory or
+ * NULL; free releases it.  When alloc is NULL the library uses cudaMalloc. */
+typedef void *(*pic_alloc_fn)(size_t bytes, void *ctx, void *stream);
+typedef void (*pic_free_fn)(void *ptr, size_t bytes, void *ctx, void *stream);
+
+typedef struct pic_config {
+    pic_mesh mesh;
+    pic_species sp[2];
+    pic_xsec xs[2];
+    pic_rf rf;
+    pic_gas gas;
+    double dt;            /* time step (s) */
+    uint64_t seed;        /* Philox key    */
+    int32_t precision;    /* PIC_FP64 or PIC_MIXED                            */
+    int32_t weighting;    /* PIC_WEIGHT_ZR2 (Eq. (9)) or PIC_WEIGHT_ZR (Eq. (8)) */
+    int32_t chi_face;     /* PIC_CHI_MAX or PIC_CHI_MEAN (Sec. 2.5)            */
+    int32_t scatter;      /* PIC_SCATTER_VS or PIC_SCATTER_ISOTROPIC           */
+    int32_t split_every;  /* weight-split period in steps, 0 = never (Sec. 2.2) */
+    int32_t mg_max_cycles;
+    double mg_tol;        /* relative max-norm residual; <= 0: run mg_max_cycles */
+    const double *phi_zL; /* nullable: nr potentials on z = L (else grounded)  */
+    int64_t births_capacity; /* per species, 0 = capacity/2                  */
+    int32_t eedf_bins;
+    double eedf_emax_eV;
+    int32_t load;         /* 1: load the species at init (uniform n0, weights ~ cell volume) */
+    pic_alloc_fn alloc;
+    pic_free_fn free;
+    void *alloc_ctx;
+    void *stream;         /* cudaStream_t */
+} pic_config;
+
+typedef struct pic_handle pic_handle;
+
+/* Host particle arrays, absolute coordinates, FP64.  cell (nullable) is
+ * filled by pic_get_particles with the stored cell index j (nz-1) + i and
+ * ignored by pic_set_particles. */
+typedef struct pic_particles_view {
+    int64_t n;
+    double *r, *z, *vr, *vt, *vz, *ar, *az, *w;
+    uint64_t *id;
+    int32_t *cell;
+} pic_particles_view;
+
+typedef struct pic_solve_info {
+    int32_t cycles;
+    double rel_residual;
+} pic_solve_info;
+
+typedef struct pic_moments_out {
+    double *ne, *ni, *phi, *Er, *Ez; /* [nz][nr] averages over steps, nullable */
+    double *eedf;                    /* [eedf_bins] weighted electron energies per step */
+    int64_t *counters;               /* [PIC_NCOUNT], nullable                  */
+    double *charge;                  /* [3] absorbed charge at z=0, z=L, r=R     */
+    int64_t nsamples;                /* out: steps averaged                     */
+    int32_t on_device;               /* grids/eedf are device pointers          */
+} pic_moments_out;
+
+/*
+ * pic_init -- validate cfg, allocate the handle's device state and, when
+ * cfg->load is 1, load both species: uniform density n0 with weights
+ * proportional to the cell volume (Sec. 2.2, Eq. (3)), particles spread
+ * evenly over cells numbered c = j (nz-1) + i (remainder to the lowest
+ * numbers), uniform in z and r^2 within a cell, Maxwellian velocities
+ * (Philox draws keyed by the particle id), zero acceleration; then deposit
+ * the charge (Sec. 2.4).  Arrays in cfg are copied; the caller keeps them.
+ * Errors: PIC_ERR_ARG (bad mesh, species, tables, capacities),
+ * PIC_ERR_CUDA (allocation or launch).  *out is NULL on error.
+ */
+pic_status pic_init(const pic_config *cfg, pic_handle **out);
+
+/*
+ * pic_step -- advance nsteps implicit timesteps (Sec. 2.1 cycle in its
+ * merged form): rho and chi from the deposit at x~ (Sec. 2.1, 2.4), solve
+ * div[(1+chi) grad phi] = -rho/eps0 by z-semi-coarsening multigrid
+ * (Sec. 2.5, Algorithm 1), E = -grad phi, then one pass over the particles:
+ * gather E, final push, axis reflection and wall absorption (Sec. 2.3),
+ * null-collision Monte Carlo (Sec. 2.6), weight splitting on split steps
+ * (Sec. 2.2), first push of the next step in the local X-Y frame with the
+ * theta rotation (Sec. 2.3), deposit of rho and chi, and a re-sort of the
+ * particles by cell.  Returns the first non-OK status of the steps;
+ * PIC_ERR_NOT_CONVERGED is non-fatal (the step completes).  On
+ * PIC_ERR_CAPACITY the particle state is left at the last completed step.
+ */
+pic_status pic_step(pic_handle *h, int32_t nsteps);
+
+/*
+ * pic_field_solve -- stand-alone solve of Eq. (2) (Sec. 2.1, 2.5) on the
+ * handle's mesh: rho (C/m^3) and chi (dimensionless) in, phi (V) out, all
+ * [nz][nr] FP64; z = 0 at potential V, z = L at the configured phi_zL (or
+ * 0), r = R at 0.  Cold start (zero interior).  Pointers are host memory
+ * unless on_device.  Does not touch the simulation's fields.  info may be
+ * NULL.  Returns PIC_ERR_NOT_CONVERGED if mg_max_cycles was reached.
+ */
+pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, double V,
+                           double *phi, int32_t on_device, pic_solve_info *info);
+
+/*
+ * pic_moments -- time averages over the steps since the last reset (Sec. 3:
+ * results are averages over time) of n_e, n_i (m^-3, deposit over node
+ * volumes, Eq. (10)), phi, E_r, E_z; the electron energy distribution
+ * (weighted, after collisions) summed per step and divided by the steps;
+ * counters and absorbed charge since the last reset.  Caller-owned
+ * buffers; NULL members are skipped.  reset != 0 clears the averages and
+ * counters after copying them out.
+ */
+pic_status pic_moments(pic_handle *h, pic_moments_out *out, int32_t reset);
+
+/*
+ * pic_get_particles -- copy the particles of species s (0 e, 1 ion) into
+ * the host arrays of *view, at most `capacity` of them, in cell order;
+ * view->n is set to the number copied.  Positions are the stored x~
+ * (after the first push of the next step, Sec. 2.1).
+ */
+pic_status pic_get_particles(pic_handle *h, int32_t s, pic_particles_view *view,
+                             int64_t capacity);
+
+/*
+ * pic_set_particles -- replace the particles of species s by view->n host
+ * particles (absolute r, z, velocities, accelerations a_bar, weights, ids)
+ * and redeposit both species.  Positions must be inside the domain.  The
+ * next id given to a newborn is max(id) + 1.  PIC_ERR_CAPACITY if n is
+ * larger than the species capacity.
+ */
+pic_status pic_set_particles(pic_handle *h, int32_t s, const pic_particles_view *view);
+
+/* pic_set_step -- set the step index that keys the Philox draws (Sec. 2.6)
+ * and the rf phase of the next solve (t = (step + 1) dt). */
+pic_status pic_set_step(pic_handle *h, int64_t step);
+
+/* pic_set_boundary -- set the nr potentials on z = L used by the next
+ * solves (Sec. 2.5 Dirichlet data); phi_zL NULL grounds it again. */
+pic_status pic_set_boundary(pic_handle *h, const double *phi_zL, int32_t on_device);
+
+/* pic_get_fields -- copy rho, chi, phi, E_z, E_r of the last step ([nz][nr],
+ * rho/chi are the ones of the deposit held now); NULL members skipped. */
+pic_status pic_get_fields(pic_handle *h, double *rho, double *chi, double *phi, double *Ez,
+                          double *Er, int32_t on_device);
+
+/* pic_get_counts -- particles alive per species, steps taken, next ids. */
+pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64_t *next_id);
+
+/* pic_save / pic_load -- checkpoint: particles, phi, step, ids, counters.
+ * Resuming is bit-exact because every draw is keyed by (id, step). */
+pic_status pic_save(pic_handle *h, const char *path);
+pic_status pic_load(pic_handle *h, const char *path);
+
+/* pic_profile -- when on, record CUDA events around each phase of every
+ * step on the handle's stream.  pic_timings returns the accumulated
+ * milliseconds per phase [0 solve, 1 particle kernels, 2 births+sort,
+ * 3 other], the number of particle-kernel launches, and the number of all
+ * kernel launches this handle has made. */
+pic_status pic_profile(pic_handle *h, int32_t on);
+pic_status pic_timings(pic_handle *h, double *ms, int64_t *particle_launches,
+                       int64_t *all_launches, int32_t reset);
+
+void pic_destroy(pic_handle *h);
+const char *pic_last_error(const pic_handle *h);
+const char *pic_status_string(pic_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,754 @@
+// particles.cu -- particle kernels of the r-z implicit PIC/MC timestep
+// (Wang, Jiang & Wang, arXiv:1001.2969): the load, the fused particle pass
+// (gather -> final push -> axis/walls -> null-collision MC -> split -> first
+// push -> deposit), the plain deposit, and the absolute-coordinate
+// conversions.  Positions are stored as an integer cell plus in-cell offsets
+// in [0, 1), so single precision keeps its resolution at large radius.
+#include <math.h>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of
+// (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)),
+// the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// draws of particle `id` of species s at `step` on `stream`
+__device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint64_t id, uint32_t step,
+                                      int stream, int s) {
+    return philox10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, (uint32_t)(stream * 2 + s)),
+                    k0, k1);
+}
+
+// uniform on (0, 1) from one 32-bit word
+template <typename T>
+__device__ __forceinline__ T unif(uint32_t x);
+template <>
+__device__ __forceinline__ float unif<float>(uint32_t x) {
+    return ((float)(x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+template <>
+__device__ __forceinline__ double unif<double>(uint32_t x) {
+    return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+// type-generic math
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
+__device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double m_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_tan(float x) { return tanf(x); }
+__device__ __forceinline__ double m_tan(double x) { return tan(x); }
+__device__ __forceinline__ float m_atan(float x) { return atanf(x); }
+__device__ __forceinline__ double m_atan(double x) { return atan(x); }
+__device__ __forceinline__ void m_sincos2pi(float u, float *s, float *c) { sincospif(2.0f * u, s, c); }
+__device__ __forceinline__ void m_sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
+__device__ __forceinline__ bool m_finite(float x) { return isfinite(x); }
+__device__ __forceinline__ bool m_finite(double x) { return isfinite(x); }
+template <typename T>
+__device__ __forceinline__ T below_one();
+template <>
+__device__ __forceinline__ float below_one<float>() { return 0.99999994f; }
+template <>
+__device__ __forceinline__ double below_one<double>() { return 0.99999999999999989; }
+
+// 128-bit vector access
+__device__ __forceinline__ void ld4(const float4 *p, float &a, float &b, float &c, float &d) {
+    float4 v = *p;
+    a = v.x;
+    b = v.y;
+    c = v.z;
+    d = v.w;
+}
+__device__ __forceinline__ void ld4(const dbl4 *p, double &a, double &b, double &c, double &d) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 u = q[0], v = q[1];
+    a = u.x;
+    b = u.y;
+    c = v.x;
+    d = v.y;
+}
+__device__ __forceinline__ void st4(float4 *p, float a, float b, float c, float d) {
+    *p = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(dbl4 *p, double a, double b, double c, double d) {
+    double2 *q = reinterpret_cast<double2 *>(p);
+    q[0] = make_double2(a, b);
+    q[1] = make_double2(c, d);
+}
+
+// particle in registers
+template <typename T>
+struct PS {
+    int i, j;
+    T oz, orr, vr, vt, vz, ar, az, w;
+};
+
+template <typename T>
+__device__ __forceinline__ PS<T> load_p(const PBuf<T> &b, int idx, int ncz) {
+    PS<T> p;
+    ld4(b.q0 + idx, p.oz, p.orr, p.vr, p.vt);
+    ld4(b.q1 + idx, p.vz, p.ar, p.az, p.w);
+    int c = b.cell[idx];
+    p.i = c % ncz;
+    p.j = c / ncz;
+    return p;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_p(const PBuf<T> &b, int idx, const PS<T> &p, int cell,
+                                        uint64_t id) {
+    st4(b.q0 + idx, p.oz, p.orr, p.vr, p.vt);
+    st4(b.q1 + idx, p.vz, p.ar, p.az, p.w);
+    b.cell[idx] = cell;
+    b.id[idx] = id;
+}
+
+// radial shape factors of Eq. (9) (z-r^2) or Eq. (8) (z-r) in offset form:
+// z-r^2: S_{j+1} = (r^2 - r_j^2)/(r_{j+1}^2 - r_j^2) = o (2j + o)/(2j + 1)
+template <typename T>
+__device__ __forceinline__ void shape_r(int weighting, int j, T o, T &s0, T &s1) {
+    if (weighting == PIC_WEIGHT_ZR) {
+        s1 = o;
+        s0 = (T)1 - o;
+    } else {
+        const T t = (T)(2 * j + 1);
+        s1 = o * ((T)(2 * j) + o) / t;
+        s0 = ((T)1 - o) * (t + o) / t;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void carry(T &off, int &idx) {
+    const T f = m_floor(off);
+    idx += (int)f;
+    off -= f;
+}
+
+// wall of a stored position (domain 0 < z < L, 0 <= r < R; z walls first)
+template <typename T>
+__device__ __forceinline__ int wall_of(int i, T oz, int j, int nz, int nr) {
+    if (i < 0 || (i == 0 && oz == (T)0)) return 0;
+    if (i >= nz - 1) return 1;
+    if (j >= nr - 1) return 2;
+    return -1;
+}
+
+// first push of Sec. 2.3 in the local X-Y frame, then the rotation by theta
+// back to r-theta; a_theta = 0, so v_y' = v_theta and a_r' = a_r cos(theta).
+// The radial step is formed without cancellation:
+// r' - r = (2 r dx + dx^2 + dy^2) / (r' + r).
+template <typename T>
+__device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p) {
+    const T vx = p.vr + (T)0.5 * p.ar * a.dt;
+    const T vy = p.vt;
+    const T vz = p.vz + (T)0.5 * p.az * a.dt;
+    p.oz += vz * a.dt_dz;
+    carry(p.oz, p.i);
+    const T r = ((T)p.j + p.orr) * a.dr;
+    const T dx = vx * a.dt, dy = vy * a.dt;
+    const T xr = r + dx;
+    const T rn = m_sqrt(xr * xr + dy * dy);
+    T c = (T)1, sn = (T)0;
+    if (rn > (T)0) {
+        c = xr / rn;
+        sn = dy / rn;
+    }
+    const T den = rn + r;
+    const T drr = den > (T)0 ? ((T)2 * r * dx + dx * dx + dy * dy) / den : (T)0;
+    T ro = p.orr + drr / a.dr;
+    const T fl = m_floor(ro);
+    int jn = p.j + (int)fl;
+    ro -= fl;
+    if (jn < 0) {
+        jn = 0;
+        ro = (T)0;
+    }
+    p.j = jn;
+    p.orr = ro;
+    p.vr = vx * c + vy * sn;
+    p.vt = -vx * sn + vy * c;
+    p.vz = vz;
+    p.ar = p.ar * c;
+}
+
+template <typename T>
+__device__ __forceinline__ T sigma_of(const Xs<T> &xs, int ch, T E) {
+    const T *sg = xs.sigma + ch * xs.n_e;
+    if (E >= xs.emax) return sg[xs.n_e - 1] * xs.emax / E;
+    if (E <= (T)0) return sg[0];
+    const T x = E * xs.inv_dE;
+    int k = x >= (T)0 ? (int)m_floor(x) : 0;  // also keeps a NaN off the table
+    if (k > xs.n_e - 2) k = xs.n_e - 2;
+    const T f = x - (T)k;
+    return sg[k] + f * (sg[k + 1] - sg[k]);
+}
+
+// Vahedi-Surendra scattering angle (isotropic below 1e-6 eV or on request)
+template <typename T>
+__device__ __forceinline__ T cos_chi(int scatter, T eps, T R) {
+    T c;
+    if (scatter == PIC_SCATTER_ISOTROPIC || eps < (T)1e-6)
+        c = (T)1 - (T)2 * R;
+    else
+        c = ((T)2 + eps - (T)2 * m_pow((T)1 + eps, R)) / eps;
+    return c > (T)1 ? (T)1 : (c < (T)-1 ? (T)-1 : c);
+}
+
+// new direction: cos(chi) u + sin(chi)[cos(phi) e1 + sin(phi) e2] with
+// e1 = (u_y, -u_x, 0)/s, e2 = (u_x u_z, u_y u_z, -s^2)/s, s^2 = u_x^2 + u_y^2
+template <typename T>
+__device__ __forceinline__ void scatter_dir(T ux, T uy, T uz, T cc, T uphi, T &ox, T &oy,
+                                            T &oz) {
+    const T sc = m_sqrt(fmax((T)0, (T)1 - cc * cc));
+    T sp, cp;
+    m_sincos2pi(uphi, &sp, &cp);
+    const T s2 = ux * ux + uy * uy;
+    const T tiny = sizeof(T) == 8 ? (T)1e-24 : (T)1e-12;
+    if (s2 < tiny) {
+        ox = sc * cp;
+        oy = sc * sp * uz;
+        oz = cc * uz;
+        return;
+    }
+    const T s = m_sqrt(s2);
+    ox = cc * ux + sc * (cp * uy + sp * ux * uz) / s;
+    oy = cc * uy + sc * (-cp * ux + sp * uy * uz) / s;
+    oz = cc * uz + sc * (-sp * s2) / s;
+}
+
+template <typename T>
+__device__ __forceinline__ void normals(uint32_t xa, uint32_t xb, T &n0, T &n1) {
+    const T ua = unif<T>(xa), ub = unif<T>(xb);
+    const T rad = m_sqrt((T)-2 * m_log(ua));
+    T s, c;
+    m_sincos2pi(ub, &s, &c);
+    n0 = rad * c;
+    n1 = rad * s;
+}
+
+// block-local tallies, flushed once per block
+struct BlockTally {
+    unsigned long long cnt[PIC_NCOUNT];
+    double q[3];
+};
+
+// deposit one particle's weight with the shape factors at its cell
+template <typename T>
+__device__ __forceinline__ void deposit_global(double *N, int nr, int weighting, const PS<T> &p) {
+    T s0, s1;
+    shape_r(weighting, p.j, p.orr, s0, s1);
+    const T z0 = (T)1 - p.oz, z1 = p.oz;
+    double *g = N + (size_t)p.i * nr + p.j;
+    atomicAdd(g, (double)(p.w * z0 * s0));
+    atomicAdd(g + 1, (double)(p.w * z0 * s1));
+    atomicAdd(g + nr, (double)(p.w * z1 * s0));
+    atomicAdd(g + nr + 1, (double)(p.w * z1 * s1));
+}
+
+// newborn: first push, wall test, deposit, count, append with its order key
+template <typename T>
+__device__ void emit_birth(const StepArgs<T> &a, BlockTally *bt, int ts, int ps, uint64_t pid,
+                           int k, PS<T> q) {
+    atomicAdd(&bt->cnt[PIC_C_BIRTHS + ts], 1ull);
+    first_push(a, q);
+    const int wall = wall_of(q.i, q.oz, q.j, a.nz, a.nr);
+    if (wall >= 0) {
+        atomicAdd(&bt->cnt[PIC_C_ABS + ts * 3 + wall], 1ull);
+        atomicAdd(&bt->q[wall], (double)q.w * a.qch[ts]);
+        return;
+    }
+    const int slot = atomicAdd(a.nb[ts], 1);
+    if (slot >= a.bcap) {
+        atomicOr(&a.ds->status, ST_BIRTH_OVERFLOW);
+        return;
+    }
+    deposit_global(a.N[ts], a.nr, a.weighting, q);
+    const int cell = q.j * a.ncz + q.i;
+    atomicAdd(a.counts[ts] + cell, 1);
+    store_p(a.births[ts], slot, q, cell, 0ull);
+    a.bkey[ts][slot] = ((uint64_t)ps << 63) | (pid << 16) | (uint64_t)k;
+}
+
+// null-collision Monte Carlo (Sec. 2.6) on the post-final-push state
+template <typename T>
+__device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, uint64_t id,
+                                        PS<T> &p) {
+    const uint4 x = draw(a.key0, a.key1, id, a.step, 0, a.s);
+    if ((unsigned long long)x.x >= a.t_null) return;
+    atomicAdd(&bt->cnt[PIC_C_CAND + a.s], 1ull);
+    T gx = p.vr, gy = p.vt, gz = p.vz;
+    T vnx = 0, vny = 0, vnz = 0;
+    if (a.s == 1) {
+        const uint4 y = draw(a.key0, a.key1, id, a.step, 1, a.s);
+        T n0, n1, n2, n3;
+        normals(y.x, y.y, n0, n1);
+        normals(y.z, y.w, n2, n3);
+        vnx = a.v_gas * n0;
+        vny = a.v_gas * n1;
+        vnz = a.v_gas * n2;
+        gx = p.vr - vnx;
+        gy = p.vt - vny;
+        gz = p.vz - vnz;
+    }
+    const T g = m_sqrt(gx * gx + gy * gy + gz * gz);
+    const T E = a.half_m_e * g * g;
+    T nu[kMaxCh];
+    T tot = 0;
+#pragma unroll
+    for (int ch = 0; ch < kMaxCh; ++ch) {
+        nu[ch] = ch < a.xs.n_ch ? a.ng * sigma_of(a.xs, ch, E) * g : (T)0;
+        tot += nu[ch];
+    }
+    if (tot > a.nu_max) atomicAdd(&bt->cnt[PIC_C_NUOVER + a.s], 1ull);
+    const T sel = unif<T>(x.y) * a.nu_max;
+    T cum = 0;
+    int ch = -1;
+#pragma unroll
+    for (int k = 0; k < kMaxCh; ++k) {
+        if (ch < 0 && k < a.xs.n_ch) {
+            cum += nu[k];
+            if (sel < cum) ch = k;
+        }
+    }
+    if (ch < 0) return;
+    const int kind = a.xs.kind[ch];
+    const T thr = a.xs.thr[ch];
+    if ((kind == PIC_XS_EXCITE || kind == PIC_XS_IONIZE) && E <= thr) return;
+    atomicAdd(&bt->cnt[PIC_C_COLL + a.s * 4 + ch], 1ull);
+    if (kind == PIC_XS_CX) {
+        p.vr = vnx;
+        p.vt = vny;
+        p.vz = vnz;
+        return;
+    }
+    const T ux = gx / g, uy = gy / g, uz = gz / g;
+    T dx, dy, dz;
+    if (kind == PIC_XS_ELASTIC) {
+        const T cc = cos_chi(a.scatter, E, unif<T>(x.z));
+        scatter_dir(ux, uy, uz, cc, unif<T>(x.w), dx, dy, dz);
+        const T gn = g * m_sqrt((T)1 - a.two_m_M * ((T)1 - cc));
+        p.vr = gn * dx;
+        p.vt = gn * dy;
+        p.vz = gn * dz;
+    } else if (kind == PIC_XS_EXCITE) {
+        const T Ep = E - thr;
+        const T cc = cos_chi(a.scatter, Ep, unif<T>(x.z));
+        scatter_dir(ux, uy, uz, cc, unif<T>(x.w), dx, dy, dz);
+        const T gn = m_sqrt(a.two_e_m * Ep);
+        p.vr = gn * dx;
+        p.vt = gn * dy;
+        p.vz = gn * dz;
+    } else {  // ionisation
+        const uint4 y = draw(a.key0, a.key1, id, a.step, 1, a.s);
+        const uint4 zz = draw(a.key0, a.key1, id, a.step, 2, a.s);
+        const T Eej = a.xs.B * m_tan(unif<T>(y.x) * m_atan((E - thr) / ((T)2 * a.xs.B)));
+        T Esc = E - thr - Eej;
+        if (Esc < (T)0) Esc = (T)0;
+        const T c1 = cos_chi(a.scatter, Esc, unif<T>(x.z));
+        scatter_dir(ux, uy, uz, c1, unif<T>(x.w), dx, dy, dz);
+        const T c2 = cos_chi(a.scatter, Eej, unif<T>(y.y));
+        T ex, ey, ez;
+        scatter_dir(ux, uy, uz, c2, unif<T>(y.z), ex, ey, ez);
+        const T g1 = m_sqrt(a.two_e_m * Esc), g2 = m_sqrt(a.two_e_m * Eej);
+        PS<T> e2 = p;
+        e2.vr = g2 * ex;
+        e2.vt = g2 * ey;
+        e2.vz = g2 * ez;
+        p.vr = g1 * dx;
+        p.vt = g1 * dy;
+        p.vz = g1 * dz;
+        PS<T> ion = p;
+        T n0, n1, n2, n3;
+        normals(zz.x, zz.y, n0, n1);
+        normals(zz.z, zz.w, n2, n3);
+        ion.vr = a.v_gas * n0;
+        ion.vt = a.v_gas * n1;
+        ion.vz = a.v_gas * n2;
+        ion.ar = p.ar * a.ion_acc;
+        ion.az = p.az * a.ion_acc;
+        emit_birth(a, bt, 0, a.s, id, 0, e2);
+        emit_birth(a, bt, 1, a.s, id, 1, ion);
+    }
+}
+
+constexpr int kThreads = 256;
+constexpr int kPPT = 4;
+constexpr int kChunk = kThreads * kPPT;
+static_assert(kChunk == kStepChunk, "chunk size");
+constexpr int kHalo = 3;
+constexpr int kWinBytes = 16384;
+
+// The fused particle pass (Sec. 2.1 merged cycle).  Each block walks chunks
+// of kChunk particles of the cell-sorted input; chunk positions are close
+// in space, so the deposit goes to a shared-memory window around the
+// chunk's cells and is flushed with one global atomic per touched node.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *win = reinterpret_cast<T *>(smem_raw);
+    double *s_eedf = reinterpret_cast<double *>(smem_raw + kWinBytes);
+    __shared__ BlockTally bt;
+    __shared__ int s_w[4];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int k = tid; k < PIC_NCOUNT; k += blockDim.x) bt.cnt[k] = 0;
+    if (tid < 3) bt.q[tid] = 0.0;
+    if (a.eedf)
+        for (int k = tid; k < a.eedf_bins; k += blockDim.x) s_eedf[k] = 0.0;
+    const int WCAP = kWinBytes / (int)sizeof(T);
+    const int n = *a.n_alive;
+    const int nmain = *a.n_main_src;
+    const int nchunks = (n + kChunk - 1) / kChunk;
+    for (int ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+        const int base = ck * kChunk;
+        const int end = min(base + kChunk, n);
+        __syncthreads();
+        if (tid == 0) {
+            const int pa = a.perm[base], pb = a.perm[end - 1];
+            const int ca = pa < nmain ? a.src_main.cell[pa] : a.src_births.cell[pa - nmain];
+            const int cb = pb < nmain ? a.src_main.cell[pb] : a.src_births.cell[pb - nmain];
+            const int ja = ca / a.ncz, jb = cb / a.ncz;
+            int ilo = 0, ihi = a.ncz - 1;
+            if (ja == jb) {
+                ilo = ca % a.ncz;
+                ihi = cb % a.ncz;
+            }
+            const int wi0 = max(ilo - kHalo, 0), wi1 = min(ihi + 1 + kHalo, a.nz - 1);
+            const int wj0 = max(ja - kHalo, 0), wj1 = min(jb + 1 + kHalo, a.nr - 1);
+            int wz = wi1 - wi0 + 1, wr = wj1 - wj0 + 1;
+            if (wz * wr > WCAP) wz = 0;
+            s_w[0] = wi0;
+            s_w[1] = wj0;
+            s_w[2] = wz;
+            s_w[3] = wr;
+        }
+        __syncthreads();
+        const int wi0 = s_w[0], wj0 = s_w[1], wz = s_w[2], wr = s_w[3];
+        for (int k = tid; k < wz * wr; k += blockDim.x) win[k] = (T)0;
+        __syncthreads();
+#pragma unroll 1
+        for (int m = 0; m < kPPT; ++m) {
+            const int k = base + m * kThreads + tid;
+            int out_cell = -1;
+            if (k < end) {
+                const int pidx = a.perm[k];
+                const bool from_main = pidx < nmain;
+                const PBuf<T> &src = from_main ? a.src_main : a.src_births;
+                const int si = from_main ? pidx : pidx - nmain;
+                PS<T> p = load_p(src, si, a.ncz);
+                const uint64_t id = src.id[si];
+                // gather E at x~ with the deposit's shape factors (Sec. 2.4)
+                T s0, s1;
+                shape_r(a.weighting, p.j, p.orr, s0, s1);
+                const T z0 = (T)1 - p.oz, z1 = p.oz;
+                const auto *Ep = a.E + (size_t)p.i * a.nr + p.j;
+                const auto e00 = Ep[0], e01 = Ep[1], e10 = Ep[a.nr], e11 = Ep[a.nr + 1];
+                const T Ez = z0 * (s0 * e00.x + s1 * e01.x) + z1 * (s0 * e10.x + s1 * e11.x);
+                const T Er = z0 * (s0 * e00.y + s1 * e01.y) + z1 * (s0 * e10.y + s1 * e11.y);
+                // final push (Sec. 2.1 finalpush, Sec. 2.3 in r-z)
+                p.oz += a.kz * Ez;
+                carry(p.oz, p.i);
+                const T ro = p.orr + a.kr * Er;
+                const T fl = m_floor(ro);
+                int jn = p.j + (int)fl;
+                bool axis = false;
+                if (jn < 0) {  // through the axis: |r|, |v_r|, |a_r|
+                    const T rr = -((T)p.j + ro);
+                    const T f2 = m_floor(rr);
+                    jn = (int)f2;
+                    p.orr = rr - f2;
+                    axis = true;
+                } else {
+                    p.orr = ro - fl;
+                }
+                p.j = jn;
+                p.vz += a.kv * Ez;
+                p.vr += a.kv * Er;
+                p.az = (T)0.5 * (a.ka * Ez + p.az);
+                p.ar = (T)0.5 * (a.ka * Er + p.ar);
+                if (axis) {
+                    p.vr = m_abs(p.vr);
+                    p.ar = m_abs(p.ar);
+                }
+                bool alive = true;
+                if (!(m_finite(p.oz) && m_finite(p.orr) && m_finite(p.vr) && m_finite(p.vt) &&
+                      m_finite(p.vz) && m_finite(p.w))) {
+                    atomicOr(&a.ds->status, ST_NAN);
+                    alive = false;
+                }
+                int wall = alive ? wall_of(p.i, p.oz, p.j, a.nz, a.nr) : -1;
+                if (wall >= 0) {
+                    atomicAdd(&bt.cnt[PIC_C_ABS + a.s * 3 + wall], 1ull);
+                    atomicAdd(&bt.q[wall], (double)p.w * a.qch[a.s]);
+                    alive = false;
+                }
+                if (alive) {
+                    collide(a, &bt, id, p);
+                    if (a.eedf) {
+                        const T Ek = a.half_m_e * (p.vr * p.vr + p.vt * p.vt + p.vz * p.vz);
+                        const T x = Ek * a.eedf_scale;
+                        if (x >= (T)0 && x < (T)a.eedf_bins)
+                            atomicAdd(&s_eedf[(int)x], (double)p.w);
+                    }
+                    if (a.do_split) {  // weight-conserving split (Sec. 2.2)
+                        const T wr_ = a.w_ref[p.j];
+                        if (p.w > wr_) {
+                            T Nf = m_floor(p.w / wr_);
+                            if (Nf > (T)kSplitNMax) Nf = (T)kSplitNMax;
+                            int Nc = (int)Nf;
+                            T rem = p.w - Nf * wr_;
+                            if (!(rem > (T)0)) {
+                                Nc -= 1;
+                                rem = p.w - (T)Nc * wr_;
+                            }
+                            if (Nc > 0) {
+                                atomicAdd(&bt.cnt[PIC_C_SPLITS + a.s], 1ull);
+                                PS<T> cp = p;
+                                cp.w = wr_;
+                                p.w = rem;
+                                for (int c = 0; c < Nc; ++c) emit_birth(a, &bt, a.s, a.s, id, 2 + c, cp);
+                            }
+                        }
+                    }
+                    first_push(a, p);
+                    wall = wall_of(p.i, p.oz, p.j, a.nz, a.nr);
+                    if (wall >= 0) {
+                        atomicAdd(&bt.cnt[PIC_C_ABS + a.s * 3 + wall], 1ull);
+                        atomicAdd(&bt.q[wall], (double)p.w * a.qch[a.s]);
+                        alive = false;
+                    }
+                }
+                if (alive) {
+                    out_cell = p.j * a.ncz + p.i;
+                    // deposit at the new x~ (Sec. 2.4)
+                    T r0, r1;
+                    shape_r(a.weighting, p.j, p.orr, r0, r1);
+                    const T y0 = (T)1 - p.oz, y1 = p.oz;
+                    const T c00 = p.w * y0 * r0, c01 = p.w * y0 * r1;
+                    const T c10 = p.w * y1 * r0, c11 = p.w * y1 * r1;
+                    const int li = p.i - wi0, lj = p.j - wj0;
+                    if (li >= 0 && li + 1 < wz && lj >= 0 && lj + 1 < wr) {
+                        T *wp = win + li * wr + lj;
+                        atomicAdd(wp, c00);
+                        atomicAdd(wp + 1, c01);
+                        atomicAdd(wp + wr, c10);
+                        atomicAdd(wp + wr + 1, c11);
+                    } else {
+                        double *g = a.N[a.s] + (size_t)p.i * a.nr + p.j;
+                        atomicAdd(g, (double)c00);
+                        atomicAdd(g + 1, (double)c01);
+                        atomicAdd(g + a.nr, (double)c10);
+                        atomicAdd(g + a.nr + 1, (double)c11);
+                    }
+                }
+                store_p(a.dst_main, k, p, out_cell, id);
+            }
+            // cell histogram of the survivors, one atomic per distinct cell per warp
+            const unsigned peers = __match_any_sync(0xffffffffu, out_cell);
+            if (out_cell >= 0 && lane == __ffs(peers) - 1)
+                atomicAdd(a.counts[a.s] + out_cell, __popc(peers));
+        }
+        __syncthreads();
+        for (int k = tid; k < wz * wr; k += blockDim.x) {
+            const T v = win[k];
+            if (v != (T)0) {
+                const int gi = wi0 + k / wr, gj = wj0 + k % wr;
+                atomicAdd(a.N[a.s] + (size_t)gi * a.nr + gj, (double)v);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < PIC_NCOUNT; k += blockDim.x)
+        if (bt.cnt[k]) atomicAdd(&a.ds->cnt[k], bt.cnt[k]);
+    if (tid < 3 && bt.q[tid] != 0.0) atomicAdd(&a.ds->qabs[tid], bt.q[tid]);
+    if (a.eedf)
+        for (int k = tid; k < a.eedf_bins; k += blockDim.x)
+            if (s_eedf[k] != 0.0) atomicAdd(a.eedf + k, s_eedf[k]);
+}
+
+template <typename T>
+void launch_step(const StepArgs<T> &a, int grid, cudaStream_t st) {
+    const size_t smem = kWinBytes + (size_t)(a.eedf ? a.eedf_bins : 0) * sizeof(double);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_step<T><<<grid, kThreads, smem, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// load: uniform density n0, weights ~ cell volume (Sec. 2.2, Eq. (3))
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_load(PBuf<T> dst, int64_t n, int s, int nz, int nr, double dz, double dr,
+                       double n0, double T_eV, double m, uint32_t k0, uint32_t k1,
+                       int64_t ncell) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int ncz = nz - 1;
+    const int64_t base = n / ncell, rem = n % ncell;
+    const int64_t c = p < rem * (base + 1) ? p / (base + 1) : rem + (p - rem * (base + 1)) / base;
+    const int64_t ppc = base + (c < rem ? 1 : 0);
+    const int i = (int)(c % ncz), j = (int)(c / ncz);
+    const uint4 x = draw(k0, k1, (uint64_t)p, 0xFFFFFFFFu, 3, s);
+    const uint4 y = draw(k0, k1, (uint64_t)p, 0xFFFFFFFFu, 4, s);
+    const double oz = unif<double>(x.x);
+    // uniform in r^2 inside the cell: offset = u(2j+1) / (sqrt(j^2 + u(2j+1)) + j)
+    const double t = unif<double>(x.y) * (2.0 * j + 1.0);
+    const double orr = t / (sqrt((double)j * j + t) + (double)j);
+    double g0, g1, g2, g3;
+    normals<double>(x.z, x.w, g0, g1);
+    normals<double>(y.x, y.y, g2, g3);
+    const double sig = sqrt(T_eV * kQe / m);
+    const double r0 = j * dr, r1 = (j + 1) * dr;
+    const double w = n0 * kPi * (r1 * r1 - r0 * r0) * dz / (double)ppc;
+    PS<T> q;
+    q.i = i;
+    q.j = j;
+    q.oz = (T)oz < (T)1 ? (T)oz : below_one<T>();
+    q.orr = (T)orr < (T)1 ? (T)orr : below_one<T>();
+    q.vr = (T)(sig * g0);
+    q.vt = (T)(sig * g1);
+    q.vz = (T)(sig * g2);
+    q.ar = q.az = (T)0;
+    q.w = (T)w;
+    store_p(dst, (int)p, q, (int)c, (uint64_t)p);
+}
+
+template <typename T>
+void launch_load(PBuf<T> dst, int64_t n, int s, int nz, int nr, double dz, double dr, double n0,
+                 double T_eV, double m, uint32_t key0, uint32_t key1, int64_t ncell,
+                 cudaStream_t st) {
+    if (n <= 0) return;
+    k_load<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, n, s, nz, nr, dz, dr, n0, T_eV, m,
+                                                            key0, key1, ncell);
+}
+
+// plain deposit of entries [0, n) (used after a load or an upload)
+template <typename T>
+__global__ void k_deposit(PBuf<T> src, const int32_t *n_dev, int nz, int nr, int weighting,
+                          double *N) {
+    const int n = *n_dev;
+    const int ncz = nz - 1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (src.cell[k] < 0) continue;
+        PS<T> p = load_p(src, k, ncz);
+        deposit_global(N, nr, weighting, p);
+    }
+}
+
+template <typename T>
+void launch_deposit(PBuf<T> src, const int32_t *n_dev, int nz, int nr, int weighting, double *N,
+                    cudaStream_t st) {
+    k_deposit<T><<<152 * 8, 256, 0, st>>>(src, n_dev, nz, nr, weighting, N);
+}
+
+// absolute (r, z) -> cell + offsets
+template <typename T>
+__global__ void k_from_abs(PBuf<T> dst, int64_t n, const double *r, const double *z,
+                           const double *vr, const double *vt, const double *vz, const double *ar,
+                           const double *az, const double *w, const uint64_t *id, int nz, int nr,
+                           double dz, double dr) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double xz = z[k] / dz, xr = r[k] / dr;
+    int i = (int)floor(xz), j = (int)floor(xr);
+    i = i < 0 ? 0 : (i > nz - 2 ? nz - 2 : i);
+    j = j < 0 ? 0 : (j > nr - 2 ? nr - 2 : j);
+    PS<T> q;
+    q.i = i;
+    q.j = j;
+    const T oz = (T)(xz - i), orr = (T)(xr - j);
+    q.oz = oz < (T)1 ? (oz < (T)0 ? (T)0 : oz) : below_one<T>();
+    q.orr = orr < (T)1 ? (orr < (T)0 ? (T)0 : orr) : below_one<T>();
+    q.vr = (T)vr[k];
+    q.vt = (T)vt[k];
+    q.vz = (T)vz[k];
+    q.ar = (T)ar[k];
+    q.az = (T)az[k];
+    q.w = (T)w[k];
+    store_p(dst, (int)k, q, j * (nz - 1) + i, id[k]);
+}
+
+template <typename T>
+void launch_from_abs(PBuf<T> dst, int64_t n, const double *r, const double *z, const double *vr,
+                     const double *vt, const double *vz, const double *ar, const double *az,
+                     const double *w, const uint64_t *id, int nz, int nr, double dz, double dr,
+                     cudaStream_t st) {
+    if (n <= 0) return;
+    k_from_abs<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, n, r, z, vr, vt, vz, ar, az, w,
+                                                                id, nz, nr, dz, dr);
+}
+
+// cell + offsets -> absolute, in perm order
+template <typename T>
+__global__ void k_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, const int32_t *perm,
+                         int64_t n, double *r, double *z, double *vr, double *vt, double *vz,
+                         double *ar, double *az, double *w, uint64_t *id, int32_t *cell, int nz,
+                         double dz, double dr) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int nmain = *n_main_src;
+    const int p = perm[k];
+    const PBuf<T> &src = p < nmain ? sm : sb;
+    const int si = p < nmain ? p : p - nmain;
+    PS<T> q = load_p(src, si, nz - 1);
+    z[k] = ((double)q.i + (double)q.oz) * dz;
+    r[k] = ((double)q.j + (double)q.orr) * dr;
+    vr[k] = q.vr;
+    vt[k] = q.vt;
+    vz[k] = q.vz;
+    ar[k] = q.ar;
+    az[k] = q.az;
+    w[k] = q.w;
+    id[k] = src.id[si];
+    cell[k] = src.cell[si];
+}
+
+template <typename T>
+void launch_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, const int32_t *perm,
+                   int64_t n, double *r, double *z, double *vr, double *vt, double *vz, double *ar,
+                   double *az, double *w, uint64_t *id, int32_t *cell, int nz, double dz, double dr,
+                   cudaStream_t st) {
+    if (n <= 0) return;
+    k_to_abs<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sm, sb, n_main_src, perm, n, r, z, vr,
+                                                              vt, vz, ar, az, w, id, cell, nz, dz,
+                                                              dr);
+}
+
+#define PIC_INST(T)                                                                              \
+    template void launch_step<T>(const StepArgs<T> &, int, cudaStream_t);                        \
+    template void launch_load<T>(PBuf<T>, int64_t, int, int, int, double, double, double, double, \
+                                 double, uint32_t, uint32_t, int64_t, cudaStream_t);              \
+    template void launch_deposit<T>(PBuf<T>, const int32_t *, int, int, int, double *,           \
+                                    cudaStream_t);                                               \
+    template void launch_from_abs<T>(PBuf<T>, int64_t, const double *, const double *,          \
+                                     const double *, const double *, const double *,            \
+                                     const double *, const double *, const double *,            \
+                                     const uint64_t *, int, int, double, double, cudaStream_t);  \
+    template void launch_to_abs<T>(PBuf<T>, PBuf<T>, const int32_t *, const int32_t *, int64_t,  \
+                                   double *, double *, double *, double *, double *, double *,   \
+                                   double *, double *, uint64_t *, int32_t *, int, double,       \
+                                   double, cudaStream_t);
+PIC_INST(float)
+PIC_INST(double)
+
+}  // namespace pic

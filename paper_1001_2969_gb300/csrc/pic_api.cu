@@ -1,0 +1,1097 @@
+// pic_api.cu -- C ABI of the GB300 r-z implicit PIC/MC library
+// (Wang, Jiang & Wang, arXiv:1001.2969): configuration checks, device state,
+// and the per-step orchestration of the field solve, the particle pass and
+// the cell sort on the caller's stream.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+namespace {
+
+constexpr int kNumTiming = 5;  // solve, particle pass e, particle pass i, sort+births, other
+constexpr int kSmallBirthsHost = 2048;
+
+struct RawBuf {
+    void *q0 = nullptr, *q1 = nullptr;
+    int32_t *cell = nullptr;
+    uint64_t *id = nullptr;
+};
+
+template <typename T>
+PBuf<T> view(const RawBuf &b) {
+    PBuf<T> p;
+    p.q0 = reinterpret_cast<typename V4<T>::type *>(b.q0);
+    p.q1 = reinterpret_cast<typename V4<T>::type *>(b.q1);
+    p.cell = b.cell;
+    p.id = b.id;
+    return p;
+}
+
+struct SpecDev {
+    RawBuf main[2], births[2];
+    uint64_t *bkey[2] = {nullptr, nullptr};
+    int32_t *perm = nullptr, *counts = nullptr, *cursor = nullptr, *block_sums = nullptr;
+    int32_t *d_nmain[2] = {nullptr, nullptr}, *d_nbirths[2] = {nullptr, nullptr};
+    int32_t *d_nalive = nullptr, *d_ntotal = nullptr;
+    void *sigma = nullptr;  // T[n_ch][n_e]
+    void *w_ref = nullptr;  // T[ncr]
+    int64_t cap = 0, bcap = 0;
+    uint64_t next_id = 0;
+    int64_t n_alive_host = 0;
+};
+
+struct EvRec {
+    int phase;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct pic_handle {
+    pic_config cfg;
+    std::vector<double> own_sigma[2], own_thr[2], own_rf, own_phiL;
+    std::vector<int32_t> own_kind[2];
+    int nz = 0, nr = 0, ncz = 0, ncr = 0, ncell = 0, ng = 0;
+    double dz = 0, dr = 0;
+    bool mixed = false;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<void *, size_t>> allocs;
+    DevScalars *ds = nullptr;
+    int32_t *scal = nullptr;  // per-species device scalars (n_main, n_births, n_alive, n_total)
+    SpecDev sp[2];
+    int cur = 0;
+    double *N[2] = {nullptr, nullptr};
+    double *rho = nullptr, *chi = nullptr, *phi = nullptr, *Ez = nullptr, *Er = nullptr, *V = nullptr;
+    void *E2 = nullptr;
+    double *phiL_d = nullptr;
+    bool has_phiL = false;
+    double *m_acc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double *eedf = nullptr;
+    double *tmp_grid[3] = {nullptr, nullptr, nullptr};
+    MGWork mg;
+    RadixTmp rtmp;
+    int64_t step = 0;
+    int64_t nsamples = 0;
+    int64_t mg_cycles_total = 0, steps_total = 0;
+    int last_cycles = 0;
+    double last_res = 0.0;
+    double ngas = 0.0, nu_max[2] = {0, 0}, p_null[2] = {0, 0};
+    unsigned long long t_null[2] = {0, 0};
+    std::string err;
+    bool prof = false;
+    std::vector<EvRec> ev_live;
+    std::vector<cudaEvent_t> ev_pool;
+    double t_ms[kNumTiming] = {0, 0, 0, 0, 0};
+    int64_t launches = 0, particle_launches = 0;
+};
+
+namespace {
+
+pic_status fail(pic_handle *h, pic_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+void *dalloc(pic_handle *h, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (h->cfg.alloc) {
+        p = h->cfg.alloc(bytes, h->cfg.alloc_ctx, (void *)h->st);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (!p) throw std::bad_alloc();
+    h->allocs.push_back({p, bytes});
+    return p;
+}
+
+void free_all(pic_handle *h) {
+    for (auto &a : h->allocs) {
+        if (h->cfg.free)
+            h->cfg.free(a.first, a.second, h->cfg.alloc_ctx, (void *)h->st);
+        else if (!h->cfg.alloc)
+            cudaFree(a.first);
+    }
+    h->allocs.clear();
+}
+
+pic_status cuda_check(pic_handle *h, const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(h, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// ---- null-collision frequency bound (Sec. 2.6) ----
+// nu_max = n_g max_E sigma_tot(E) sqrt(2 E e / m) over the table: endpoints
+// of every linear segment and, on falling segments, the stationary point of
+// (alpha + beta E) sqrt(E) at E = -alpha / (3 beta); beyond the table nu
+// falls as E^-1/2.  A relative margin of 1e-6 absorbs rounding.
+double nu_max_of(const pic_handle *h, int s) {
+    const int ne = h->cfg.xs[s].n_e, nch = h->cfg.xs[s].n_ch;
+    const double emax = h->cfg.xs[s].E_max_eV, dE = emax / (ne - 1), m = h->cfg.sp[s].m;
+    auto tot = [&](int k) {
+        double t = 0.0;
+        for (int ch = 0; ch < nch; ++ch) t += h->own_sigma[s][(size_t)ch * ne + k];
+        return t;
+    };
+    double best = 0.0;
+    for (int k = 0; k < ne; ++k) {
+        const double E = k * dE;
+        best = std::max(best, tot(k) * sqrt(2.0 * E * kQe / m));
+    }
+    for (int k = 0; k + 1 < ne; ++k) {
+        const double s0 = tot(k), s1 = tot(k + 1);
+        const double beta = (s1 - s0) / dE;
+        if (beta < 0.0) {
+            const double alpha = s0 - beta * (k * dE);
+            const double Es = -alpha / (3.0 * beta);
+            if (Es > k * dE && Es < (k + 1) * dE)
+                best = std::max(best, (alpha + beta * Es) * sqrt(2.0 * Es * kQe / m));
+        }
+    }
+    return h->ngas * best * (1.0 + 1e-6);
+}
+
+pic_status validate(const pic_config *c, std::string &why) {
+    auto bad = [&](const char *m) {
+        why = m;
+        return PIC_ERR_ARG;
+    };
+    if (!(c->mesh.R > 0) || !(c->mesh.L > 0)) return bad("mesh R and L must be positive");
+    if (c->mesh.nz < 3 || !pow2(c->mesh.nz - 1)) return bad("nz must be 2^k + 1 >= 3");
+    if (c->mesh.nr < 3 || c->mesh.nr > 2049) return bad("nr must be in [3, 2049]");
+    if ((int64_t)(c->mesh.nz - 1) * (c->mesh.nr - 1) >= (1LL << 30)) return bad("mesh too large");
+    if (!(c->dt > 0)) return bad("dt must be positive");
+    if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return bad("precision");
+    if (c->weighting != PIC_WEIGHT_ZR2 && c->weighting != PIC_WEIGHT_ZR) return bad("weighting");
+    if (c->chi_face != PIC_CHI_MAX && c->chi_face != PIC_CHI_MEAN) return bad("chi_face");
+    if (c->scatter != PIC_SCATTER_VS && c->scatter != PIC_SCATTER_ISOTROPIC) return bad("scatter");
+    if (c->split_every < 0) return bad("split_every must be >= 0");
+    if (c->mg_max_cycles < 1) return bad("mg_max_cycles must be >= 1");
+    if (c->eedf_bins < 0 || c->eedf_bins > 4096) return bad("eedf_bins must be in [0, 4096]");
+    if (c->eedf_bins > 0 && !(c->eedf_emax_eV > 0)) return bad("eedf_emax_eV must be positive");
+    if (!(c->gas.T_K > 0) || !(c->gas.m_gas > 0) || c->gas.p_Pa < 0) return bad("gas");
+    if (c->rf.n < 0 || (c->rf.n > 0 && (!c->rf.amp_V || !c->rf.freq_Hz || !c->rf.phase_rad)))
+        return bad("rf");
+    for (int s = 0; s < 2; ++s) {
+        const pic_species &p = c->sp[s];
+        if (!(p.m > 0) || p.q == 0 || p.n0 < 0 || p.T_eV < 0) return bad("species q, m, n0, T");
+        if (p.n_init < 0 || p.capacity < p.n_init || p.capacity < 1) return bad("species capacity");
+        const int64_t bc = c->births_capacity > 0 ? c->births_capacity : std::max<int64_t>(4096, p.capacity / 2);
+        if (p.capacity + bc >= (1LL << 31) - 1) return bad("capacity too large for 32-bit indices");
+        const pic_xsec &x = c->xs[s];
+        if (x.n_e < 2 || !(x.E_max_eV > 0) || x.n_ch < 1 || x.n_ch > PIC_MAX_CH || !x.sigma_m2 ||
+            !x.threshold_eV || !x.kind)
+            return bad("cross-section table");
+        for (int ch = 0; ch < x.n_ch; ++ch) {
+            const int k = x.kind[ch];
+            if (s == 0 && k != PIC_XS_ELASTIC && k != PIC_XS_EXCITE && k != PIC_XS_IONIZE)
+                return bad("electron channels must be ELASTIC, EXCITE or IONIZE");
+            if (s == 1 && k != PIC_XS_CX) return bad("ion channels must be CX");
+            if (k == PIC_XS_IONIZE && !(x.B_eV > 0)) return bad("ionisation needs B_eV > 0");
+        }
+    }
+    return PIC_OK;
+}
+
+double voltage(const pic_handle *h, double t) {
+    double v = 0.0;
+    for (int k = 0; k < h->cfg.rf.n; ++k)
+        v += h->own_rf[k] * sin(2.0 * kPi * h->own_rf[h->cfg.rf.n + k] * t + h->own_rf[2 * h->cfg.rf.n + k]);
+    return v;
+}
+
+// node volumes of Sec. 2.4 (z-r^2 or z-r), inner halves on the boundary rows
+// and on r = R
+void node_volumes(const pic_handle *h, std::vector<double> &V) {
+    V.assign((size_t)h->ng, 0.0);
+    for (int i = 0; i < h->nz; ++i) {
+        const double hz = (i == 0 || i == h->nz - 1) ? 0.5 * h->dz : h->dz;
+        for (int j = 0; j < h->nr; ++j) {
+            const double r = j * h->dr, rp = (j + 1) * h->dr, rm = (j - 1) * h->dr, r1 = h->dr;
+            double v;
+            if (h->cfg.weighting == PIC_WEIGHT_ZR) {
+                if (j == 0)
+                    v = kPi / 3.0 * r1 * r1;
+                else if (j == h->nr - 1)
+                    v = kPi / 3.0 * h->dr * (2.0 * r + rm);
+                else
+                    v = kPi / 3.0 * (rp * (r + rp) - rm * (r + rm));
+            } else {
+                if (j == 0)
+                    v = kPi / 2.0 * r1 * r1;
+                else if (j == h->nr - 1)
+                    v = kPi / 2.0 * (r * r - rm * rm);
+                else
+                    v = kPi / 2.0 * (rp * rp - rm * rm);
+            }
+            V[(size_t)i * h->nr + j] = v * hz;
+        }
+    }
+}
+
+__global__ void k_iota(int32_t *p, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) p[k] = k;
+}
+
+__global__ void k_scale(const double *src, double *dst, int n, double f) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = src[k] * f;
+}
+
+cudaEvent_t ev_get(pic_handle *h) {
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseTimer {
+    pic_handle *h;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(pic_handle *hh, int ph) : h(hh), phase(ph) {
+        if (h->prof) {
+            a = ev_get(h);
+            cudaEventRecord(a, h->st);
+        }
+    }
+    ~PhaseTimer() {
+        if (h->prof) {
+            cudaEvent_t b = ev_get(h);
+            cudaEventRecord(b, h->st);
+            h->ev_live.push_back({phase, a, b});
+        }
+    }
+};
+
+void resolve_events(pic_handle *h) {
+    if (h->ev_live.empty()) return;
+    cudaStreamSynchronize(h->st);
+    for (auto &r : h->ev_live) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        h->t_ms[r.phase] += ms;
+        h->ev_pool.push_back(r.a);
+        h->ev_pool.push_back(r.b);
+    }
+    h->ev_live.clear();
+}
+
+template <typename T>
+void alloc_tables(pic_handle *h) {
+    for (int s = 0; s < 2; ++s) {
+        const pic_xsec &x = h->cfg.xs[s];
+        std::vector<T> sg((size_t)x.n_ch * x.n_e);
+        for (size_t k = 0; k < sg.size(); ++k) sg[k] = (T)h->own_sigma[s][k];
+        h->sp[s].sigma = dalloc(h, sg.size() * sizeof(T));
+        cudaMemcpyAsync(h->sp[s].sigma, sg.data(), sg.size() * sizeof(T), cudaMemcpyHostToDevice, h->st);
+        // reference weight of radial cell j (Sec. 2.2): n0 pi (r_{j+1}^2 - r_j^2) dz / ppc_ref
+        const int64_t base = h->cfg.sp[s].n_init / h->ncell;
+        const double ppc = (double)(base > 0 ? base : 1);
+        std::vector<T> wr(h->ncr);
+        for (int j = 0; j < h->ncr; ++j) {
+            const double r0 = j * h->dr, r1 = (j + 1) * h->dr;
+            wr[j] = (T)(h->cfg.sp[s].n0 * kPi * (r1 * r1 - r0 * r0) * h->dz / ppc);
+        }
+        h->sp[s].w_ref = dalloc(h, wr.size() * sizeof(T));
+        cudaMemcpyAsync(h->sp[s].w_ref, wr.data(), wr.size() * sizeof(T), cudaMemcpyHostToDevice, h->st);
+    }
+    cudaStreamSynchronize(h->st);
+}
+
+void alloc_rawbuf(pic_handle *h, RawBuf &b, int64_t n, size_t tsize) {
+    b.q0 = dalloc(h, (size_t)n * 4 * tsize);
+    b.q1 = dalloc(h, (size_t)n * 4 * tsize);
+    b.cell = (int32_t *)dalloc(h, (size_t)n * sizeof(int32_t));
+    b.id = (uint64_t *)dalloc(h, (size_t)n * sizeof(uint64_t));
+}
+
+void setup_device(pic_handle *h) {
+    const size_t ts = h->mixed ? sizeof(float) : sizeof(double);
+    h->ds = (DevScalars *)dalloc(h, sizeof(DevScalars));
+    cudaMemsetAsync(h->ds, 0, sizeof(DevScalars), h->st);
+    h->scal = (int32_t *)dalloc(h, 2 * 8 * sizeof(int32_t));
+    cudaMemsetAsync(h->scal, 0, 2 * 8 * sizeof(int32_t), h->st);
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        d.cap = h->cfg.sp[s].capacity;
+        d.bcap = h->cfg.births_capacity > 0 ? h->cfg.births_capacity : std::max<int64_t>(4096, d.cap / 2);
+        for (int k = 0; k < 2; ++k) {
+            alloc_rawbuf(h, d.main[k], d.cap, ts);
+            alloc_rawbuf(h, d.births[k], d.bcap, ts);
+            d.bkey[k] = (uint64_t *)dalloc(h, (size_t)d.bcap * sizeof(uint64_t));
+        }
+        d.perm = (int32_t *)dalloc(h, (size_t)d.cap * sizeof(int32_t));
+        d.counts = (int32_t *)dalloc(h, (size_t)h->ncell * sizeof(int32_t));
+        d.cursor = (int32_t *)dalloc(h, (size_t)h->ncell * sizeof(int32_t));
+        d.block_sums = (int32_t *)dalloc(h, (size_t)(h->ncell / 4096 + 2) * sizeof(int32_t));
+        int32_t *sc = h->scal + s * 8;
+        d.d_nmain[0] = sc + 0;
+        d.d_nmain[1] = sc + 1;
+        d.d_nbirths[0] = sc + 2;
+        d.d_nbirths[1] = sc + 3;
+        d.d_nalive = sc + 4;
+        d.d_ntotal = sc + 5;
+    }
+    const size_t gb = (size_t)h->ng * sizeof(double);
+    for (int s = 0; s < 2; ++s) h->N[s] = (double *)dalloc(h, gb);
+    h->rho = (double *)dalloc(h, gb);
+    h->chi = (double *)dalloc(h, gb);
+    h->phi = (double *)dalloc(h, gb);
+    h->Ez = (double *)dalloc(h, gb);
+    h->Er = (double *)dalloc(h, gb);
+    h->V = (double *)dalloc(h, gb);
+    for (int k = 0; k < 3; ++k) h->tmp_grid[k] = (double *)dalloc(h, gb);
+    for (int k = 0; k < 5; ++k) h->m_acc[k] = (double *)dalloc(h, gb);
+    h->E2 = dalloc(h, (size_t)h->ng * 2 * ts);
+    h->phiL_d = (double *)dalloc(h, (size_t)h->nr * sizeof(double));
+    h->eedf = (double *)dalloc(h, (size_t)std::max(1, h->cfg.eedf_bins) * sizeof(double));
+    for (int s = 0; s < 2; ++s) cudaMemsetAsync(h->N[s], 0, gb, h->st);
+    cudaMemsetAsync(h->phi, 0, gb, h->st);
+    cudaMemsetAsync(h->Ez, 0, gb, h->st);
+    cudaMemsetAsync(h->Er, 0, gb, h->st);
+    cudaMemsetAsync(h->rho, 0, gb, h->st);
+    cudaMemsetAsync(h->chi, 0, gb, h->st);
+    for (int k = 0; k < 5; ++k) cudaMemsetAsync(h->m_acc[k], 0, gb, h->st);
+    cudaMemsetAsync(h->eedf, 0, (size_t)std::max(1, h->cfg.eedf_bins) * sizeof(double), h->st);
+    if (h->has_phiL)
+        cudaMemcpyAsync(h->phiL_d, h->own_phiL.data(), (size_t)h->nr * sizeof(double),
+                        cudaMemcpyHostToDevice, h->st);
+    std::vector<double> V;
+    node_volumes(h, V);
+    cudaMemcpyAsync(h->V, V.data(), gb, cudaMemcpyHostToDevice, h->st);
+    // multigrid hierarchy
+    int nl = 0;
+    for (int n = h->nz;; n = (n + 1) / 2) {
+        MGLevel &lv = h->mg.lv[nl++];
+        lv.nz = n;
+        lv.dz = h->cfg.mesh.L / (n - 1);
+        const size_t g = (size_t)n * h->nr;
+        lv.chi = (double *)dalloc(h, g * sizeof(double));
+        lv.cz = (double *)dalloc(h, g * sizeof(double));
+        lv.cr = (double *)dalloc(h, g * sizeof(double));
+        lv.u = (double *)dalloc(h, g * sizeof(double));
+        lv.f = (double *)dalloc(h, g * sizeof(double));
+        lv.cz32 = (float *)dalloc(h, g * sizeof(float));
+        lv.cr32 = (float *)dalloc(h, g * sizeof(float));
+        lv.u32 = (float *)dalloc(h, g * sizeof(float));
+        lv.f32 = (float *)dalloc(h, g * sizeof(float));
+        if (n == 3) break;
+    }
+    h->mg.nlev = nl;
+    h->mg.r = (double *)dalloc(h, gb);
+    h->mg.f0 = (double *)dalloc(h, gb);
+    h->mg.ds = h->ds;
+    // births radix scratch
+    int64_t bmax = std::max(h->sp[0].bcap, h->sp[1].bcap);
+    h->rtmp.max_n = (int)bmax;
+    h->rtmp.k0 = (uint64_t *)dalloc(h, (size_t)bmax * 8);
+    h->rtmp.k1 = (uint64_t *)dalloc(h, (size_t)bmax * 8);
+    h->rtmp.v0 = (uint32_t *)dalloc(h, (size_t)bmax * 4);
+    h->rtmp.v1 = (uint32_t *)dalloc(h, (size_t)bmax * 4);
+    h->rtmp.hist = (uint32_t *)dalloc(h, (size_t)256 * (bmax / 2048 + 2) * 4);
+    if (h->mixed)
+        alloc_tables<float>(h);
+    else
+        alloc_tables<double>(h);
+}
+
+template <typename T>
+void deposit_current(pic_handle *h) {
+    for (int s = 0; s < 2; ++s) cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), h->st);
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        launch_deposit<T>(view<T>(d.main[h->cur]), d.d_nmain[h->cur], h->nz, h->nr,
+                          h->cfg.weighting, h->N[s], h->st);
+        launch_deposit<T>(view<T>(d.births[h->cur]), d.d_nbirths[h->cur], h->nz, h->nr,
+                          h->cfg.weighting, h->N[s], h->st);
+        h->launches += 2;
+    }
+}
+
+template <typename T>
+pic_status load_all(pic_handle *h) {
+    const uint32_t k0 = (uint32_t)h->cfg.seed, k1 = (uint32_t)(h->cfg.seed >> 32);
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        const pic_species &p = h->cfg.sp[s];
+        const int64_t n = h->cfg.load ? p.n_init : 0;
+        launch_load<T>(view<T>(d.main[0]), n, s, h->nz, h->nr, h->dz, h->dr, p.n0, p.T_eV, p.m, k0,
+                       k1, h->ncell, h->st);
+        if (n > 0) k_iota<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(d.perm, (int)n);
+        const int32_t vals[8] = {(int32_t)n, 0, 0, 0, (int32_t)n, (int32_t)n, 0, 0};
+        cudaMemcpyAsync(h->scal + s * 8, vals, sizeof(vals), cudaMemcpyHostToDevice, h->st);
+        d.next_id = (uint64_t)n;
+        d.n_alive_host = n;
+        h->launches += 2;
+    }
+    h->cur = 0;
+    deposit_current<T>(h);
+    cudaStreamSynchronize(h->st);
+    return cuda_check(h, "load");
+}
+
+template <typename T>
+void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_set) {
+    const pic_species &p = h->cfg.sp[s];
+    const double dt = h->cfg.dt, qm = p.q / p.m;
+    a.nz = h->nz;
+    a.nr = h->nr;
+    a.ncz = h->ncz;
+    a.ncr = h->ncr;
+    a.s = s;
+    a.qch[0] = h->cfg.sp[0].q;
+    a.qch[1] = h->cfg.sp[1].q;
+    a.weighting = h->cfg.weighting;
+    a.scatter = h->cfg.scatter;
+    a.kz = (T)(0.5 * qm * dt * dt / h->dz);
+    a.kr = (T)(0.5 * qm * dt * dt / h->dr);
+    a.kv = (T)(0.5 * qm * dt);
+    a.ka = (T)qm;
+    a.dt = (T)dt;
+    a.dt_dz = (T)(dt / h->dz);
+    a.dt_dr = (T)(dt / h->dr);
+    a.dr = (T)h->dr;
+    a.t_null = h->t_null[s];
+    a.nu_max = (T)h->nu_max[s];
+    a.ng = (T)h->ngas;
+    a.half_m_e = (T)(0.5 * p.m / kQe);
+    a.two_e_m = (T)(2.0 * kQe / p.m);
+    a.two_m_M = (T)(2.0 * p.m / h->cfg.gas.m_gas);
+    a.v_gas = (T)sqrt(kKB * h->cfg.gas.T_K / h->cfg.gas.m_gas);
+    a.ion_acc = (T)((h->cfg.sp[1].q * h->cfg.sp[0].m) / (h->cfg.sp[0].q * h->cfg.sp[1].m));
+    const pic_xsec &x = h->cfg.xs[s];
+    a.xs.sigma = (const T *)h->sp[s].sigma;
+    a.xs.n_e = x.n_e;
+    a.xs.n_ch = x.n_ch;
+    a.xs.emax = (T)x.E_max_eV;
+    a.xs.inv_dE = (T)((x.n_e - 1) / x.E_max_eV);
+    for (int ch = 0; ch < kMaxCh; ++ch) {
+        a.xs.kind[ch] = ch < x.n_ch ? h->own_kind[s][ch] : 0;
+        a.xs.thr[ch] = ch < x.n_ch ? (T)h->own_thr[s][ch] : (T)0;
+    }
+    a.xs.B = (T)x.B_eV;
+    a.key0 = (uint32_t)h->cfg.seed;
+    a.key1 = (uint32_t)(h->cfg.seed >> 32);
+    a.step = (uint32_t)h->step;
+    a.do_split = h->cfg.split_every > 0 &&
+                 (h->step % h->cfg.split_every) == h->cfg.split_every - 1;
+    a.w_ref = (const T *)h->sp[s].w_ref;
+    a.E = (const typename V2<T>::type *)h->E2;
+    SpecDev &d = h->sp[s];
+    a.src_main = view<T>(d.main[src_set]);
+    a.src_births = view<T>(d.births[src_set]);
+    a.n_main_src = d.d_nmain[src_set];
+    a.perm = d.perm;
+    a.n_alive = d.d_nalive;
+    a.dst_main = view<T>(d.main[dst_set]);
+    for (int t = 0; t < 2; ++t) {
+        a.births[t] = view<T>(h->sp[t].births[dst_set]);
+        a.bkey[t] = h->sp[t].bkey[dst_set];
+        a.nb[t] = h->sp[t].d_nbirths[dst_set];
+        a.N[t] = h->N[t];
+        a.counts[t] = h->sp[t].counts;
+    }
+    a.bcap = (int)std::min(h->sp[0].bcap, h->sp[1].bcap);
+    a.ds = h->ds;
+    a.eedf = (s == 0 && h->cfg.eedf_bins > 0) ? h->eedf : nullptr;
+    a.eedf_bins = h->cfg.eedf_bins;
+    a.eedf_scale = h->cfg.eedf_bins > 0 ? (T)(h->cfg.eedf_bins / h->cfg.eedf_emax_eV) : (T)0;
+}
+
+struct StepHost {
+    int32_t n_births[2];
+    int32_t n_total[2];
+    int32_t status;
+};
+
+template <typename T>
+pic_status one_step(pic_handle *h) {
+    cudaStream_t st = h->st;
+    pic_status result = PIC_OK;
+    const int src = h->cur, dst = 1 - h->cur;
+    {
+        PhaseTimer t(h, 0);
+        launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q,
+                        h->cfg.sp[0].q * h->cfg.sp[0].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[0].m),
+                        h->cfg.sp[1].q * h->cfg.sp[1].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[1].m),
+                        h->rho, h->chi, h->ng, st);
+        const double Vt = voltage(h, (double)(h->step + 1) * h->cfg.dt);
+        FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
+        int L = 0;
+        double res = 0.0;
+        const int r = mg_solve(fd, h->mg, h->rho, h->chi, Vt, h->has_phiL ? h->phiL_d : nullptr,
+                               h->phi, true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, &res,
+                               &L, st);
+        h->last_cycles = r >= 0 ? r : -r - 1;
+        h->last_res = res;
+        h->mg_cycles_total += h->last_cycles;
+        if (r < 0) result = PIC_ERR_NOT_CONVERGED;
+        launch_efield<T>(h->phi, h->Ez, h->Er, (typename V2<T>::type *)h->E2, h->nz, h->nr, h->dz,
+                         h->dr, st);
+        h->launches += L + 2;
+    }
+    for (int s = 0; s < 2; ++s) {
+        cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), st);
+        cudaMemsetAsync(h->sp[s].counts, 0, (size_t)h->ncell * sizeof(int32_t), st);
+        cudaMemsetAsync(h->sp[s].d_nbirths[dst], 0, sizeof(int32_t), st);
+    }
+    for (int s = 0; s < 2; ++s) {
+        PhaseTimer t(h, 1 + s);
+        StepArgs<T> a;
+        fill_step_args<T>(h, a, s, src, dst);
+        const int64_t nch = (h->sp[s].n_alive_host + kStepChunk - 1) / kStepChunk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 8));
+        launch_step<T>(a, grid, st);
+        h->launches += 1;
+        h->particle_launches += 1;
+    }
+    {
+        PhaseTimer t(h, 3);
+        for (int s = 0; s < 2; ++s) {
+            SpecDev &d = h->sp[s];
+            // entries the pass wrote into the destination main buffer
+            cudaMemcpyAsync(d.d_nmain[dst], d.d_nalive, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+            launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, st);
+            launch_rank<T>(view<T>(d.main[dst]), d.d_nmain[dst], view<T>(d.births[dst]),
+                           d.d_nbirths[dst], d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, st);
+            h->launches += 4;
+        }
+        StepHost sh;
+        for (int s = 0; s < 2; ++s) {
+            cudaMemcpyAsync(&sh.n_births[s], h->sp[s].d_nbirths[dst], 4, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(&sh.n_total[s], h->sp[s].d_ntotal, 4, cudaMemcpyDeviceToHost, st);
+        }
+        cudaMemcpyAsync(&sh.status, &h->ds->status, 4, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        pic_status ce = cuda_check(h, "particle pass");
+        if (ce != PIC_OK) return ce;
+        if (sh.status & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
+            // leave the state at the last completed step
+            cudaMemsetAsync(&h->ds->status, 0, 4, st);
+            deposit_current<T>(h);
+            cudaStreamSynchronize(st);
+            return fail(h, PIC_ERR_CAPACITY, (sh.status & ST_CAPACITY)
+                                                 ? "particle capacity exceeded"
+                                                 : "births capacity exceeded");
+        }
+        for (int s = 0; s < 2; ++s) {
+            SpecDev &d = h->sp[s];
+            const int nb = sh.n_births[s];
+            if (nb > 0) {
+                if (nb <= kSmallBirthsHost) {
+                    launch_birth_ids_small(d.bkey[dst], d.births[dst].id, nb, d.next_id, st);
+                    h->launches += 1;
+                } else {
+                    int L = 0;
+                    launch_birth_ids_radix(d.bkey[dst], d.births[dst].id, nb, d.next_id, h->rtmp, &L, st);
+                    h->launches += L;
+                }
+                d.next_id += (uint64_t)nb;
+            }
+            cudaMemcpyAsync(d.d_nalive, d.d_ntotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+            d.n_alive_host = sh.n_total[s];
+        }
+        if (sh.status & ST_NAN) {
+            cudaMemsetAsync(&h->ds->status, 0, 4, st);
+            result = PIC_ERR_NUMERIC;
+            h->err = "non-finite particle state (particles dropped)";
+        }
+    }
+    {
+        PhaseTimer t(h, 4);
+        launch_moments(h->N[0], h->N[1], h->V, h->phi, h->Ez, h->Er, h->m_acc[0], h->m_acc[1],
+                       h->m_acc[2], h->m_acc[3], h->m_acc[4], h->ng, st);
+        h->launches += 1;
+    }
+    h->nsamples += 1;
+    h->steps_total += 1;
+    h->cur = dst;
+    h->step += 1;
+    pic_status ce = cuda_check(h, "step");
+    if (ce != PIC_OK) return ce;
+    return result;
+}
+
+void release(pic_handle *h, void *p) {
+    for (size_t k = 0; k < h->allocs.size(); ++k)
+        if (h->allocs[k].first == p) {
+            if (h->cfg.free)
+                h->cfg.free(p, h->allocs[k].second, h->cfg.alloc_ctx, (void *)h->st);
+            else if (!h->cfg.alloc)
+                cudaFree(p);
+            h->allocs.erase(h->allocs.begin() + k);
+            return;
+        }
+}
+
+template <typename T>
+pic_status set_particles_t(pic_handle *h, int s, const pic_particles_view *v) {
+    SpecDev &d = h->sp[s];
+    const int64_t n = v->n;
+    if (n > d.cap) return fail(h, PIC_ERR_CAPACITY, "more particles than the species capacity");
+    uint64_t mx = 0;
+    for (int64_t k = 0; k < n; ++k) mx = std::max<uint64_t>(mx, v->id[k] + 1);
+    double *stage = n > 0 ? (double *)dalloc(h, (size_t)n * 8 * sizeof(double)) : nullptr;
+    uint64_t *sid = n > 0 ? (uint64_t *)dalloc(h, (size_t)n * sizeof(uint64_t)) : nullptr;
+    const double *srcs[8] = {v->r, v->z, v->vr, v->vt, v->vz, v->ar, v->az, v->w};
+    for (int f = 0; f < 8 && n > 0; ++f)
+        cudaMemcpyAsync(stage + (size_t)f * n, srcs[f], (size_t)n * sizeof(double),
+                        cudaMemcpyHostToDevice, h->st);
+    if (n > 0) cudaMemcpyAsync(sid, v->id, (size_t)n * sizeof(uint64_t), cudaMemcpyHostToDevice, h->st);
+    const int c = h->cur;
+    launch_from_abs<T>(view<T>(d.main[c]), n, stage, stage + n, stage + 2 * n, stage + 3 * n,
+                       stage + 4 * n, stage + 5 * n, stage + 6 * n, stage + 7 * n, sid, h->nz, h->nr,
+                       h->dz, h->dr, h->st);
+    const int32_t nn = (int32_t)n, zero = 0;
+    cudaMemcpyAsync(d.d_nmain[c], &nn, 4, cudaMemcpyHostToDevice, h->st);
+    cudaMemcpyAsync(d.d_nbirths[c], &zero, 4, cudaMemcpyHostToDevice, h->st);
+    cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), h->st);
+    launch_hist<T>(view<T>(d.main[c]), d.d_nmain[c], d.counts, h->st);
+    launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, h->st);
+    launch_rank<T>(view<T>(d.main[c]), d.d_nmain[c], view<T>(d.births[c]), d.d_nbirths[c],
+                   d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->st);
+    cudaMemcpyAsync(d.d_nalive, d.d_ntotal, 4, cudaMemcpyDeviceToDevice, h->st);
+    h->launches += 6;
+    d.next_id = mx;
+    d.n_alive_host = n;
+    deposit_current<T>(h);
+    cudaStreamSynchronize(h->st);
+    if (stage) release(h, stage);
+    if (sid) release(h, sid);
+    return cuda_check(h, "set_particles");
+}
+
+template <typename T>
+pic_status get_particles_t(pic_handle *h, int s, pic_particles_view *v, int64_t capacity) {
+    SpecDev &d = h->sp[s];
+    int32_t n = 0;
+    cudaMemcpyAsync(&n, d.d_nalive, 4, cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    const int64_t m = std::min<int64_t>(n, capacity);
+    v->n = m;
+    if (m <= 0) return PIC_OK;
+    double *stage = (double *)dalloc(h, (size_t)n * 8 * sizeof(double));
+    uint64_t *sid = (uint64_t *)dalloc(h, (size_t)n * sizeof(uint64_t));
+    int32_t *scell = (int32_t *)dalloc(h, (size_t)n * sizeof(int32_t));
+    const int c = h->cur;
+    launch_to_abs<T>(view<T>(d.main[c]), view<T>(d.births[c]), d.d_nmain[c], d.perm, n, stage + n,
+                     stage, stage + 2 * n, stage + 3 * n, stage + 4 * n, stage + 5 * n,
+                     stage + 6 * n, stage + 7 * n, sid, scell, h->nz, h->dz, h->dr, h->st);
+    h->launches += 1;
+    double *dsts[8] = {v->z, v->r, v->vr, v->vt, v->vz, v->ar, v->az, v->w};
+    for (int f = 0; f < 8; ++f)
+        if (dsts[f])
+            cudaMemcpyAsync(dsts[f], stage + (size_t)f * n, (size_t)m * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->st);
+    if (v->id) cudaMemcpyAsync(v->id, sid, (size_t)m * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->st);
+    if (v->cell)
+        cudaMemcpyAsync(v->cell, scell, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    release(h, stage);
+    release(h, sid);
+    release(h, scell);
+    return cuda_check(h, "get_particles");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pic_status_string(pic_status s) {
+    switch (s) {
+    case PIC_OK: return "ok";
+    case PIC_ERR_ARG: return "invalid argument";
+    case PIC_ERR_CAPACITY: return "capacity exceeded";
+    case PIC_ERR_CUDA: return "CUDA error";
+    case PIC_ERR_NOT_CONVERGED: return "multigrid not converged";
+    case PIC_ERR_NUMERIC: return "non-finite particle state";
+    case PIC_ERR_TIMEOUT: return "device wait timed out";
+    case PIC_ERR_STATE: return "invalid state";
+    }
+    return "unknown";
+}
+
+const char *pic_last_error(const pic_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+pic_status pic_init(const pic_config *cfg, pic_handle **out) {
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return PIC_ERR_ARG;
+    std::string why;
+    if (validate(cfg, why) != PIC_OK) {
+        fprintf(stderr, "pic_init: %s\n", why.c_str());
+        return PIC_ERR_ARG;
+    }
+    pic_handle *h = new (std::nothrow) pic_handle();
+    if (!h) return PIC_ERR_ARG;
+    h->cfg = *cfg;
+    h->st = (cudaStream_t)cfg->stream;
+    for (int s = 0; s < 2; ++s) {
+        const pic_xsec &x = cfg->xs[s];
+        h->own_sigma[s].assign(x.sigma_m2, x.sigma_m2 + (size_t)x.n_ch * x.n_e);
+        h->own_thr[s].assign(x.threshold_eV, x.threshold_eV + x.n_ch);
+        h->own_kind[s].assign(x.kind, x.kind + x.n_ch);
+        h->cfg.xs[s].sigma_m2 = h->own_sigma[s].data();
+        h->cfg.xs[s].threshold_eV = h->own_thr[s].data();
+        h->cfg.xs[s].kind = h->own_kind[s].data();
+    }
+    h->own_rf.resize(3 * (size_t)std::max(cfg->rf.n, 0));
+    for (int k = 0; k < cfg->rf.n; ++k) {
+        h->own_rf[k] = cfg->rf.amp_V[k];
+        h->own_rf[cfg->rf.n + k] = cfg->rf.freq_Hz[k];
+        h->own_rf[2 * cfg->rf.n + k] = cfg->rf.phase_rad[k];
+    }
+    h->has_phiL = cfg->phi_zL != nullptr;
+    if (h->has_phiL) h->own_phiL.assign(cfg->phi_zL, cfg->phi_zL + cfg->mesh.nr);
+    h->cfg.phi_zL = nullptr;
+    h->cfg.rf.amp_V = h->cfg.rf.freq_Hz = h->cfg.rf.phase_rad = nullptr;
+    h->nz = cfg->mesh.nz;
+    h->nr = cfg->mesh.nr;
+    h->ncz = h->nz - 1;
+    h->ncr = h->nr - 1;
+    h->ncell = h->ncz * h->ncr;
+    h->ng = h->nz * h->nr;
+    h->dz = cfg->mesh.L / h->ncz;
+    h->dr = cfg->mesh.R / h->ncr;
+    h->mixed = cfg->precision == PIC_MIXED;
+    h->ngas = cfg->gas.p_Pa / (kKB * cfg->gas.T_K);
+    for (int s = 0; s < 2; ++s) {
+        h->nu_max[s] = nu_max_of(h, s);
+        h->p_null[s] = 1.0 - exp(-h->nu_max[s] * cfg->dt);
+        // candidate iff (x + 1/2) 2^-32 < P_null  <=>  x < ceil(P_null 2^32 - 1/2)
+        const double c = ldexp(h->p_null[s], 32) - 0.5;
+        h->t_null[s] = c <= 0.0 ? 0ull : (unsigned long long)ceil(c);
+    }
+    try {
+        setup_device(h);
+        pic_status s = h->mixed ? load_all<float>(h) : load_all<double>(h);
+        if (s != PIC_OK) {
+            fprintf(stderr, "pic_init: %s\n", h->err.c_str());
+            free_all(h);
+            delete h;
+            return s;
+        }
+    } catch (const std::bad_alloc &) {
+        fprintf(stderr, "pic_init: device allocation failed\n");
+        free_all(h);
+        delete h;
+        return PIC_ERR_CUDA;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_handle *h, int32_t nsteps) {
+    if (!h) return PIC_ERR_ARG;
+    if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps < 0");
+    pic_status first = PIC_OK;
+    for (int k = 0; k < nsteps; ++k) {
+        pic_status s = h->mixed ? one_step<float>(h) : one_step<double>(h);
+        if (s == PIC_ERR_NOT_CONVERGED || s == PIC_ERR_NUMERIC) {
+            if (first == PIC_OK) first = s;
+            continue;
+        }
+        if (s != PIC_OK) return s;
+    }
+    return first;
+}
+
+pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, double V,
+                           double *phi, int32_t on_device, pic_solve_info *info) {
+    if (!h || !rho || !chi || !phi) return fail(h, PIC_ERR_ARG, "null argument");
+    const size_t gb = (size_t)h->ng * sizeof(double);
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaMemcpyAsync(h->tmp_grid[0], rho, gb, kin, h->st);
+    cudaMemcpyAsync(h->tmp_grid[1], chi, gb, kin, h->st);
+    FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
+    int L = 0;
+    double res = 0.0;
+    const int r = mg_solve(fd, h->mg, h->tmp_grid[0], h->tmp_grid[1], V,
+                           h->has_phiL ? h->phiL_d : nullptr, h->tmp_grid[2], false, h->mixed,
+                           h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, h->st);
+    h->launches += L;
+    cudaMemcpyAsync(phi, h->tmp_grid[2], gb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    if (info) {
+        info->cycles = r >= 0 ? r : -r - 1;
+        info->rel_residual = res;
+    }
+    pic_status ce = cuda_check(h, "field_solve");
+    if (ce != PIC_OK) return ce;
+    return r >= 0 ? PIC_OK : PIC_ERR_NOT_CONVERGED;
+}
+
+pic_status pic_moments(pic_handle *h, pic_moments_out *out, int32_t reset) {
+    if (!h || !out) return fail(h, PIC_ERR_ARG, "null argument");
+    const size_t gb = (size_t)h->ng * sizeof(double);
+    const double f = h->nsamples > 0 ? 1.0 / (double)h->nsamples : 0.0;
+    double *dst[5] = {out->ne, out->ni, out->phi, out->Ez, out->Er};
+    for (int k = 0; k < 5; ++k) {
+        if (!dst[k]) continue;
+        if (out->on_device) {
+            k_scale<<<(h->ng + 255) / 256, 256, 0, h->st>>>(h->m_acc[k], dst[k], h->ng, f);
+        } else {
+            std::vector<double> tmp((size_t)h->ng);
+            cudaMemcpyAsync(tmp.data(), h->m_acc[k], gb, cudaMemcpyDeviceToHost, h->st);
+            cudaStreamSynchronize(h->st);
+            for (int q = 0; q < h->ng; ++q) dst[k][q] = tmp[q] * f;
+        }
+    }
+    if (out->eedf && h->cfg.eedf_bins > 0) {
+        if (out->on_device) {
+            k_scale<<<(h->cfg.eedf_bins + 255) / 256, 256, 0, h->st>>>(h->eedf, out->eedf, h->cfg.eedf_bins, f);
+        } else {
+            std::vector<double> tmp((size_t)h->cfg.eedf_bins);
+            cudaMemcpyAsync(tmp.data(), h->eedf, tmp.size() * 8, cudaMemcpyDeviceToHost, h->st);
+            cudaStreamSynchronize(h->st);
+            for (int q = 0; q < h->cfg.eedf_bins; ++q) out->eedf[q] = tmp[q] * f;
+        }
+    }
+    DevScalars ds;
+    cudaMemcpyAsync(&ds, h->ds, sizeof(ds), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    if (out->counters) {
+        for (int k = 0; k < PIC_NCOUNT; ++k) out->counters[k] = (int64_t)ds.cnt[k];
+        out->counters[PIC_C_MGCYC] = h->mg_cycles_total;
+        out->counters[PIC_C_STEPS] = h->steps_total;
+    }
+    if (out->charge)
+        for (int k = 0; k < 3; ++k) out->charge[k] = ds.qabs[k];
+    out->nsamples = h->nsamples;
+    if (reset) {
+        for (int k = 0; k < 5; ++k) cudaMemsetAsync(h->m_acc[k], 0, gb, h->st);
+        cudaMemsetAsync(h->eedf, 0, (size_t)std::max(1, h->cfg.eedf_bins) * 8, h->st);
+        cudaMemsetAsync(h->ds->cnt, 0, sizeof(ds.cnt), h->st);
+        cudaMemsetAsync(h->ds->qabs, 0, sizeof(ds.qabs), h->st);
+        h->nsamples = 0;
+        h->mg_cycles_total = 0;
+        h->steps_total = 0;
+        cudaStreamSynchronize(h->st);
+    }
+    return cuda_check(h, "moments");
+}
+
+pic_status pic_get_particles(pic_handle *h, int32_t s, pic_particles_view *view_, int64_t capacity) {
+    if (!h || !view_ || s < 0 || s > 1) return fail(h, PIC_ERR_ARG, "bad argument");
+    try {
+        return h->mixed ? get_particles_t<float>(h, s, view_, capacity)
+                        : get_particles_t<double>(h, s, view_, capacity);
+    } catch (const std::bad_alloc &) {
+        return fail(h, PIC_ERR_CUDA, "staging allocation failed");
+    }
+}
+
+pic_status pic_set_particles(pic_handle *h, int32_t s, const pic_particles_view *v) {
+    if (!h || !v || s < 0 || s > 1 || v->n < 0) return fail(h, PIC_ERR_ARG, "bad argument");
+    if (v->n > 0 && (!v->r || !v->z || !v->vr || !v->vt || !v->vz || !v->ar || !v->az || !v->w || !v->id))
+        return fail(h, PIC_ERR_ARG, "null particle array");
+    try {
+        pic_status st = h->mixed ? set_particles_t<float>(h, s, v) : set_particles_t<double>(h, s, v);
+        return st;
+    } catch (const std::bad_alloc &) {
+        return fail(h, PIC_ERR_CUDA, "staging allocation failed");
+    }
+}
+
+pic_status pic_set_step(pic_handle *h, int64_t step) {
+    if (!h || step < 0) return fail(h, PIC_ERR_ARG, "bad step");
+    h->step = step;
+    return PIC_OK;
+}
+
+pic_status pic_set_boundary(pic_handle *h, const double *phi_zL, int32_t on_device) {
+    if (!h) return PIC_ERR_ARG;
+    if (!phi_zL) {
+        h->has_phiL = false;
+        return PIC_OK;
+    }
+    cudaMemcpyAsync(h->phiL_d, phi_zL, (size_t)h->nr * sizeof(double),
+                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st);
+    h->has_phiL = true;
+    if (!on_device) cudaStreamSynchronize(h->st);
+    return cuda_check(h, "set_boundary");
+}
+
+pic_status pic_get_fields(pic_handle *h, double *rho, double *chi, double *phi, double *Ez,
+                          double *Er, int32_t on_device) {
+    if (!h) return PIC_ERR_ARG;
+    launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q,
+                    h->cfg.sp[0].q * h->cfg.sp[0].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[0].m),
+                    h->cfg.sp[1].q * h->cfg.sp[1].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[1].m),
+                    h->rho, h->chi, h->ng, h->st);
+    h->launches += 1;
+    const size_t gb = (size_t)h->ng * sizeof(double);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    double *src[5] = {h->rho, h->chi, h->phi, h->Ez, h->Er};
+    double *dst[5] = {rho, chi, phi, Ez, Er};
+    for (int q = 0; q < 5; ++q)
+        if (dst[q]) cudaMemcpyAsync(dst[q], src[q], gb, k, h->st);
+    cudaStreamSynchronize(h->st);
+    return cuda_check(h, "get_fields");
+}
+
+pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64_t *next_id) {
+    if (!h) return PIC_ERR_ARG;
+    int32_t n[2] = {0, 0};
+    for (int s = 0; s < 2; ++s) cudaMemcpyAsync(&n[s], h->sp[s].d_nalive, 4, cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    if (n_alive) {
+        n_alive[0] = n[0];
+        n_alive[1] = n[1];
+    }
+    if (step) *step = h->step;
+    if (next_id) {
+        next_id[0] = h->sp[0].next_id;
+        next_id[1] = h->sp[1].next_id;
+    }
+    return cuda_check(h, "get_counts");
+}
+
+static const uint64_t kCkptMagic = 0x50494352475a3031ull;  // "PICRGZ01"
+
+pic_status pic_save(pic_handle *h, const char *path) {
+    if (!h || !path) return PIC_ERR_ARG;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint for writing");
+    int64_t hdr[8] = {(int64_t)kCkptMagic, h->nz, h->nr, h->step, h->mixed ? 1 : 0, 0, 0, 0};
+    uint64_t ids[2] = {h->sp[0].next_id, h->sp[1].next_id};
+    fwrite(hdr, sizeof(hdr), 1, f);
+    fwrite(ids, sizeof(ids), 1, f);
+    std::vector<double> g((size_t)h->ng);
+    for (double *src : {h->phi, h->N[0], h->N[1]}) {
+        cudaMemcpy(g.data(), src, g.size() * 8, cudaMemcpyDeviceToHost);
+        fwrite(g.data(), 8, g.size(), f);
+    }
+    pic_status st = PIC_OK;
+    for (int s = 0; s < 2 && st == PIC_OK; ++s) {
+        int64_t n = 0;
+        int32_t n32 = 0;
+        cudaMemcpy(&n32, h->sp[s].d_nalive, 4, cudaMemcpyDeviceToHost);
+        n = n32;
+        std::vector<double> a((size_t)std::max<int64_t>(n, 1) * 8);
+        std::vector<uint64_t> id((size_t)std::max<int64_t>(n, 1));
+        pic_particles_view v;
+        v.n = n;
+        v.r = a.data();
+        v.z = a.data() + n;
+        v.vr = a.data() + 2 * n;
+        v.vt = a.data() + 3 * n;
+        v.vz = a.data() + 4 * n;
+        v.ar = a.data() + 5 * n;
+        v.az = a.data() + 6 * n;
+        v.w = a.data() + 7 * n;
+        v.id = id.data();
+        v.cell = nullptr;
+        st = pic_get_particles(h, s, &v, n);
+        fwrite(&n, 8, 1, f);
+        fwrite(a.data(), 8, (size_t)n * 8, f);
+        fwrite(id.data(), 8, (size_t)n, f);
+    }
+    fclose(f);
+    return st;
+}
+
+pic_status pic_load(pic_handle *h, const char *path) {
+    if (!h || !path) return PIC_ERR_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint");
+    int64_t hdr[8];
+    uint64_t ids[2];
+    if (fread(hdr, sizeof(hdr), 1, f) != 1 || (uint64_t)hdr[0] != kCkptMagic || hdr[1] != h->nz ||
+        hdr[2] != h->nr || fread(ids, sizeof(ids), 1, f) != 1) {
+        fclose(f);
+        return fail(h, PIC_ERR_ARG, "checkpoint does not match this handle");
+    }
+    std::vector<double> g((size_t)h->ng), N0((size_t)h->ng), N1((size_t)h->ng);
+    bool ok = fread(g.data(), 8, g.size(), f) == g.size() && fread(N0.data(), 8, N0.size(), f) == N0.size() &&
+              fread(N1.data(), 8, N1.size(), f) == N1.size();
+    pic_status st = ok ? PIC_OK : fail(h, PIC_ERR_ARG, "truncated checkpoint");
+    for (int s = 0; s < 2 && st == PIC_OK; ++s) {
+        int64_t n = 0;
+        if (fread(&n, 8, 1, f) != 1 || n < 0 || n > h->sp[s].cap) {
+            st = fail(h, PIC_ERR_ARG, "bad particle count in checkpoint");
+            break;
+        }
+        std::vector<double> a((size_t)std::max<int64_t>(n, 1) * 8);
+        std::vector<uint64_t> id((size_t)std::max<int64_t>(n, 1));
+        if (fread(a.data(), 8, (size_t)n * 8, f) != (size_t)n * 8 || fread(id.data(), 8, (size_t)n, f) != (size_t)n) {
+            st = fail(h, PIC_ERR_ARG, "truncated checkpoint");
+            break;
+        }
+        pic_particles_view v;
+        v.n = n;
+        v.r = a.data();
+        v.z = a.data() + n;
+        v.vr = a.data() + 2 * n;
+        v.vt = a.data() + 3 * n;
+        v.vz = a.data() + 4 * n;
+        v.ar = a.data() + 5 * n;
+        v.az = a.data() + 6 * n;
+        v.w = a.data() + 7 * n;
+        v.id = id.data();
+        v.cell = nullptr;
+        st = pic_set_particles(h, s, &v);
+    }
+    fclose(f);
+    if (st != PIC_OK) return st;
+    h->step = hdr[3];
+    h->sp[0].next_id = ids[0];
+    h->sp[1].next_id = ids[1];
+    cudaMemcpy(h->phi, g.data(), g.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(h->N[0], N0.data(), N0.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(h->N[1], N1.data(), N1.size() * 8, cudaMemcpyHostToDevice);
+    return cuda_check(h, "load");
+}
+
+pic_status pic_profile(pic_handle *h, int32_t on) {
+    if (!h) return PIC_ERR_ARG;
+    h->prof = on != 0;
+    return PIC_OK;
+}
+
+pic_status pic_timings(pic_handle *h, double *ms, int64_t *particle_launches, int64_t *all_launches,
+                       int32_t reset) {
+    if (!h) return PIC_ERR_ARG;
+    resolve_events(h);
+    if (ms)
+        for (int k = 0; k < kNumTiming; ++k) ms[k] = h->t_ms[k];
+    if (particle_launches) *particle_launches = h->particle_launches;
+    if (all_launches) *all_launches = h->launches;
+    if (reset) {
+        for (int k = 0; k < kNumTiming; ++k) h->t_ms[k] = 0.0;
+        h->particle_launches = 0;
+        h->launches = 0;
+    }
+    return PIC_OK;
+}
+
+void pic_destroy(pic_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->st);
+    resolve_events(h);
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

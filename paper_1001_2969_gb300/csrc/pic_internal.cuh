@@ -1,0 +1,213 @@
+// pic_internal.cuh -- device data layout, kernel argument blocks and launcher
+// declarations of the GB300 r-z implicit PIC/MC library (arXiv:1001.2969).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pic.h"
+
+namespace pic {
+
+// CODATA 2018 values
+constexpr double kQe = 1.602176634e-19;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kKB = 1.380649e-23;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxCh = PIC_MAX_CH;
+constexpr int kSplitNMax = 4096;  // copies per parent per split, at most
+
+// status bits raised by kernels
+enum : int {
+    ST_BIRTH_OVERFLOW = 1,
+    ST_CAPACITY = 2,
+    ST_NAN = 4,
+    ST_TIMEOUT = 8,
+};
+
+// four-wide vectors: float4 for the mixed path, two 16-byte halves for FP64
+struct alignas(16) dbl4 {
+    double x, y, z, w;
+};
+template <typename T>
+struct V4;
+template <>
+struct V4<float> {
+    using type = float4;
+};
+template <>
+struct V4<double> {
+    using type = dbl4;
+};
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+    using type = float2;
+};
+template <>
+struct V2<double> {
+    using type = double2;
+};
+
+// Particle store of one species (structure of 128-bit vectors):
+//   q0 = {dz offset in [0,1), dr offset in [0,1), v_r, v_theta}
+//   q1 = {v_z, a_r, a_z, w}
+//   cell = j (nz-1) + i of the stored position x~, -1 when dead
+//   id = 64-bit identity that keys the Philox draws
+template <typename T>
+struct PBuf {
+    typename V4<T>::type *q0;
+    typename V4<T>::type *q1;
+    int32_t *cell;
+    uint64_t *id;
+};
+
+// device-side scalars of one handle
+struct DevScalars {
+    int32_t n_alive[2];     // particles the next pass reads through perm
+    int32_t n_main[2];      // main entries of the current set
+    int32_t n_births[2][2]; // births in births buffer [set][species]
+    int32_t status;
+    int32_t pad;
+    unsigned long long cnt[PIC_NCOUNT];
+    double qabs[3];
+    unsigned long long mg_res_bits;  // max |residual| of the last residual kernel
+    unsigned long long mg_aux_bits;
+};
+
+// cross-section block for the particle kernel
+template <typename T>
+struct Xs {
+    const T *sigma;  // [n_ch][n_e]
+    int n_e, n_ch;
+    T emax, inv_dE;
+    int kind[kMaxCh];
+    T thr[kMaxCh];
+    T B;
+};
+
+// per-launch arguments of the fused particle kernel (one species)
+template <typename T>
+struct StepArgs {
+    int nz, nr, ncz, ncr;
+    int s;          // species of this launch
+    double qch[2];  // species charges (absorbed-charge tallies)
+    int weighting;  // PIC_WEIGHT_*
+    int scatter;    // PIC_SCATTER_*
+    // final push: offsets/velocities/accelerations change per unit E
+    T kz, kr, kv, ka;
+    // first push
+    T dt, dt_dz, dt_dr, dr;
+    // Monte Carlo
+    unsigned long long t_null;  // candidate iff word < t_null
+    T nu_max, ng, half_m_e;     // half_m_e = m / (2 e): E[eV] = half_m_e g^2
+    T two_e_m;                  // 2 e / m: g^2 = two_e_m E[eV]
+    T two_m_M;                  // 2 m / M_gas (elastic energy loss)
+    T v_gas;                    // sqrt(k T_gas / M_gas)
+    T ion_acc;                  // a_ion = a_e * ion_acc (newborn ion)
+    Xs<T> xs;
+    uint32_t key0, key1, step;
+    // splitting
+    int do_split;
+    const T *w_ref;  // [ncr]
+    // fields at the nodes {E_z, E_r}
+    const typename V2<T>::type *E;
+    // input set, read through perm
+    PBuf<T> src_main, src_births;
+    const int32_t *n_main_src;
+    const int32_t *perm;
+    const int32_t *n_alive;
+    // output set
+    PBuf<T> dst_main;
+    PBuf<T> births[2];
+    uint64_t *bkey[2];
+    int32_t *nb[2];
+    int bcap;
+    double *N[2];
+    int32_t *counts[2];
+    DevScalars *ds;
+    double *eedf;
+    int eedf_bins;
+    T eedf_scale;  // bins per eV
+};
+
+constexpr int kStepChunk = 1024;  // particles per chunk of the particle kernel
+
+// ---- launchers (particles.cu) ----
+template <typename T>
+void launch_step(const StepArgs<T> &a, int grid, cudaStream_t st);
+template <typename T>
+void launch_load(PBuf<T> dst, int64_t n, int s, int nz, int nr, double dz, double dr,
+                 double n0, double T_eV, double m, uint32_t key0, uint32_t key1,
+                 int64_t ncell_pop, cudaStream_t st);
+template <typename T>
+void launch_deposit(PBuf<T> src, const int32_t *n_dev, int nz, int nr, int weighting,
+                    double *N, cudaStream_t st);
+template <typename T>
+void launch_from_abs(PBuf<T> dst, int64_t n, const double *r, const double *z, const double *vr,
+                     const double *vt, const double *vz, const double *ar, const double *az,
+                     const double *w, const uint64_t *id, int nz, int nr, double dz, double dr,
+                     cudaStream_t st);
+template <typename T>
+void launch_to_abs(PBuf<T> src_main, PBuf<T> src_births, const int32_t *n_main_src,
+                   const int32_t *perm, int64_t n, double *r, double *z, double *vr, double *vt,
+                   double *vz, double *ar, double *az, double *w, uint64_t *id, int32_t *cell,
+                   int nz, double dz, double dr, cudaStream_t st);
+
+// ---- launchers (sortk.cu) ----
+template <typename T>
+void launch_hist(PBuf<T> buf, const int32_t *n_dev, int32_t *counts, cudaStream_t st);
+// exclusive scan of counts[ncell] into cursor, total into *n_alive, capacity check
+void launch_scan(const int32_t *counts, int32_t *cursor, int ncell, int32_t *block_sums,
+                 int32_t *n_alive, int64_t capacity, DevScalars *ds, cudaStream_t st);
+template <typename T>
+void launch_rank(PBuf<T> main, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,
+                 int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
+                 const int32_t *status, cudaStream_t st);
+// assigns births ids next_id + rank of (key) among the nb births
+void launch_birth_ids_small(const uint64_t *key, uint64_t *id, int nb, uint64_t next_id,
+                            cudaStream_t st);
+struct RadixTmp {
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    uint32_t *hist;
+    int max_n;
+};
+void launch_birth_ids_radix(const uint64_t *key, uint64_t *id, int nb, uint64_t next_id,
+                            RadixTmp tmp, int *launches, cudaStream_t st);
+
+// ---- multigrid (field.cu) ----
+struct MGLevel {
+    int nz;
+    double dz;
+    double *chi, *cz, *cr, *u, *f;
+    float *cz32, *cr32, *u32, *f32;
+};
+struct MGWork {
+    int nlev;
+    MGLevel lv[16];
+    double *r;        // fine residual
+    double *f0;       // fine right-hand side
+    DevScalars *ds;   // residual max goes to ds->mg_res_bits
+};
+struct FieldDims {
+    int nz, nr;
+    double dz, dr, L;
+    int chi_face;
+};
+void launch_finalize(const double *Ne, const double *Ni, const double *V, double q0, double q1,
+                     double chi0, double chi1, double *rho, double *chi, int ng, cudaStream_t st);
+// multigrid solve into phi (device); returns cycles, residual and the launch count
+int mg_solve(const FieldDims &fd, MGWork &mg, const double *rho, const double *chi, double V,
+             const double *phi_zL, double *phi, bool warm, bool mixed, double tol, int max_cycles,
+             double *rel_res, int *launches, cudaStream_t st);
+template <typename T>
+void launch_efield(const double *phi, double *Ez, double *Er, typename V2<T>::type *E2, int nz,
+                   int nr, double dz, double dr, cudaStream_t st);
+void launch_moments(const double *Ne, const double *Ni, const double *V, const double *phi,
+                    const double *Ez, const double *Er, double *m_ne, double *m_ni,
+                    double *m_phi, double *m_ez, double *m_er, int ng, cudaStream_t st);
+
+}  // namespace pic

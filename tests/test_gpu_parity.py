@@ -1,0 +1,285 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 path 1e-12 relative per step (normalised by each output's
+largest magnitude), integer work bit-exact (cells, ids, collision and split
+counts, absorbed counts); mixed FP32/FP64 path 2e-5 relative, integer
+decisions equal except where FP32 rounding moves a value across a threshold
+(a handful, counted and bounded).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import C_ABS, C_BIRTHS, C_CAND, C_COLL, C_SPLITS, Oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 2e-5}
+FIELDS = ("r", "z", "vr", "vt", "vz", "ar", "az", "w")
+
+
+@pytest.fixture(scope="module")
+def pic():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1001_2969_gb300 import build
+    from paper_1001_2969_gb300 import pic as P
+
+    build()
+    return P
+
+
+def by_id(p):
+    o = np.argsort(p["id"], kind="stable")
+    return {k: np.asarray(v)[o] for k, v in p.items()}
+
+
+def nerr(a, b):
+    """max |a - b| normalised by max |b| (0 when both vanish)."""
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if a.size == 0:
+        return 0.0
+    s = np.abs(b).max()
+    return float(np.abs(a - b).max() / s) if s > 0 else float(np.abs(a).max())
+
+
+def cells_of(cfg, p):
+    dz = cfg["L"] / (cfg["nz"] - 1)
+    dr = cfg["R"] / (cfg["nr"] - 1)
+    i = np.clip(np.floor(p["z"] / dz).astype(np.int64), 0, cfg["nz"] - 2)
+    j = np.clip(np.floor(p["r"] / dr).astype(np.int64), 0, cfg["nr"] - 2)
+    return j * (cfg["nz"] - 1) + i
+
+
+def compare_particles(cfg, g, o, prec, max_outliers=0):
+    g, o = by_id(g), by_id(o)
+    if prec == "fp64":
+        assert np.array_equal(g["id"], o["id"])
+        for k in FIELDS:
+            e = nerr(g[k], o[k])
+            assert e <= TOL[prec], (k, e)
+        assert np.array_equal(g["cell"], cells_of(cfg, o))
+        return 0
+    common, gi, oi = np.intersect1d(g["id"], o["id"], return_indices=True)
+    nd = len(g["id"]) + len(o["id"]) - 2 * len(common)
+    bad = np.zeros(len(common), bool)
+    for k in FIELDS:
+        s = np.abs(o[k][oi]).max() if len(oi) else 1.0
+        bad |= np.abs(g[k][gi] - o[k][oi]) > TOL[prec] * max(s, 1e-300)
+    nbad = int(bad.sum()) + nd
+    assert nbad <= max_outliers, (nbad, nd)
+    return nbad
+
+
+def make_pair(pic, cfg, load=True, capacity=None):
+    o = Oracle(cfg, capacity=capacity)
+    if load:
+        o.load()
+    h = pic.pic_init(cfg, load=load)
+    return h, o
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_load_parity(pic, prec):
+    cfg = W.config("c1", precision=prec)
+    h, o = make_pair(pic, cfg)
+    for s in (0, 1):
+        g = pic.pic_get_particles(h, s)
+        ref = o.get_particles(s)
+        assert len(g["id"]) == len(ref["id"])
+        # the load's cell of particle p follows from integer arithmetic alone
+        n = cfg["species"][s]["n_init"]
+        ncell = (cfg["nz"] - 1) * (cfg["nr"] - 1)
+        base, rem = divmod(n, ncell)
+        p = np.arange(n)
+        c = np.where(p < rem * (base + 1), p // (base + 1), rem + (p - rem * (base + 1)) // max(base, 1))
+        gs = by_id(g)
+        assert np.array_equal(gs["cell"], c)
+        compare_particles(cfg, g, ref, prec if prec == "fp64" else "mixed")
+        if prec == "mixed":
+            for k in FIELDS:
+                assert nerr(gs[k], by_id(ref)[k]) < 2e-7, k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_deposit_parity_after_load(pic, prec):
+    cfg = W.config("c1", precision=prec)
+    h, o = make_pair(pic, cfg)
+    o.finalize()
+    f = pic.pic_get_fields(h)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert nerr(f["rho"], o.grid("rho")) < tol
+    assert nerr(f["chi"], o.grid("chi")) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("mesh", [(33, 65), (65, 257), (129, 513)])
+def test_field_solve_parity(pic, prec, mesh):
+    nz, nr = mesh
+    cfg = W.config("c1", nz=nz, nr=nr, precision=prec, mg_tol=1e-13 if prec == "fp64" else 1e-10,
+                   mg_max_cycles=100)
+    cfg = W.scaled(cfg, 0)
+    h = pic.pic_init(cfg, load=False)
+    o = Oracle(cfg)
+    chi = W.random_grid(cfg, seed=nz, scale=2.0)
+    rho = 1e-5 * (W.random_grid(cfg, seed=nr, smooth=False) - 0.5)
+    phi, cyc, res, st = pic.pic_field_solve(h, rho, chi, 80.0)
+    o.set_grid("chi", chi)
+    o.set_grid("rho", rho)
+    o.set_grid("phi", np.zeros((nz, nr)))
+    ost, ocyc, ores = o.solve(80.0)
+    assert st == 0 and ost == 0
+    assert nerr(phi, o.grid("phi")) < (1e-12 if prec == "fp64" else 1e-9)
+    if prec == "fp64":
+        assert abs(cyc - ocyc) <= 1
+
+
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_field_solve_fixed_cycles_fp64_iterates(pic, cycles):
+    """Same V-cycle, same number of cycles: the FP64 iterates agree to rounding."""
+    cfg = W.scaled(W.config("c1", nz=65, nr=129, mg_tol=0.0, mg_max_cycles=cycles), 0)
+    h = pic.pic_init(cfg, load=False)
+    o = Oracle(cfg)
+    chi = W.random_grid(cfg, seed=1, scale=1.0)
+    rho = 1e-5 * (W.random_grid(cfg, seed=2, smooth=False) - 0.5)
+    phi, cyc, res, st = pic.pic_field_solve(h, rho, chi, -40.0)
+    o.set_grid("chi", chi)
+    o.set_grid("rho", rho)
+    o.set_grid("phi", np.zeros((65, 129)))
+    o.solve(-40.0, tol=0.0, max_cycles=cycles)
+    assert cyc == cycles
+    assert nerr(phi, o.grid("phi")) < 1e-13
+
+
+def _state_cfg(prec, **kw):
+    cfg = W.config("c1", precision=prec, **kw)
+    return W.scaled(cfg, 0)
+
+
+def _random_state(cfg, n_e, n_i, seed, hot=3.0):
+    e = W.random_particles(cfg, 0, n_e, seed=seed, hot=hot, accel=2e14, wscale=1.5e6)
+    i = W.random_particles(cfg, 1, n_i, seed=seed + 1, hot=30.0, accel=5e9, wscale=1.5e6)
+    return e, i
+
+
+def _counters_match(gc, oc, prec):
+    idx = list(range(C_COLL, C_COLL + 8)) + [C_CAND, C_CAND + 1] + [C_BIRTHS, C_BIRTHS + 1] + \
+        [C_SPLITS, C_SPLITS + 1] + list(range(C_ABS, C_ABS + 6))
+    for k in idx:
+        if prec == "fp64":
+            assert gc[k] == oc[k], (k, gc[k], oc[k])
+        else:
+            assert abs(int(gc[k]) - int(oc[k])) <= max(3, 1e-4 * oc[k]), (k, gc[k], oc[k])
+
+
+def _one_step(pic, cfg, e, i, step_index, prec, max_outliers=0):
+    h = pic.pic_init(cfg, load=False)
+    o = Oracle(cfg)
+    pic.pic_set_particles(h, 0, e)
+    pic.pic_set_particles(h, 1, i)
+    o.set_particles(0, e)
+    o.set_particles(1, i)
+    pic.pic_set_step(h, step_index)
+    o.set_step(step_index)
+    st = pic.pic_step(h, 1)
+    o.step(1)
+    assert st == 0
+    f = pic.pic_get_fields(h)
+    o.finalize()
+    tol = TOL[prec]
+    for name in ("phi", "Ez", "Er"):
+        assert nerr(f[name], o.grid(name)) < (tol if prec == "fp64" else 1e-6), name
+    for name in ("rho", "chi"):
+        assert nerr(f[name], o.grid(name)) < (tol if prec == "fp64" else 5e-5), name
+    nb = 0
+    for s in (0, 1):
+        g = pic.pic_get_particles(h, s)
+        ref = o.get_particles(s)
+        nb += compare_particles(cfg, g, ref, prec, max_outliers)
+    m = pic.pic_moments(h)
+    oc, oq = o.counters()
+    _counters_match(m["counters"], oc, prec)
+    assert nerr(m["charge"], oq) < (1e-12 if prec == "fp64" else 1e-4)
+    cnt = pic.pic_get_counts(h)
+    if prec == "fp64":
+        assert list(cnt["next_id"]) == [o.next_id(0), o.next_id(1)]
+    return h, o, oc
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_one_step_parity_with_collisions_and_births(pic, prec):
+    cfg = _state_cfg(prec)
+    e, i = _random_state(cfg, 60_001, 40_003, seed=5)
+    h, o, oc = _one_step(pic, cfg, e, i, 17, prec, max_outliers=40)
+    assert oc[C_COLL + 2] > 50  # ionisations happened
+    assert oc[C_COLL + 4] > 0  # charge exchange happened
+    assert oc[C_ABS:C_ABS + 6].sum() > 0  # walls absorbed
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_one_step_parity_with_splitting(pic, prec):
+    cfg = _state_cfg(prec, split_every=1)
+    e, i = _random_state(cfg, 20_000, 20_000, seed=9, hot=1.0)
+    o = Oracle(cfg)
+    dr = cfg["R"] / (cfg["nr"] - 1)
+    rng = np.random.default_rng(3)
+    for p, s in ((e, 0), (i, 1)):
+        j = np.minimum(np.floor(p["r"] / dr).astype(int), cfg["nr"] - 2)
+        wr = np.array([o.w_ref(s, int(k)) for k in j])
+        p["w"] = wr * rng.uniform(0.3, 12.0, len(j))
+    h, o2, oc = _one_step(pic, cfg, e, i, 0, prec, max_outliers=60)
+    assert oc[C_SPLITS] > 1000 and oc[C_SPLITS + 1] > 1000
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tiny_and_empty_inputs(pic, prec):
+    cfg = W.config("tiny", precision=prec)
+    rng = np.random.default_rng(0)
+    e = W.random_particles(cfg, 0, 7, seed=1, hot=4.0)
+    i = W.random_particles(cfg, 1, 0, seed=2)
+    _one_step(pic, cfg, e, i, 3, prec, max_outliers=2)
+    # both species empty: the field is the vacuum (Laplace) solution
+    cfg2 = W.config("tiny", precision=prec)
+    h = pic.pic_init(W.scaled(cfg2, 0), load=False)
+    assert pic.pic_step(h, 2) == 0
+    assert list(pic.pic_get_counts(h)["n_alive"]) == [0, 0]
+
+
+def test_multi_step_parity_fp64(pic):
+    cfg = W.scaled(W.config("c1", precision="fp64"), 20_000)
+    h, o = make_pair(pic, cfg)
+    K = 5
+    pic.pic_step(h, K)
+    o.step(K)
+    f = pic.pic_get_fields(h)
+    for name in ("phi", "Ez", "Er"):
+        assert nerr(f[name], o.grid(name)) < 1e-11, name
+    for s in (0, 1):
+        g = by_id(pic.pic_get_particles(h, s))
+        ref = by_id(o.get_particles(s))
+        assert np.array_equal(g["id"], ref["id"])
+        for k in FIELDS:
+            assert nerr(g[k], ref[k]) < 1e-10, k
+    m = pic.pic_moments(h)
+    oc, _ = o.counters()
+    _counters_match(m["counters"], oc, "fp64")
+    om = o.moments()
+    for k in ("ne", "ni", "phi", "Ez", "Er"):
+        assert nerr(m[k], om[k]) < 1e-10, k
+    assert nerr(m["eedf"], om["eedf"]) < 1e-9
+
+
+def test_births_capacity_error_keeps_the_state(pic):
+    cfg = _state_cfg("fp64", births_capacity=16)
+    e, i = _random_state(cfg, 30_000, 1000, seed=21, hot=4.0)
+    h = pic.pic_init(cfg, load=False)
+    pic.pic_set_particles(h, 0, e)
+    pic.pic_set_particles(h, 1, i)
+    before = by_id(pic.pic_get_particles(h, 0))
+    with pytest.raises(pic.PicError) as err:
+        pic.pic_step(h, 1)
+    assert err.value.status == pic.PIC_ERR_CAPACITY
+    after = by_id(pic.pic_get_particles(h, 0))
+    for k in FIELDS + ("id",):
+        assert np.array_equal(before[k], after[k])
