@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
         for (int m = 0; m < kPPT; ++m) {
             const int k = base + m * kThreads + tid;
             int out_cell = -1;
+            T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
             if (k < end) {
                 const int pidx = a.perm[k];
                 const bool from_main = pidx < nmain;
@@ -540,33 +541,56 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
                 }
                 if (alive) {
                     out_cell = p.j * a.ncz + p.i;
-                    // deposit at the new x~ (Sec. 2.4)
+                    // deposit weights at the new x~ (Sec. 2.4)
                     T r0, r1;
                     shape_r(a.weighting, p.j, p.orr, r0, r1);
                     const T y0 = (T)1 - p.oz, y1 = p.oz;
-                    const T c00 = p.w * y0 * r0, c01 = p.w * y0 * r1;
-                    const T c10 = p.w * y1 * r0, c11 = p.w * y1 * r1;
-                    const int li = p.i - wi0, lj = p.j - wj0;
-                    if (li >= 0 && li + 1 < wz && lj >= 0 && lj + 1 < wr) {
-                        T *wp = win + li * wr + lj;
-                        atomicAdd(wp, c00);
-                        atomicAdd(wp + 1, c01);
-                        atomicAdd(wp + wr, c10);
-                        atomicAdd(wp + wr + 1, c11);
-                    } else {
-                        double *g = a.N[a.s] + (size_t)p.i * a.nr + p.j;
-                        atomicAdd(g, (double)c00);
-                        atomicAdd(g + 1, (double)c01);
-                        atomicAdd(g + a.nr, (double)c10);
-                        atomicAdd(g + a.nr + 1, (double)c11);
-                    }
+                    c00 = p.w * y0 * r0;
+                    c01 = p.w * y0 * r1;
+                    c10 = p.w * y1 * r0;
+                    c11 = p.w * y1 * r1;
                 }
                 store_p(a.dst_main, k, p, out_cell, id);
             }
-            // cell histogram of the survivors, one atomic per distinct cell per warp
-            const unsigned peers = __match_any_sync(0xffffffffu, out_cell);
-            if (out_cell >= 0 && lane == __ffs(peers) - 1)
-                atomicAdd(a.counts[a.s] + out_cell, __popc(peers));
+            // Lanes hold consecutive particles of the cell-sorted input, so runs
+            // of lanes share an output cell: sum each run into its first lane,
+            // which then makes the four deposit atomics and the histogram count.
+            const int cprev = __shfl_up_sync(0xffffffffu, out_cell, 1);
+            const bool head = lane == 0 || cprev != out_cell;
+            const unsigned heads = __ballot_sync(0xffffffffu, head);
+            const unsigned above = heads & ~((2u << lane) - 1u);
+            const int rend = above ? __ffs(above) - 1 : 32;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const T t00 = __shfl_down_sync(0xffffffffu, c00, d);
+                const T t01 = __shfl_down_sync(0xffffffffu, c01, d);
+                const T t10 = __shfl_down_sync(0xffffffffu, c10, d);
+                const T t11 = __shfl_down_sync(0xffffffffu, c11, d);
+                if (lane + d < rend) {
+                    c00 += t00;
+                    c01 += t01;
+                    c10 += t10;
+                    c11 += t11;
+                }
+            }
+            if (head && out_cell >= 0) {
+                atomicAdd(a.counts[a.s] + out_cell, rend - lane);
+                const int ci = out_cell % a.ncz, cj = out_cell / a.ncz;
+                const int li = ci - wi0, lj = cj - wj0;
+                if (li >= 0 && li + 1 < wz && lj >= 0 && lj + 1 < wr) {
+                    T *wp = win + li * wr + lj;
+                    atomicAdd(wp, c00);
+                    atomicAdd(wp + 1, c01);
+                    atomicAdd(wp + wr, c10);
+                    atomicAdd(wp + wr + 1, c11);
+                } else {
+                    double *g = a.N[a.s] + (size_t)ci * a.nr + cj;
+                    atomicAdd(g, (double)c00);
+                    atomicAdd(g + 1, (double)c01);
+                    atomicAdd(g + a.nr, (double)c10);
+                    atomicAdd(g + a.nr + 1, (double)c11);
+                }
+            }
         }
         __syncthreads();
         for (int k = tid; k < wz * wr; k += blockDim.x) {

@@ -152,9 +152,13 @@ def test_field_solve_fixed_cycles_fp64_iterates(pic, cycles):
     assert nerr(phi, o.grid("phi")) < 1e-13
 
 
-def _state_cfg(prec, **kw):
+def _state_cfg(prec, capacity=400_000, **kw):
+    """c1 geometry, no load (n_init 0: one reference particle per cell), room for `capacity`."""
     cfg = W.config("c1", precision=prec, **kw)
-    return W.scaled(cfg, 0)
+    for sp in cfg["species"]:
+        sp["n_init"] = 0
+        sp["capacity"] = capacity
+    return cfg
 
 
 def _random_state(cfg, n_e, n_i, seed, hot=3.0):
