@@ -349,7 +349,10 @@ int mg_solve(const FieldDims &fd, MGWork &mg, const double *rho, const double *c
             status = tol > 0.0 ? 1 : 0;
             break;
         }
-        if (!mixed) {
+        if (nlev == 1) {
+            // nz = 3: the single interior row is the whole problem; solve it exactly
+            line_rows<double, double, double>(mg.lv[0].cz, mg.lv[0].cr, mg.f0, phi, nz, nr, 1, st, &L);
+        } else if (!mixed) {
             // restrict the residual down; coarse levels start from zero
             for (int l = 1; l < nlev; ++l) {
                 const MGLevel &c = mg.lv[l];

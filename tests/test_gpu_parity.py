@@ -135,6 +135,25 @@ def test_field_solve_parity(pic, prec, mesh):
         assert abs(cyc - ocyc) <= 1
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_field_solve_single_interior_row(pic, prec):
+    """nz = 3: one level, one interior row; the solve is one exact line solve.  (The
+    r couplings of this row are ~160x its z couplings, so rounding leaves a relative
+    residual near 1e-13: the tolerance sits above that floor.)"""
+    cfg = W.scaled(W.config("c1", nz=3, nr=65, precision=prec, mg_tol=1e-11), 0)
+    h = pic.pic_init(cfg, load=False)
+    o = Oracle(cfg)
+    chi = W.random_grid(cfg, seed=4, scale=1.5)
+    rho = 1e-5 * (W.random_grid(cfg, seed=5, smooth=False) - 0.5)
+    phi, cyc, res, st = pic.pic_field_solve(h, rho, chi, 25.0)
+    o.set_grid("chi", chi)
+    o.set_grid("rho", rho)
+    o.set_grid("phi", np.zeros((3, 65)))
+    ost, ocyc, _ = o.solve(25.0)
+    assert st == 0 and ost == 0 and cyc == ocyc == 1
+    assert nerr(phi, o.grid("phi")) < 1e-12
+
+
 @pytest.mark.parametrize("cycles", [1, 3])
 def test_field_solve_fixed_cycles_fp64_iterates(pic, cycles):
     """Same V-cycle, same number of cycles: the FP64 iterates agree to rounding."""
