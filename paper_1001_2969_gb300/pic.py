@@ -86,7 +86,7 @@ class pic_moments_out(C.Structure):
 SYMBOLS = ("pic_init", "pic_step", "pic_field_solve", "pic_moments", "pic_get_particles",
            "pic_set_particles", "pic_set_step", "pic_set_boundary", "pic_get_fields",
            "pic_get_counts", "pic_save", "pic_load", "pic_profile", "pic_timings", "pic_destroy",
-           "pic_last_error", "pic_status_string")
+           "pic_last_error", "pic_status_string", "pic_field_solve_noalloc")
 
 
 class PicError(RuntimeError):
@@ -125,6 +125,9 @@ def lib():
         L.pic_destroy.restype = None
         L.pic_last_error.argtypes = [vp]
         L.pic_last_error.restype = C.c_char_p
+        L.pic_field_solve_noalloc.argtypes = [C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                              C.c_int32, vp, vp, C.c_double, vp, vp, C.c_double,
+                                              C.c_int32, vp, C.POINTER(pic_solve_info)]
         L.pic_status_string.argtypes = [C.c_int]
         L.pic_status_string.restype = C.c_char_p
         for name in SYMBOLS:
@@ -262,6 +265,19 @@ def pic_field_solve_device(h: Handle, rho_ptr: int, chi_ptr: int, V: float, phi_
     st = lib().pic_field_solve(h.ptr, rho_ptr, chi_ptr, float(V), phi_ptr, 1, C.byref(info))
     _check(h, st)
     return info.cycles, info.rel_residual, st
+
+
+def pic_field_solve_noalloc(R: float, L: float, nz: int, nr: int, chi_face: int, rho_ptr: int,
+                            chi_ptr: int, V: float, phi_zL_ptr, phi_ptr: int, tol: float,
+                            max_cycles: int, stream=None):
+    """Handle-free FP64 solve on device arrays that allocates no device memory (for
+    callers that cannot allocate, e.g. during stream capture).  Returns
+    (status, cycles, rel_residual); never raises, so callers can test the status."""
+    info = pic_solve_info()
+    st = lib().pic_field_solve_noalloc(float(R), float(L), int(nz), int(nr), int(chi_face),
+                                       rho_ptr, chi_ptr, float(V), phi_zL_ptr, phi_ptr,
+                                       float(tol), int(max_cycles), stream, C.byref(info))
+    return st, info.cycles, info.rel_residual
 
 
 def pic_moments(h: Handle, reset: bool = False) -> dict:
