@@ -124,6 +124,8 @@ def run_gpu(args, rank, world):
     for prec in (args.precision, "fp64") if args.fp64_steps > 0 else (args.precision,):
         steps = args.steps if prec == args.precision else args.fp64_steps
         cfg = W.config(args.config, precision=prec, seed=1 + rank)
+        if args.particles:
+            cfg = W.scaled(cfg, args.particles)
         h = pic.pic_init(cfg, stream=stream.cuda_stream)
         pic.pic_step(h, args.warmup)
         n0 = pic.pic_get_counts(h)["n_alive"].sum()
@@ -214,6 +216,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="particles per species (default: the workload's; smaller for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

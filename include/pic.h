@@ -58,7 +58,8 @@ enum { PIC_XS_ELASTIC = 0, PIC_XS_EXCITE = 1, PIC_XS_IONIZE = 2, PIC_XS_CX = 3 }
 #define PIC_NCOUNT 24
 
 /* Mesh: uniform node-centred r-z mesh, z in [0, L], r in [0, R] (Sec. 2.4,
- * Sec. 3.2).  nz must be 2^k + 1 (z-semi-coarsening, Sec. 2.5), nr >= 3. */
+ * Sec. 3.2).  nz must be 2^k + 1 (z-semi-coarsening, Sec. 2.5); 3 <= nr <= 1025
+ * (one r-line unknown per thread of a line solve). */
 typedef struct pic_mesh {
     double R, L;
     int32_t nz, nr;

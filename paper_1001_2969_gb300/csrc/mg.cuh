@@ -1,0 +1,61 @@
+// mg.cuh -- workspace and control block of the multigrid solve in mg.cu.
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// device-side control of one solve: the residual kernel's last block fills
+// it and raises `done`; the other kernels of a cycle return early once done
+struct MGCtl {
+    unsigned long long res_bits;  // max |r| of the current cycle (bits of a positive double)
+    unsigned long long b_bits;    // max |b| (first cycle)
+    unsigned long long rb[2];     // per-cycle max |r| of the one-launch solve (alternating)
+    unsigned int blocks_in;
+    int done, converged, zero_rhs, cycles, max_cycles, timeout;
+    double tol, last_res, bnorm;
+    // two-level grid barrier of the one-launch solve: a counter per group of
+    // blocks, a top counter over the groups and the generation that waiting
+    // blocks poll, each on its own cache line
+    struct alignas(128) Line {
+        unsigned int v;
+        unsigned int pad[31];
+    };
+    Line bar_group[32];
+    Line bar_top;
+    Line bar_gen;
+};
+
+// returned by mg_fast_solve when a bounded device wait gave up
+constexpr int kSolveTimeout = -1000000;
+
+constexpr int kMaxLevels = 16;
+
+struct MGFast;
+struct MGFast {
+    int nlev;
+    int nz[kMaxLevels];
+    double dz[kMaxLevels];
+    double *chi[kMaxLevels], *cz[kMaxLevels], *cr[kMaxLevels];
+    float *cz32[kMaxLevels], *cr32[kMaxLevels];
+    double *u64[kMaxLevels], *f64[kMaxLevels];  // FP64 V-cycle, levels >= 1
+    float *u32[kMaxLevels], *f32[kMaxLevels];   // FP32 V-cycle (mixed), levels >= 0
+    double *fac64[kMaxLevels];                  // line factors, FP64 path
+    float *fac32[kMaxLevels];                   // line factors, FP32 V-cycle
+    double *facc;                               // coarsest level's line factors (FP64)
+    double *fc64;                               // coarsest level's right-hand side (FP64)
+    double *f0;                                 // fine right-hand side
+    double *r;                                  // fine residual (FP64)
+    MGCtl *ctl;
+    MGFast *self;  // device copy of this struct (kernels read it through a pointer)
+};
+
+// elements of FP64 (returned) and FP32 (*n32) line-factor storage of a mesh
+size_t mg_fast_factor_elems(int nz, int nr, bool mixed, size_t *n32);
+
+// solve into phi; returns the cycles (>= 0, converged) or -cycles-1
+int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
+                  const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
+                  int max_cycles, double *rel_res, int *launches, cudaStream_t st);
+
+}  // namespace pic

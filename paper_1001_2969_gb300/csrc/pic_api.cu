@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "mg.cuh"
 #include "pic_internal.cuh"
 
 using namespace pic;
@@ -77,7 +78,7 @@ struct pic_handle {
     double *m_acc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     double *eedf = nullptr;
     double *tmp_grid[3] = {nullptr, nullptr, nullptr};
-    MGWork mg;
+    MGFast mgf;
     RadixTmp rtmp;
     int64_t step = 0;
     int64_t nsamples = 0;
@@ -172,7 +173,7 @@ pic_status validate(const pic_config *c, std::string &why) {
     };
     if (!(c->mesh.R > 0) || !(c->mesh.L > 0)) return bad("mesh R and L must be positive");
     if (c->mesh.nz < 3 || !pow2(c->mesh.nz - 1)) return bad("nz must be 2^k + 1 >= 3");
-    if (c->mesh.nr < 3 || c->mesh.nr > 2049) return bad("nr must be in [3, 2049]");
+    if (c->mesh.nr < 3 || c->mesh.nr > 1025) return bad("nr must be in [3, 1025]");
     if ((int64_t)(c->mesh.nz - 1) * (c->mesh.nr - 1) >= (1LL << 30)) return bad("mesh too large");
     if (!(c->dt > 0)) return bad("dt must be positive");
     if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return bad("precision");
@@ -379,28 +380,46 @@ void setup_device(pic_handle *h) {
     std::vector<double> V;
     node_volumes(h, V);
     cudaMemcpyAsync(h->V, V.data(), gb, cudaMemcpyHostToDevice, h->st);
-    // multigrid hierarchy
+    // multigrid hierarchy: per level nodal chi and face coefficients, the
+    // V-cycle's correction and right-hand side, and the r-line factors
+    MGFast &m = h->mgf;
+    memset(&m, 0, sizeof(m));
+    const int nline = h->nr - 1;
+    int K = 0;
+    for (int s = 1; s < nline; s <<= 1) ++K;
     int nl = 0;
-    for (int n = h->nz;; n = (n + 1) / 2) {
-        MGLevel &lv = h->mg.lv[nl++];
-        lv.nz = n;
-        lv.dz = h->cfg.mesh.L / (n - 1);
-        const size_t g = (size_t)n * h->nr;
-        lv.chi = (double *)dalloc(h, g * sizeof(double));
-        lv.cz = (double *)dalloc(h, g * sizeof(double));
-        lv.cr = (double *)dalloc(h, g * sizeof(double));
-        lv.u = (double *)dalloc(h, g * sizeof(double));
-        lv.f = (double *)dalloc(h, g * sizeof(double));
-        lv.cz32 = (float *)dalloc(h, g * sizeof(float));
-        lv.cr32 = (float *)dalloc(h, g * sizeof(float));
-        lv.u32 = (float *)dalloc(h, g * sizeof(float));
-        lv.f32 = (float *)dalloc(h, g * sizeof(float));
-        if (n == 3) break;
+    for (int z = h->nz;; z = (z + 1) / 2) {
+        const int l = nl++;
+        m.nz[l] = z;
+        m.dz[l] = h->cfg.mesh.L / (z - 1);
+        const size_t g = (size_t)z * h->nr;
+        m.chi[l] = (double *)dalloc(h, g * sizeof(double));
+        m.cz[l] = (double *)dalloc(h, g * sizeof(double));
+        m.cr[l] = (double *)dalloc(h, g * sizeof(double));
+        if (h->mixed) {
+            m.cz32[l] = (float *)dalloc(h, g * sizeof(float));
+            m.cr32[l] = (float *)dalloc(h, g * sizeof(float));
+            m.u32[l] = (float *)dalloc(h, g * sizeof(float));
+            m.f32[l] = (float *)dalloc(h, g * sizeof(float));
+        } else if (l > 0) {
+            m.u64[l] = (double *)dalloc(h, g * sizeof(double));
+            m.f64[l] = (double *)dalloc(h, g * sizeof(double));
+        }
+        const size_t fe = (size_t)(z - 2) * (2 * K + 1) * nline;
+        if (z == 3)
+            m.facc = (double *)dalloc(h, fe * sizeof(double));
+        else if (!h->mixed)
+            m.fac64[l] = (double *)dalloc(h, fe * sizeof(double));
+        else
+            m.fac32[l] = (float *)dalloc(h, fe * sizeof(float));
+        if (z == 3) break;
     }
-    h->mg.nlev = nl;
-    h->mg.r = (double *)dalloc(h, gb);
-    h->mg.f0 = (double *)dalloc(h, gb);
-    h->mg.ds = h->ds;
+    m.nlev = nl;
+    m.fc64 = (double *)dalloc(h, (size_t)3 * h->nr * sizeof(double));
+    m.f0 = (double *)dalloc(h, gb);
+    m.r = (double *)dalloc(h, gb);
+    m.ctl = (MGCtl *)dalloc(h, sizeof(MGCtl));
+    m.self = (MGFast *)dalloc(h, sizeof(MGFast));
     // births radix scratch
     int64_t bmax = std::max(h->sp[0].bcap, h->sp[1].bcap);
     h->rtmp.max_n = (int)bmax;
@@ -539,9 +558,13 @@ pic_status one_step(pic_handle *h) {
         FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
         int L = 0;
         double res = 0.0;
-        const int r = mg_solve(fd, h->mg, h->rho, h->chi, Vt, h->has_phiL ? h->phiL_d : nullptr,
-                               h->phi, true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, &res,
-                               &L, st);
+        const int r = mg_fast_solve(fd, h->mgf, h->rho, h->chi, Vt,
+                                    h->has_phiL ? h->phiL_d : nullptr, h->phi, true, h->mixed,
+                                    h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, st);
+        if (r == kSolveTimeout) {
+            h->launches += L;
+            return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
+        }
         h->last_cycles = r >= 0 ? r : -r - 1;
         h->last_res = res;
         h->mg_cycles_total += h->last_cycles;
@@ -826,10 +849,11 @@ pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, 
     FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
     int L = 0;
     double res = 0.0;
-    const int r = mg_solve(fd, h->mg, h->tmp_grid[0], h->tmp_grid[1], V,
-                           h->has_phiL ? h->phiL_d : nullptr, h->tmp_grid[2], false, h->mixed,
-                           h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, h->st);
+    const int r = mg_fast_solve(fd, h->mgf, h->tmp_grid[0], h->tmp_grid[1], V,
+                                h->has_phiL ? h->phiL_d : nullptr, h->tmp_grid[2], false,
+                                h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, h->st);
     h->launches += L;
+    if (r == kSolveTimeout) return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
     cudaMemcpyAsync(phi, h->tmp_grid[2], gb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st);
     cudaStreamSynchronize(h->st);
     if (info) {
