@@ -56,6 +56,9 @@ __device__ __forceinline__ double m_abs(double x) { return fabs(x); }
 __device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
+// x^R for x >= 1, R in (0, 1): FP32 through the hardware base-2 log/exp
+__device__ __forceinline__ float m_powR(float x, float R) { return exp2f(R * __log2f(x)); }
+__device__ __forceinline__ double m_powR(double x, double R) { return pow(x, R); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
 __device__ __forceinline__ float m_tan(float x) { return tanf(x); }
 __device__ __forceinline__ double m_tan(double x) { return tan(x); }
@@ -65,6 +68,13 @@ __device__ __forceinline__ void m_sincos2pi(float u, float *s, float *c) { sinco
 __device__ __forceinline__ void m_sincos2pi(double u, double *s, double *c) { sincospi(2.0 * u, s, c); }
 __device__ __forceinline__ bool m_finite(float x) { return isfinite(x); }
 __device__ __forceinline__ bool m_finite(double x) { return isfinite(x); }
+// a / b: IEEE in FP64; in FP32 the approximate division (2 ulp), used only
+// where the result feeds positions/weights (never a threshold test on its own)
+__device__ __forceinline__ float m_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double m_rsqrt(double x) { return 1.0 / sqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ T below_one();
 template <>
@@ -104,6 +114,32 @@ struct PS {
     T oz, orr, vr, vt, vz, ar, az, w;
 };
 
+// c = j ncz + i -> (i, j) without an integer division: (c + 1/2)/ncz lies
+// strictly inside (j, j+1), far from its ends compared with FP32 rounding
+// for c < 2^24; one correction step covers the rest
+__device__ __forceinline__ void decode_cell(int c, int ncz, float inv_ncz, int &i, int &j) {
+    int jj = __float2int_rz(((float)c + 0.5f) * inv_ncz);
+    int ii = c - jj * ncz;
+    if (ii < 0) {
+        jj -= 1;
+        ii += ncz;
+    } else if (ii >= ncz) {
+        jj += 1;
+        ii -= ncz;
+    }
+    i = ii;
+    j = jj;
+}
+
+template <typename T>
+__device__ __forceinline__ PS<T> load_p_fast(const PBuf<T> &b, int idx, int ncz, float inv_ncz) {
+    PS<T> p;
+    ld4(b.q0 + idx, p.oz, p.orr, p.vr, p.vt);
+    ld4(b.q1 + idx, p.vz, p.ar, p.az, p.w);
+    decode_cell(b.cell[idx], ncz, inv_ncz, p.i, p.j);
+    return p;
+}
+
 template <typename T>
 __device__ __forceinline__ PS<T> load_p(const PBuf<T> &b, int idx, int ncz) {
     PS<T> p;
@@ -133,8 +169,8 @@ __device__ __forceinline__ void shape_r(int weighting, int j, T o, T &s0, T &s1)
         s0 = (T)1 - o;
     } else {
         const T t = (T)(2 * j + 1);
-        s1 = o * ((T)(2 * j) + o) / t;
-        s0 = ((T)1 - o) * (t + o) / t;
+        s1 = m_div(o * ((T)(2 * j) + o), t);
+        s0 = m_div(((T)1 - o) * (t + o), t);
     }
 }
 
@@ -168,15 +204,23 @@ __device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p) {
     const T r = ((T)p.j + p.orr) * a.dr;
     const T dx = vx * a.dt, dy = vy * a.dt;
     const T xr = r + dx;
-    const T rn = m_sqrt(xr * xr + dy * dy);
-    T c = (T)1, sn = (T)0;
-    if (rn > (T)0) {
-        c = xr / rn;
-        sn = dy / rn;
+    const T q2 = xr * xr + dy * dy;
+    T c = (T)1, sn = (T)0, rn = (T)0;
+    if (q2 > (T)0) {
+        if (sizeof(T) == 4) {
+            const T inv = m_rsqrt(q2);
+            rn = q2 * inv;
+            c = xr * inv;
+            sn = dy * inv;
+        } else {
+            rn = m_sqrt(q2);
+            c = xr / rn;
+            sn = dy / rn;
+        }
     }
     const T den = rn + r;
-    const T drr = den > (T)0 ? ((T)2 * r * dx + dx * dx + dy * dy) / den : (T)0;
-    T ro = p.orr + drr / a.dr;
+    const T drr = den > (T)0 ? m_div((T)2 * r * dx + dx * dx + dy * dy, den) : (T)0;
+    T ro = p.orr + drr * a.inv_dr;
     const T fl = m_floor(ro);
     int jn = p.j + (int)fl;
     ro -= fl;
@@ -190,6 +234,32 @@ __device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p) {
     p.vt = -vx * sn + vy * c;
     p.vz = vz;
     p.ar = p.ar * c;
+}
+
+// all channels' sigma(E) at once from the interleaved table sig4[k] = {s0..s3}
+template <typename T>
+__device__ __forceinline__ void sigma_all(const Xs<T> &xs, T E, T s[4]) {
+    T a0, a1, a2, a3;
+    if (E >= xs.emax) {
+        ld4(xs.sig4 + (xs.n_e - 1), a0, a1, a2, a3);
+        const T f = m_div(xs.emax, E);
+        s[0] = a0 * f;
+        s[1] = a1 * f;
+        s[2] = a2 * f;
+        s[3] = a3 * f;
+        return;
+    }
+    const T x = E * xs.inv_dE;
+    int k = x >= (T)0 ? (int)m_floor(x) : 0;  // also keeps a NaN off the table
+    if (k > xs.n_e - 2) k = xs.n_e - 2;
+    const T f = x - (T)k;
+    T b0, b1, b2, b3;
+    ld4(xs.sig4 + k, a0, a1, a2, a3);
+    ld4(xs.sig4 + k + 1, b0, b1, b2, b3);
+    s[0] = a0 + f * (b0 - a0);
+    s[1] = a1 + f * (b1 - a1);
+    s[2] = a2 + f * (b2 - a2);
+    s[3] = a3 + f * (b3 - a3);
 }
 
 template <typename T>
@@ -211,7 +281,7 @@ __device__ __forceinline__ T cos_chi(int scatter, T eps, T R) {
     if (scatter == PIC_SCATTER_ISOTROPIC || eps < (T)1e-6)
         c = (T)1 - (T)2 * R;
     else
-        c = ((T)2 + eps - (T)2 * m_pow((T)1 + eps, R)) / eps;
+        c = m_div((T)2 + eps - (T)2 * m_powR((T)1 + eps, R), eps);
     return c > (T)1 ? (T)1 : (c < (T)-1 ? (T)-1 : c);
 }
 
@@ -314,10 +384,12 @@ __device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, ui
     const T g = m_sqrt(gx * gx + gy * gy + gz * gz);
     const T E = a.half_m_e * g * g;
     T nu[kMaxCh];
+    sigma_all(a.xs, E, nu);
     T tot = 0;
+    const T ngg = a.ng * g;
 #pragma unroll
     for (int ch = 0; ch < kMaxCh; ++ch) {
-        nu[ch] = ch < a.xs.n_ch ? a.ng * sigma_of(a.xs, ch, E) * g : (T)0;
+        nu[ch] = ch < a.xs.n_ch ? ngg * nu[ch] : (T)0;
         tot += nu[ch];
     }
     if (tot > a.nu_max) atomicAdd(&bt->cnt[PIC_C_NUOVER + a.s], 1ull);
@@ -407,14 +479,14 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *win = reinterpret_cast<T *>(smem_raw);
-    double *s_eedf = reinterpret_cast<double *>(smem_raw + kWinBytes);
+    T *s_eedf = reinterpret_cast<T *>(smem_raw + kWinBytes);
     __shared__ BlockTally bt;
     __shared__ int s_w[4];
     const int tid = threadIdx.x, lane = tid & 31;
     for (int k = tid; k < PIC_NCOUNT; k += blockDim.x) bt.cnt[k] = 0;
     if (tid < 3) bt.q[tid] = 0.0;
     if (a.eedf)
-        for (int k = tid; k < a.eedf_bins; k += blockDim.x) s_eedf[k] = 0.0;
+        for (int k = tid; k < a.eedf_bins; k += blockDim.x) s_eedf[k] = (T)0;
     const int WCAP = kWinBytes / (int)sizeof(T);
     const int n = *a.n_alive;
     const int nmain = *a.n_main_src;
@@ -427,11 +499,13 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
             const int pa = a.perm[base], pb = a.perm[end - 1];
             const int ca = pa < nmain ? a.src_main.cell[pa] : a.src_births.cell[pa - nmain];
             const int cb = pb < nmain ? a.src_main.cell[pb] : a.src_births.cell[pb - nmain];
-            const int ja = ca / a.ncz, jb = cb / a.ncz;
+            int ia, ja, ib, jb;
+            decode_cell(ca, a.ncz, a.inv_ncz, ia, ja);
+            decode_cell(cb, a.ncz, a.inv_ncz, ib, jb);
             int ilo = 0, ihi = a.ncz - 1;
             if (ja == jb) {
-                ilo = ca % a.ncz;
-                ihi = cb % a.ncz;
+                ilo = ia;
+                ihi = ib;
             }
             const int wi0 = max(ilo - kHalo, 0), wi1 = min(ihi + 1 + kHalo, a.nz - 1);
             const int wj0 = max(ja - kHalo, 0), wj1 = min(jb + 1 + kHalo, a.nr - 1);
@@ -456,7 +530,7 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
                 const bool from_main = pidx < nmain;
                 const PBuf<T> &src = from_main ? a.src_main : a.src_births;
                 const int si = from_main ? pidx : pidx - nmain;
-                PS<T> p = load_p(src, si, a.ncz);
+                PS<T> p = load_p_fast(src, si, a.ncz, a.inv_ncz);
                 const uint64_t id = src.id[si];
                 // gather E at x~ with the deposit's shape factors (Sec. 2.4)
                 T s0, s1;
@@ -509,7 +583,7 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
                         const T Ek = a.half_m_e * (p.vr * p.vr + p.vt * p.vt + p.vz * p.vz);
                         const T x = Ek * a.eedf_scale;
                         if (x >= (T)0 && x < (T)a.eedf_bins)
-                            atomicAdd(&s_eedf[(int)x], (double)p.w);
+                            atomicAdd(&s_eedf[(int)x], p.w);
                     }
                     if (a.do_split) {  // weight-conserving split (Sec. 2.2)
                         const T wr_ = a.w_ref[p.j];
@@ -575,7 +649,8 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
             }
             if (head && out_cell >= 0) {
                 atomicAdd(a.counts[a.s] + out_cell, rend - lane);
-                const int ci = out_cell % a.ncz, cj = out_cell / a.ncz;
+                int ci, cj;
+                decode_cell(out_cell, a.ncz, a.inv_ncz, ci, cj);
                 const int li = ci - wi0, lj = cj - wj0;
                 if (li >= 0 && li + 1 < wz && lj >= 0 && lj + 1 < wr) {
                     T *wp = win + li * wr + lj;
@@ -607,12 +682,12 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
     if (tid < 3 && bt.q[tid] != 0.0) atomicAdd(&a.ds->qabs[tid], bt.q[tid]);
     if (a.eedf)
         for (int k = tid; k < a.eedf_bins; k += blockDim.x)
-            if (s_eedf[k] != 0.0) atomicAdd(a.eedf + k, s_eedf[k]);
+            if (s_eedf[k] != (T)0) atomicAdd(a.eedf + k, (double)s_eedf[k]);
 }
 
 template <typename T>
 void launch_step(const StepArgs<T> &a, int grid, cudaStream_t st) {
-    const size_t smem = kWinBytes + (size_t)(a.eedf ? a.eedf_bins : 0) * sizeof(double);
+    const size_t smem = kWinBytes + (size_t)(a.eedf ? a.eedf_bins : 0) * sizeof(T);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_step<T><<<grid, kThreads, smem, st>>>(a);

@@ -44,6 +44,7 @@ struct SpecDev {
     int32_t *d_nmain[2] = {nullptr, nullptr}, *d_nbirths[2] = {nullptr, nullptr};
     int32_t *d_nalive = nullptr, *d_ntotal = nullptr;
     void *sigma = nullptr;  // T[n_ch][n_e]
+    void *sig4 = nullptr;   // T[n_e][4], channels interleaved
     void *w_ref = nullptr;  // T[ncr]
     int64_t cap = 0, bcap = 0;
     uint64_t next_id = 0;
@@ -174,7 +175,7 @@ pic_status validate(const pic_config *c, std::string &why) {
     if (!(c->mesh.R > 0) || !(c->mesh.L > 0)) return bad("mesh R and L must be positive");
     if (c->mesh.nz < 3 || !pow2(c->mesh.nz - 1)) return bad("nz must be 2^k + 1 >= 3");
     if (c->mesh.nr < 3 || c->mesh.nr > 1025) return bad("nr must be in [3, 1025]");
-    if ((int64_t)(c->mesh.nz - 1) * (c->mesh.nr - 1) >= (1LL << 30)) return bad("mesh too large");
+    if ((int64_t)(c->mesh.nz - 1) * (c->mesh.nr - 1) >= (1LL << 24)) return bad("mesh too large (cells < 2^24)");
     if (!(c->dt > 0)) return bad("dt must be positive");
     if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return bad("precision");
     if (c->weighting != PIC_WEIGHT_ZR2 && c->weighting != PIC_WEIGHT_ZR) return bad("weighting");
@@ -305,6 +306,12 @@ void alloc_tables(pic_handle *h) {
         for (size_t k = 0; k < sg.size(); ++k) sg[k] = (T)h->own_sigma[s][k];
         h->sp[s].sigma = dalloc(h, sg.size() * sizeof(T));
         cudaMemcpyAsync(h->sp[s].sigma, sg.data(), sg.size() * sizeof(T), cudaMemcpyHostToDevice, h->st);
+        std::vector<T> s4((size_t)x.n_e * 4, (T)0);
+        for (int ch = 0; ch < x.n_ch; ++ch)
+            for (int k = 0; k < x.n_e; ++k) s4[(size_t)k * 4 + ch] = (T)h->own_sigma[s][(size_t)ch * x.n_e + k];
+        h->sp[s].sig4 = dalloc(h, s4.size() * sizeof(T));
+        cudaMemcpyAsync(h->sp[s].sig4, s4.data(), s4.size() * sizeof(T), cudaMemcpyHostToDevice, h->st);
+        cudaStreamSynchronize(h->st);
         // reference weight of radial cell j (Sec. 2.2): n0 pi (r_{j+1}^2 - r_j^2) dz / ppc_ref
         const int64_t base = h->cfg.sp[s].n_init / h->ncell;
         const double ppc = (double)(base > 0 ? base : 1);
@@ -477,6 +484,7 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     a.nr = h->nr;
     a.ncz = h->ncz;
     a.ncr = h->ncr;
+    a.inv_ncz = 1.0f / (float)h->ncz;
     a.s = s;
     a.qch[0] = h->cfg.sp[0].q;
     a.qch[1] = h->cfg.sp[1].q;
@@ -490,6 +498,7 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     a.dt_dz = (T)(dt / h->dz);
     a.dt_dr = (T)(dt / h->dr);
     a.dr = (T)h->dr;
+    a.inv_dr = (T)(1.0 / h->dr);
     a.t_null = h->t_null[s];
     a.nu_max = (T)h->nu_max[s];
     a.ng = (T)h->ngas;
@@ -500,6 +509,7 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     a.ion_acc = (T)((h->cfg.sp[1].q * h->cfg.sp[0].m) / (h->cfg.sp[0].q * h->cfg.sp[1].m));
     const pic_xsec &x = h->cfg.xs[s];
     a.xs.sigma = (const T *)h->sp[s].sigma;
+    a.xs.sig4 = (const typename V4<T>::type *)h->sp[s].sig4;
     a.xs.n_e = x.n_e;
     a.xs.n_ch = x.n_ch;
     a.xs.emax = (T)x.E_max_eV;

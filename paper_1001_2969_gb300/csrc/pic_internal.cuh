@@ -77,10 +77,13 @@ struct DevScalars {
     unsigned long long mg_aux_bits;
 };
 
+template <typename T>
+struct V4;
 // cross-section block for the particle kernel
 template <typename T>
 struct Xs {
-    const T *sigma;  // [n_ch][n_e]
+    const T *sigma;                       // [n_ch][n_e]
+    const typename V4<T>::type *sig4;     // [n_e] {sigma_0..sigma_3}, zero-padded
     int n_e, n_ch;
     T emax, inv_dE;
     int kind[kMaxCh];
@@ -92,6 +95,7 @@ struct Xs {
 template <typename T>
 struct StepArgs {
     int nz, nr, ncz, ncr;
+    float inv_ncz;  // 1/ncz for the cell decode
     int s;          // species of this launch
     double qch[2];  // species charges (absorbed-charge tallies)
     int weighting;  // PIC_WEIGHT_*
@@ -99,7 +103,7 @@ struct StepArgs {
     // final push: offsets/velocities/accelerations change per unit E
     T kz, kr, kv, ka;
     // first push
-    T dt, dt_dz, dt_dr, dr;
+    T dt, dt_dz, dt_dr, dr, inv_dr;
     // Monte Carlo
     unsigned long long t_null;  // candidate iff word < t_null
     T nu_max, ng, half_m_e;     // half_m_e = m / (2 e): E[eV] = half_m_e g^2
