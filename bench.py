@@ -181,6 +181,39 @@ def run_gpu(args, rank, world):
     return results
 
 
+def solve_only(args):
+    """Time the stand-alone field solve (pic_field_solve on device arrays) on the
+    workload's mesh with seeded random rho and chi, both precisions."""
+    import torch
+
+    import workloads as W
+    from paper_1001_2969_gb300 import build
+    from paper_1001_2969_gb300 import pic
+
+    build()
+    out = {}
+    for prec in ("mixed", "fp64"):
+        cfg = W.scaled(W.config(args.config, precision=prec), 0)
+        h = pic.pic_init(cfg, load=False)
+        chi = W.random_grid(cfg, seed=1, scale=1.0)
+        rho = 1e-5 * (W.random_grid(cfg, seed=2, smooth=False) - 0.5)
+        d_rho = torch.tensor(rho, device="cuda")
+        d_chi = torch.tensor(chi, device="cuda")
+        d_phi = torch.zeros_like(d_rho)
+        pic.pic_field_solve_device(h, d_rho.data_ptr(), d_chi.data_ptr(), 100.0, d_phi.data_ptr())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            cyc, res, st = pic.pic_field_solve_device(h, d_rho.data_ptr(), d_chi.data_ptr(), 100.0,
+                                                      d_phi.data_ptr())
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / max(args.steps, 1)
+        out[prec] = {"ms_per_solve": dt * 1e3, "cycles": cyc, "rel_residual": res, "status": st}
+        pic.pic_destroy(h)
+    print(json.dumps({"solve_only": out, "config": args.config}))
+    return 0
+
+
 def cpu_baseline(cfg_name, n_per_species, steps):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
     import workloads as W
@@ -216,12 +249,16 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="time only the stand-alone field solve on the workload's mesh")
     ap.add_argument("--particles", type=int, default=0,
                     help="particles per species (default: the workload's; smaller for profiling)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.solve_only:
+        return solve_only(args) if rank == 0 else 0
 
     if args.impl == "reference":
         if rank != 0:
