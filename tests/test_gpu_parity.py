@@ -306,3 +306,88 @@ def test_births_capacity_error_keeps_the_state(pic):
     after = by_id(pic.pic_get_particles(h, 0))
     for k in FIELDS + ("id",):
         assert np.array_equal(before[k], after[k])
+
+
+@pytest.mark.parametrize("variant", ["zr", "mean", "isotropic", "phi_zL"])
+def test_one_step_parity_variants(pic, variant):
+    """The flags of the paper's alternatives (Sec. 2.4 z-r weighting, Sec. 2.5 mean face
+    rule) and of the test scattering law, and Dirichlet data on z = L."""
+    kw = {"zr": dict(weighting="zr"), "mean": dict(chi_face="mean"),
+          "isotropic": dict(scatter="isotropic"), "phi_zL": {}}[variant]
+    cfg = _state_cfg("fp64", **kw)
+    if variant == "phi_zL":
+        cfg["phi_zL"] = 20.0 * np.cos(np.linspace(0, np.pi / 2, cfg["nr"]))
+    e, i = _random_state(cfg, 30_000, 20_000, seed=31)
+    _one_step(pic, cfg, e, i, 5, "fp64")
+
+
+def test_checkpoint_resume_matches_uninterrupted_run(pic, tmp_path):
+    cfg = W.scaled(W.config("c1", precision="fp64"), 20_000)
+    h1 = pic.pic_init(cfg)
+    pic.pic_step(h1, 3)
+    path = str(tmp_path / "ck.bin")
+    pic.pic_save(h1, path)
+    h2 = pic.pic_init(cfg, load=False)
+    pic.pic_load(h2, path)
+    assert pic.pic_get_counts(h2)["step"] == 3
+    pic.pic_step(h1, 2)
+    pic.pic_step(h2, 2)
+    for s in (0, 1):
+        a, b = by_id(pic.pic_get_particles(h1, s)), by_id(pic.pic_get_particles(h2, s))
+        assert np.array_equal(a["id"], b["id"])
+        for k in FIELDS:
+            assert nerr(b[k], a[k]) < 1e-12, k
+    fa, fb = pic.pic_get_fields(h1), pic.pic_get_fields(h2)
+    assert nerr(fb["phi"], fa["phi"]) < 1e-12
+
+
+def test_particle_capacity_error_keeps_the_state(pic):
+    cfg = _state_cfg("fp64", capacity=30_050, split_every=1)
+    e, i = _random_state(cfg, 30_000, 1000, seed=41, hot=1.0)
+    o = Oracle(cfg)
+    dr = cfg["R"] / (cfg["nr"] - 1)
+    j = np.minimum(np.floor(e["r"] / dr).astype(int), cfg["nr"] - 2)
+    e["w"] = np.array([o.w_ref(0, int(k)) for k in j]) * 3.5  # every electron splits into 3-4
+    h = pic.pic_init(cfg, load=False)
+    pic.pic_set_particles(h, 0, e)
+    pic.pic_set_particles(h, 1, i)
+    before = by_id(pic.pic_get_particles(h, 0))
+    with pytest.raises(pic.PicError) as err:
+        pic.pic_step(h, 1)
+    assert err.value.status == pic.PIC_ERR_CAPACITY
+    after = by_id(pic.pic_get_particles(h, 0))
+    for k in FIELDS + ("id",):
+        assert np.array_equal(before[k], after[k])
+    assert pic.pic_get_counts(h)["step"] == 0
+
+
+def test_non_finite_particles_are_dropped_and_reported(pic):
+    cfg = _state_cfg("fp64")
+    e, i = _random_state(cfg, 1000, 1000, seed=51)
+    e["vz"][7] = np.nan
+    h = pic.pic_init(cfg, load=False)
+    pic.pic_set_particles(h, 0, e)
+    pic.pic_set_particles(h, 1, i)
+    st = pic.pic_step(h, 1)
+    assert st == pic.PIC_ERR_NUMERIC
+    g = pic.pic_get_particles(h, 0)
+    assert e["id"][7] not in set(g["id"].tolist())
+    assert np.all(np.isfinite(g["vz"]))
+
+
+def test_moments_into_device_buffers(pic):
+    torch = pytest.importorskip("torch")
+    import ctypes as C
+
+    cfg = W.scaled(W.config("c1", precision="mixed"), 20_000)
+    h = pic.pic_init(cfg)
+    pic.pic_step(h, 3)
+    host = pic.pic_moments(h)
+    bufs = [torch.zeros(cfg["nz"] * cfg["nr"], dtype=torch.float64, device="cuda") for _ in range(5)]
+    dp = C.POINTER(C.c_double)
+    out = pic.pic_moments_out(*[C.cast(b.data_ptr(), dp) for b in bufs], None, None, None, 0, 1)
+    pic.pic_moments_into(h, out)
+    torch.cuda.synchronize()
+    for name, b in zip(("ne", "ni", "phi", "Er", "Ez"), bufs):
+        np.testing.assert_array_equal(b.cpu().numpy().reshape(cfg["nz"], cfg["nr"]), host[name])
+    assert out.nsamples == 3
