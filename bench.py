@@ -131,6 +131,7 @@ def run_gpu(args, rank, world):
         n0 = pic.pic_get_counts(h)["n_alive"].sum()
         if world > 1:
             torch.distributed.barrier()
+        pic.pic_moments(h, reset=True)  # restarts the V-cycle count
         torch.cuda.synchronize()
         clocks = Clocks(dev) if prec == args.precision else None
         if clocks:
@@ -148,9 +149,11 @@ def run_gpu(args, rank, world):
         pic.pic_profile(h, False)
         tm = pic.pic_timings(h, reset=True)
         ms = ev0.elapsed_time(ev1)
+        cycles = int(pic.pic_moments(h)["counters"][pic.PIC_C_MGCYC])
         n1 = pic.pic_get_counts(h)["n_alive"].sum()
         psteps = 0.5 * (n0 + n1) * steps
-        res = dict(ms=ms, psteps=psteps, n0=int(n0), n1=int(n1), timings=tm, clocks=ck, status=st)
+        res = dict(ms=ms, psteps=psteps, n0=int(n0), n1=int(n1), timings=tm, clocks=ck, status=st,
+                   mg_cycles=cycles / steps)
         if prec == args.precision:
             # end to end through the public API with host buffers: per step the z = L
             # boundary row goes host -> device from pinned memory and the time-averaged
@@ -331,6 +334,7 @@ def main():
                      "traffic": tb * main_r["psteps"] / (2 * args.steps) if tb else None,
                      "kernel_ms_per_step": k_ms / args.steps},
         "phases_ms_per_step": {k[:-3]: v / args.steps for k, v in tm.items() if k.endswith("_ms")},
+        "mg_cycles_per_step": main_r["mg_cycles"],
         "gpu_launches": tm["launches"],
         "clocks": main_r["clocks"],
     }
@@ -341,7 +345,8 @@ def main():
         line["fp64"] = {"value": r["psteps"] / (r["ms"] * 1e-3), "unit": UNIT,
                         "ms_per_step": r["ms"] / args.fp64_steps, "steps": args.fp64_steps,
                         "particle_pass_ms_per_step": k64 / args.fp64_steps,
-                        "solve_ms_per_step": t64["solve_ms"] / args.fp64_steps}
+                        "solve_ms_per_step": t64["solve_ms"] / args.fp64_steps,
+                        "mg_cycles_per_step": r["mg_cycles"]}
     e = main_r["e2e"]
     line["e2e"] = {"value": e["psteps"] / e["seconds"], "unit": UNIT,
                    "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"],

@@ -30,6 +30,11 @@ namespace pic {
 
 namespace {
 
+// bit pattern of |x|: ordered like |x| for numbers, above them for a NaN
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
 __device__ __forceinline__ void atomic_max_pos(unsigned long long *dst, double v) {
     atomicMax(dst, (unsigned long long)__double_as_longlong(v));
 }
@@ -498,12 +503,24 @@ __global__ void k_single_row(const MGFast *__restrict__ mp, double *phi, int nr,
 // The whole solve in one cooperative launch.  Blocks are co-resident (the
 // launch guarantees it), and phases are separated by a grid barrier whose
 // spin is bounded: after kSpinLimit polls a block raises `timeout` and every
-// block leaves.  Per cycle: residual + norms -> convergence decision (same
-// value read by every block) -> restriction chain (warp per column) ->
-// coarsest row -> red and black line sweeps per level -> (mixed) phi += delta.
+// block leaves.  The V-cycle works on the correction delta of phi in both
+// precisions (FP32 delta and residual for the mixed path).  Per cycle:
+//   1. residual of phi + delta, its norms and the restriction chain down to
+//      the coarsest level, one tile of columns per block (coalesced rows);
+//   2. convergence decision (every block reads the same maxima), then
+//      phi += delta;
+//   3. up the levels, one phase per level: the block owning black line
+//      i = 2q + 2 solves the red lines 2q + 1 and 2q + 3 beside it (the two
+//      halves of the block at once when they fit), keeps them in shared
+//      memory and solves the black line.  A red line shared by two blocks is
+//      computed by both from the same data, bit for bit, and stored by one.
+//      So one barrier separates two levels instead of two.
+// The coarsest row is solved by block 0 in the phase of level L-1, which
+// block 0 sweeps alone.  Levels with at most kBarGroup black lines belong to
+// the first kBarGroup blocks, separated by a barrier among those blocks only;
+// the rest of the grid waits at the next full barrier.
 // ---------------------------------------------------------------------------
 constexpr long long kSpinLimit = 1LL << 26;
-constexpr int kChainWarps = 8;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
@@ -511,41 +528,28 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
 __device__ __forceinline__ void atom_add_release(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid barrier in two levels: blocks arrive on their group's counter (groups
-// of kBarGroup); the last of a group arrives on the top counter; the last
-// group releases the next generation, which the others poll with a bounded
-// number of tries.  Acquire-release atomics carry the blocks' writes across.
-constexpr int kBarGroup = 8;
+// Barrier on a counter that only grows: thread 0 of each block adds 1 with
+// release semantics and polls with acquire loads until the counter reaches
+// the target of this barrier (its number of participants times the number
+// of barriers of this kind the block has passed).  The block's writes before
+// the barrier are visible to every participant after it.  The poll is
+// bounded: after kSpinLimit tries (or once another block gave up) the block
+// raises `timeout` and returns false.
+constexpr int kBarGroup = 8;  // blocks that sweep the coarse levels alone
 
-__device__ __forceinline__ bool grid_barrier(MGCtl *ctl, unsigned nblocks) {
+__device__ __forceinline__ bool count_barrier(unsigned *count, unsigned target, MGCtl *ctl) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned g = blockIdx.x / kBarGroup;
-        const unsigned gsize = min((unsigned)kBarGroup, nblocks - g * kBarGroup);
-        const unsigned ngroups = (nblocks + kBarGroup - 1) / kBarGroup;
-        const unsigned gen = ld_acquire(&ctl->bar_gen.v);
-        if (atom_add_acq_rel(&ctl->bar_group[g].v, 1u) == gsize - 1) {
-            ctl->bar_group[g].v = 0u;
-            if (atom_add_acq_rel(&ctl->bar_top.v, 1u) == ngroups - 1) {
-                ctl->bar_top.v = 0u;
-                atom_add_release(&ctl->bar_gen.v, 1u);
-            }
-        }
+        atom_add_release(count, 1u);
         long long it = 0;
-        while (ld_acquire(&ctl->bar_gen.v) == gen) {
-            if (++it > kSpinLimit || *(volatile int *)&ctl->timeout) {
+        while ((int)(ld_acquire(count) - target) < 0) {
+            if ((++it & 255) == 0 && (it > kSpinLimit || *(volatile int *)&ctl->timeout)) {
                 atomicExch(&ctl->timeout, 1);
                 ok = 0;
                 break;
@@ -557,35 +561,45 @@ __device__ __forceinline__ bool grid_barrier(MGCtl *ctl, unsigned nblocks) {
     return s_ok != 0;
 }
 
-// async copies of one line's factors into shared memory F[(2K+1) n]
-// (issued first, so they overlap the right-hand-side loads)
-template <typename Ts>
-__device__ __forceinline__ void fac_prefetch(Ts *F, const Ts *__restrict__ fac, int n, int K) {
-    const int j = threadIdx.x;
-    if (j < n) {
-        for (int k = 0; k <= 2 * K; ++k) {
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(F + (size_t)k * n + j);
-            const Ts *src = fac + (size_t)k * n + j;
-            if (sizeof(Ts) == 8)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-            else
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-        }
+// Asynchronous copy of `bytes` (a multiple of the element size) from global
+// to shared memory by threads t = 0..nt-1 of the block: 16-byte pieces when
+// both ends and the length allow it, else 8- or 4-byte pieces.  The caller
+// commits the group.
+__device__ __forceinline__ void copy_async(void *dst, const void *src, int bytes, int t, int nt) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const char *s = static_cast<const char *>(src);
+    const unsigned long long a = (unsigned long long)s | d | (unsigned)bytes;
+    if ((a & 15) == 0) {
+        for (int o = t * 16; o < bytes; o += nt * 16)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + o), "l"(s + o) : "memory");
+    } else if ((a & 7) == 0) {
+        for (int o = t * 8; o < bytes; o += nt * 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + o), "l"(s + o) : "memory");
+    } else {
+        for (int o = t * 4; o < bytes; o += nt * 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + o), "l"(s + o) : "memory");
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
 }
+__device__ __forceinline__ void copy_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void copy_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// PCR reduction with factors already requested into F; d = this thread's
-// right-hand side; returns the solution of unknown j
+// PCR reduction of one line whose factors F were requested with cp.async:
+// unknown j of the line (active when act) with right-hand side d; returns
+// its solution.  Every thread of the block calls it (the two halves of a
+// block may reduce two lines at once).  keep_newest: the most recent copy
+// group may still be in flight (it belongs to a later line).
 template <typename Ts>
-__device__ __forceinline__ Ts pcr_steps_sm(Ts d, Ts *D, Ts *D2, const Ts *F, int n, int K) {
-    const int j = threadIdx.x;
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (j < n) D[j] = d;
+__device__ __forceinline__ Ts pcr_line(Ts d, Ts *D, Ts *D2, const Ts *F, int n, int K, int j, bool act,
+                                       bool keep_newest) {
+    if (keep_newest)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (act) D[j] = d;
     __syncthreads();
     int k = 0;
     for (int s = 1; s < n; s <<= 1, ++k) {
-        if (j < n) {
+        if (act) {
             Ts v = D[j];
             if (j - s >= 0) v += F[(size_t)(2 * k) * n + j] * D[j - s];
             if (j + s < n) v += F[(size_t)(2 * k + 1) * n + j] * D[j + s];
@@ -597,68 +611,152 @@ __device__ __forceinline__ Ts pcr_steps_sm(Ts d, Ts *D, Ts *D2, const Ts *F, int
         D = D2;
         D2 = t;
     }
-    const Ts x = j < n ? d * F[(size_t)(2 * K) * n + j] : (Ts)0;
+    const Ts x = act ? d * F[(size_t)(2 * K) * n + j] : (Ts)0;
     __syncthreads();  // F and D are reused by the next line
     return x;
 }
 
+// Shared-memory layout of the one-launch solve (byte offsets), set on the host.
+struct SolveLayout {
+    int offD;   // PCR scratch: per half 2n values of 8 bytes
+    int offX;   // the two red lines' solutions, kept for the black line's right-hand side
+    int offR0;  // factors of the first red line; the coarsest row's FP64 factors
+    int offR1;  // factors of the second red line (== offR0: reds one after the other)
+    int offB;   // factors of the black line (== offR0: requested after the reds)
+    int offT;   // residual / restriction tile (== offR0: no early request of the coarsest factors)
+    int tw;     // columns per residual tile
+    int lt;     // threads per line (power of two >= n)
+    int pair;   // the two halves of the block reduce the two red lines at once
+};
+
+// black lines of a level with nz rows (at least one unit of work: nz = 3 has
+// a red line only)
+__device__ __forceinline__ int units_of(int nz) { return max((nz - 3) / 2, 1); }
+
 template <typename Tv>
 __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restrict__ mp, double *phi, int nr, int K,
-                                   int first_cycle, int dbl) {
+                                   int first_cycle, SolveLayout lay) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MGFast &m = *mp;
     MGCtl *ctl = m.ctl;
     const int n = nr - 1, nz0 = m.nz[0], ng = nz0 * nr, L = m.nlev - 1;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     const bool mixed = sizeof(Tv) == 4;
-    __shared__ double s_r[32], s_b[32];
+    Tv *delta = mixed ? (Tv *)m.u32[0] : (Tv *)m.u64[0];  // level-0 correction (zero on the boundary)
+    const bool cpre = lay.offT != lay.offR0;                // coarsest factors requested early
+    const bool bsep = lay.offB != lay.offR0;
+    const int FE = (2 * K + 1) * n;                         // factor elements of a line
+    // levels whose work fits in G blocks are swept by the first G blocks only
+    const int G = min(kBarGroup, (int)gridDim.x);
+    int lb = L;
+    while (lb > 0 && units_of(m.nz[lb - 1]) <= G) --lb;
+    const bool in_group = (int)blockIdx.x < G;
+    __shared__ unsigned long long s_r[32], s_b[32];
     __shared__ int s_decide;
     int first = first_cycle;
+    unsigned ngrid = 0, ngroup = 0;  // barriers of each kind passed
+    Tv *X = reinterpret_cast<Tv *>(smem_raw + lay.offX);
+    Tv *R0 = reinterpret_cast<Tv *>(smem_raw + lay.offR0);
+    Tv *R1 = reinterpret_cast<Tv *>(smem_raw + lay.offR1);
+    Tv *FBk = reinterpret_cast<Tv *>(smem_raw + lay.offB);
+    const int half = lay.pair ? (tid >= lay.lt) : 0;
+    const int jl = lay.pair ? tid - half * lay.lt : tid;  // unknown of this thread's line
+    Tv *Dh = reinterpret_cast<Tv *>(smem_raw + lay.offD + (size_t)half * 2 * n * sizeof(double));
     for (int cyc = 0;; ++cyc) {
-        // ---- residual and norms ----
-        double rmax = 0.0, bmax = 0.0;
+        // ---- residual of phi + delta, its norms, and the restriction chain ----
+        if (cpre && blockIdx.x == 0 && L > 0) copy_async(R0, m.facc, FE * 8, tid, nt);
+        copy_commit();
+        // maxima as bit patterns of |x| (ordered like the values; a NaN
+        // compares above every number), so the reductions are integer work
+        unsigned long long rmax = 0ull, bmax = 0ull;
         {
             const double *cz = m.cz[0], *cr = m.cr[0];
-            for (int k = blockIdx.x * blockDim.x + tid; k < ng; k += gridDim.x * blockDim.x) {
-                const int i = k / nr, j = k % nr;
-                double r = 0.0;
-                if (i > 0 && i < nz0 - 1 && j < nr - 1) {
-                    const double a = cz[k - nr], c = cz[k], e = cr[k], d = j > 0 ? cr[k - 1] : 0.0;
-                    double Au = (a + c + d + e) * phi[k] - a * phi[k - nr] - c * phi[k + nr] - e * phi[k + 1];
-                    if (j > 0) Au -= d * phi[k - 1];
-                    r = m.f0[k] - Au;
-                    rmax = fmax(rmax, fabs(r));
-                    if (first) {
-                        double b = m.f0[k];
-                        if (i == 1) b += a * phi[k - nr];
-                        if (i == nz0 - 2) b += c * phi[k + nr];
-                        if (j == nr - 2) b += e * phi[k + 1];
-                        bmax = fmax(bmax, fabs(b));
+            const int tw = lay.tw;
+            // the restriction chain runs in the V-cycle's type
+            Tv *T0 = reinterpret_cast<Tv *>(smem_raw + lay.offT);
+            Tv *T1 = T0 + (size_t)tw * nz0;
+            Tv *f0v = mixed ? (Tv *)m.f32[0] : (Tv *)m.f64[0];
+            const int ntile = (n + tw - 1) / tw;
+            for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+                const int j0 = t * tw;
+                // interior rows only: the chain never reads a level's boundary rows
+                for (int e = tid; e < tw * (nz0 - 2); e += nt) {
+                    const int c = e % tw, i = 1 + e / tw, j = j0 + c;
+                    double r = 0.0;
+                    if (j < n) {
+                        const size_t k = (size_t)i * nr + j;
+                        const double pc = phi[k] + (double)delta[k], ps = phi[k - nr] + (double)delta[k - nr];
+                        const double pn = phi[k + nr] + (double)delta[k + nr], pe = phi[k + 1] + (double)delta[k + 1];
+                        const double pw = j > 0 ? phi[k - 1] + (double)delta[k - 1] : 0.0;
+                        const double a = cz[k - nr], cc = cz[k], ee = cr[k], d = j > 0 ? cr[k - 1] : 0.0;
+                        double Au = (a + cc + d + ee) * pc - a * ps - cc * pn - ee * pe;
+                        if (j > 0) Au -= d * pw;
+                        const double f = m.f0[k];
+                        r = f - Au;
+                        rmax = max(rmax, abs_bits(r));
+                        if (first) {
+                            double bb = f;
+                            if (i == 1) bb += a * phi[k - nr];
+                            if (i == nz0 - 2) bb += cc * phi[k + nr];
+                            if (j == nr - 2) bb += ee * phi[k + 1];
+                            bmax = max(bmax, abs_bits(bb));
+                        }
+                        if (L > 0) f0v[k] = (Tv)r;
                     }
+                    T0[(size_t)c * nz0 + i] = (Tv)r;
                 }
-                m.r[k] = r;
-                if (mixed) m.f32[0][k] = (float)r;
+                __syncthreads();
+                Tv *src = T0, *dst = T1;
+                int nzp = nz0;
+                for (int l = 1; l <= L; ++l) {
+                    const int nzc = m.nz[l];
+                    Tv *fl = mixed ? (Tv *)m.f32[l] : (Tv *)m.f64[l];
+                    for (int e = tid; e < tw * (nzc - 2); e += nt) {
+                        const int c = e % tw, I = 1 + e / tw, j = j0 + c;
+                        const Tv *s = src + (size_t)c * nzp;
+                        const Tv v = (Tv)0.5 * s[2 * I - 1] + s[2 * I] + (Tv)0.5 * s[2 * I + 1];
+                        dst[(size_t)c * nzc + I] = v;
+                        if (j < n) {
+                            const size_t k = (size_t)I * nr + j;
+                            if (l == L)
+                                m.fc64[k] = (double)v;
+                            else
+                                fl[k] = v;
+                        }
+                    }
+                    __syncthreads();
+                    Tv *tmp = src;
+                    src = dst;
+                    dst = tmp;
+                    nzp = nzc;
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-                bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+                rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+                bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
             }
             if (lane == 0) {
                 s_r[warp] = rmax;
                 s_b[warp] = bmax;
             }
             __syncthreads();
-            if (tid == 0) {
-                double r = 0.0, b = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                    r = fmax(r, s_r[w]);
-                    b = fmax(b, s_b[w]);
+            if (tid < 32) {
+                unsigned long long r = tid < (nt >> 5) ? s_r[tid] : 0ull;
+                unsigned long long b = tid < (nt >> 5) ? s_b[tid] : 0ull;
+                for (int o = 16; o > 0; o >>= 1) {
+                    r = max(r, __shfl_xor_sync(0xffffffffu, r, o));
+                    b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
                 }
-                atomic_max_pos(&ctl->rb[cyc & 1], r);
-                if (first) atomic_max_pos(&ctl->b_bits, b);
+                if (tid == 0) {
+                    atomicMax(&ctl->rb[cyc & 1], r);
+                    if (first) atomicMax(&ctl->b_bits, b);
+                }
             }
         }
-        if (!grid_barrier(ctl, gridDim.x)) return;
+        if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
+            copy_wait_all();
+            return;
+        }
         // ---- decision: every block reads the same maxima ----
         if (tid == 0) {
             const double rn = __longlong_as_double((long long)*(volatile unsigned long long *)&ctl->rb[cyc & 1]);
@@ -684,167 +782,194 @@ __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restr
         const int decide = s_decide;
         first = 0;
         if (decide == 3) {
-            for (int k = blockIdx.x * blockDim.x + tid; k < ng; k += gridDim.x * blockDim.x) {
+            for (int k = blockIdx.x * nt + tid; k < ng; k += gridDim.x * nt) {
                 const int i = k / nr, j = k % nr;
                 if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] = 0.0;
             }
+            copy_wait_all();
             return;
         }
-        if (decide != 0) return;
+        // the pending correction goes into phi (also on the way out); nothing
+        // reads phi again before the next residual
+        if (L > 0)
+            for (int k = blockIdx.x * nt + tid; k < ng; k += gridDim.x * nt) {
+                const int i = k / nr, j = k % nr;
+                if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] += (double)delta[k];
+            }
+        if (decide != 0) {
+            copy_wait_all();
+            return;
+        }
         if (L == 0) {
             // nz = 3: the single interior row of phi, exactly
             if (blockIdx.x == 0) {
-                double *D = reinterpret_cast<double *>(smem_raw);
-                fac_prefetch<double>(D + 2 * n, m.facc, n, K);  // right after the D region
+                double *D = reinterpret_cast<double *>(smem_raw + lay.offD);
+                double *F = reinterpret_cast<double *>(smem_raw + lay.offR0);
+                copy_async(F, m.facc, FE * 8, tid, nt);
+                copy_commit();
                 double rhs = 0.0;
-                if (tid < n) {
+                const bool act = tid < n;
+                if (act) {
                     const double *cz = m.cz[0], *cr = m.cr[0];
                     const size_t k = (size_t)nr + tid;
                     rhs = m.f0[k] + cz[k - nr] * phi[k - nr] + cz[k] * phi[k + nr];
                     if (tid == n - 1) rhs += cr[k] * phi[k + 1];
                 }
-                const double x = pcr_steps_sm<double>(rhs, D, D + n, D + 2 * n, n, K);
-                if (tid < n) phi[(size_t)nr + tid] = x;
+                const double x = pcr_line<double>(rhs, D, D + n, F, n, K, tid, act, false);
+                if (act) phi[(size_t)nr + tid] = x;
             }
-            if (!grid_barrier(ctl, gridDim.x)) return;
+            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) return;
             continue;
         }
-        // ---- restriction chain: warp per column, lanes over rows ----
-        const int cw = min(kChainWarps, (int)(blockDim.x >> 5));  // warps doing the chain
-        if (warp < cw) {
-            double *colA = reinterpret_cast<double *>(smem_raw) + (size_t)warp * 2 * nz0;
-            double *colB = colA + nz0;
-            for (int j = blockIdx.x * cw + warp; j < n; j += gridDim.x * cw) {
-                for (int i = lane; i < nz0; i += 32) colA[i] = m.r[(size_t)i * nr + j];
-                __syncwarp();
-                double *src = colA, *dst = colB;
-                for (int l = 1; l <= L; ++l) {
-                    const int nzc = m.nz[l];
-                    for (int I = lane; I < nzc; I += 32) {
-                        double v = 0.0;
-                        if (I > 0 && I < nzc - 1) v = 0.5 * src[2 * I - 1] + src[2 * I] + 0.5 * src[2 * I + 1];
-                        dst[I] = v;
-                        const size_t k = (size_t)I * nr + j;
-                        if (l == L)
-                            m.fc64[k] = v;
-                        else if (mixed)
-                            m.f32[l][k] = (float)v;
-                        else
-                            m.f64[l][k] = v;
-                    }
-                    __syncwarp();
-                    double *t = src;
-                    src = dst;
-                    dst = t;
-                }
+        // level 0's sweeps rewrite delta: when they run in the group alone,
+        // every block's update of phi has to be in first
+        if (lb == 0)
+            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
+                copy_wait_all();
+                return;
             }
-        }
-        if (!grid_barrier(ctl, gridDim.x)) return;
-        // ---- coarsest row ----
-        if (blockIdx.x == 0) {
-            double *D = reinterpret_cast<double *>(smem_raw);
-            fac_prefetch<double>(D + 2 * n, m.facc, n, K);
-            const double rhs = tid < n ? m.fc64[(size_t)nr + tid] : 0.0;
-            const double x = pcr_steps_sm<double>(rhs, D, D + n, D + 2 * n, n, K);
-            Tv *u = mixed ? (Tv *)m.u32[L] : (Tv *)m.u64[L];
-            if (tid < n) u[(size_t)nr + tid] = (Tv)x;
-        }
-        if (!grid_barrier(ctl, gridDim.x)) return;
-        // ---- up: red then black line sweeps per level ----
-        // line factors: buffer A, and B when double-buffered; the first line
-        // of the next phase is requested before each barrier
-        Tv *FA = reinterpret_cast<Tv *>(smem_raw + 2 * (size_t)n * sizeof(double));
-        Tv *FB = FA + (size_t)(2 * K + 1) * n;
-        Tv *Fnext = FA;
-        int have = 0;
+        // ---- up: per level, each black line with the two red lines beside it ----
+        bool have = false;  // this block's first red factors of the level are requested
         for (int l = L - 1; l >= 0; --l) {
-            const bool on_phi = !mixed && l == 0;
-            Tv *u = on_phi ? (Tv *)phi : (mixed ? (Tv *)m.u32[l] : (Tv *)m.u64[l]);
+            const bool grp = l >= lb;
+            const int P = grp ? G : (int)gridDim.x;
+            const int nzl = m.nz[l], nzc = m.nz[l + 1];
+            const int NB = (nzl - 3) / 2;  // black lines
+            const int nq = units_of(nzl);
+            Tv *u = mixed ? (Tv *)m.u32[l] : (Tv *)m.u64[l];
             const Tv *uc = mixed ? (const Tv *)m.u32[l + 1] : (const Tv *)m.u64[l + 1];
-            const Tv *f = l == 0 ? (mixed ? (const Tv *)m.f32[0] : (const Tv *)m.f0)
-                                 : (mixed ? (const Tv *)m.f32[l] : (const Tv *)m.f64[l]);
+            const Tv *f = mixed ? (const Tv *)m.f32[l] : (const Tv *)m.f64[l];
             const Tv *cz = mixed ? (const Tv *)m.cz32[l] : (const Tv *)m.cz[l];
-            const Tv *cr = mixed ? (const Tv *)m.cr32[l] : (const Tv *)m.cr[l];
             const Tv *fac = mixed ? (const Tv *)m.fac32[l] : (const Tv *)m.fac64[l];
-            const int nz = m.nz[l], nzc = m.nz[l + 1];
-            Tv *D = reinterpret_cast<Tv *>(smem_raw);
-            for (int color = 0; color < 2; ++color) {
-                const int nlines = color == 0 ? (nz - 1) / 2 : (nz - 3) / 2;
-                Tv *F = Fnext;
-                for (int q = blockIdx.x; q < nlines; q += gridDim.x) {
-                    const int i = color == 0 ? 1 + 2 * q : 2 + 2 * q;
-                    const size_t rowk = (size_t)i * nr;
-                    if (!(have && q == (int)blockIdx.x))
-                        fac_prefetch<Tv>(F, fac + (size_t)(i - 1) * (2 * K + 1) * n, n, K);
-                    Tv rhs = 0;
-                    if (tid < n) {
-                        const size_t k = rowk + tid;
-                        Tv udn, uup;
-                        if (color == 0) {
-                            const int Idn = (i - 1) / 2, Iup = (i + 1) / 2;
-                            if (i - 1 == 0)
-                                udn = on_phi ? u[k - nr] : (Tv)0;
-                            else
-                                udn = (on_phi ? u[k - nr] : (Tv)0) +
-                                      ((Idn > 0 && Idn < nzc - 1) ? uc[(size_t)Idn * nr + tid] : (Tv)0);
-                            if (i + 1 == nz - 1)
-                                uup = on_phi ? u[k + nr] : (Tv)0;
-                            else
-                                uup = (on_phi ? u[k + nr] : (Tv)0) +
-                                      ((Iup > 0 && Iup < nzc - 1) ? uc[(size_t)Iup * nr + tid] : (Tv)0);
+            if ((int)blockIdx.x < P) {
+                if (l == L - 1 && blockIdx.x == 0) {
+                    // the coarsest row (FP64 factors), then level L-1 in this block alone
+                    double *D = reinterpret_cast<double *>(smem_raw + lay.offD);
+                    double *F = reinterpret_cast<double *>(smem_raw + lay.offR0);
+                    if (!cpre) copy_async(F, m.facc, FE * 8, tid, nt);
+                    copy_commit();
+                    const bool act = tid < n;
+                    const double rhs = act ? m.fc64[(size_t)nr + tid] : 0.0;
+                    const double x = pcr_line<double>(rhs, D, D + n, F, n, K, tid, act, false);
+                    Tv *ucw = mixed ? (Tv *)m.u32[L] : (Tv *)m.u64[L];
+                    if (act) ucw[(size_t)nr + tid] = (Tv)x;
+                    __syncthreads();
+                    have = false;
+                }
+                for (int q = blockIdx.x; q < nq; q += P) {
+                    const int ra = 2 * q + 1, rb = 2 * q + 3, ib = 2 * q + 2;
+                    const bool hasb = NB >= 1;
+                    // factor requests: the reds (unless already in), then the black
+                    if (!(have && q == (int)blockIdx.x)) {
+                        if (lay.pair) {
+                            copy_async(R0, fac + (size_t)(ra - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
+                            if (hasb) copy_async(R1, fac + (size_t)(rb - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
                         } else {
-                            udn = u[k - nr];
-                            uup = u[k + nr];
-                        }
-                        rhs = f[k] + cz[k - nr] * udn + cz[k] * uup;
-                        if (tid == n - 1 && on_phi) rhs += cr[k] * u[k + 1];
-                    }
-                    const Tv x = pcr_steps_sm<Tv>(rhs, D, D + n, F, n, K);
-                    if (tid < n) u[rowk + tid] = x;
-                }
-                have = 0;
-                Fnext = FA;
-                if (dbl) {
-                    // next phase: black of this level, else red of the level below
-                    int ln = -1, cn = 0;
-                    if (color == 0) {
-                        ln = l;
-                        cn = 1;
-                    } else if (l > 0) {
-                        ln = l - 1;
-                        cn = 0;
-                    }
-                    if (ln >= 0) {
-                        const int nzn = m.nz[ln];
-                        const int nl = cn == 0 ? (nzn - 1) / 2 : (nzn - 3) / 2;
-                        if ((int)blockIdx.x < nl) {
-                            const int in = cn == 0 ? 1 + 2 * (int)blockIdx.x : 2 + 2 * (int)blockIdx.x;
-                            const Tv *facn = mixed ? (const Tv *)m.fac32[ln] : (const Tv *)m.fac64[ln];
-                            Fnext = (F == FA) ? FB : FA;
-                            fac_prefetch<Tv>(Fnext, facn + (size_t)(in - 1) * (2 * K + 1) * n, n, K);
-                            have = 1;
+                            copy_async(R0, fac + (size_t)(ra - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
                         }
                     }
+                    copy_commit();
+                    if (hasb && bsep) copy_async(FBk, fac + (size_t)(ib - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
+                    copy_commit();
+                    have = false;
+                    // the black line's own inputs do not depend on the reds: load them first
+                    Tv fb = 0, cb0 = 0, cb1 = 0;
+                    if (hasb && tid < n) {
+                        const size_t k = (size_t)ib * nr + tid;
+                        fb = f[k];
+                        cb0 = cz[k - nr];
+                        cb1 = cz[k];
+                    }
+                    // red right-hand sides: f plus the coarse correction injected at rows i -/+ 1
+                    auto red_rhs = [&](int i, int j) -> Tv {
+                        const size_t k = (size_t)i * nr + j;
+                        const int Idn = (i - 1) / 2, Iup = (i + 1) / 2;
+                        const Tv udn = (Idn > 0 && Idn < nzc - 1) ? uc[(size_t)Idn * nr + j] : (Tv)0;
+                        const Tv uup = (Iup > 0 && Iup < nzc - 1) ? uc[(size_t)Iup * nr + j] : (Tv)0;
+                        return f[k] + cz[k - nr] * udn + cz[k] * uup;
+                    };
+                    if (lay.pair) {
+                        const int i = half ? rb : ra;
+                        const bool act = jl < n && (half == 0 || hasb);
+                        const Tv rhs = act ? red_rhs(i, jl) : (Tv)0;
+                        const Tv x = pcr_line<Tv>(rhs, Dh, Dh + n, half ? R1 : R0, n, K, jl, act, true);
+                        if (act) {
+                            X[half * n + jl] = x;
+                            // red rb is also the next black's red ra: one block writes it
+                            if (half == 0 || q == NB - 1) u[(size_t)i * nr + jl] = x;
+                        }
+                    } else {
+                        const bool act = tid < n;
+                        Tv rhs = act ? red_rhs(ra, tid) : (Tv)0;
+                        Tv x = pcr_line<Tv>(rhs, Dh, Dh + n, R0, n, K, tid, act, true);
+                        if (act) {
+                            X[tid] = x;
+                            u[(size_t)ra * nr + tid] = x;
+                        }
+                        if (hasb) {
+                            copy_async(R0, fac + (size_t)(rb - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
+                            copy_commit();
+                            rhs = act ? red_rhs(rb, tid) : (Tv)0;
+                            x = pcr_line<Tv>(rhs, Dh, Dh + n, R0, n, K, tid, act, false);
+                            if (act) {
+                                X[n + tid] = x;
+                                if (q == NB - 1) u[(size_t)rb * nr + tid] = x;
+                            }
+                        }
+                    }
+                    if (hasb) {
+                        __syncthreads();  // X complete
+                        Tv *F = FBk;
+                        if (!bsep) {
+                            copy_async(R0, fac + (size_t)(ib - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
+                            copy_commit();
+                            F = R0;
+                        }
+                        const bool act = tid < n;
+                        const Tv rhs = act ? fb + cb0 * X[tid] + cb1 * X[n + tid] : (Tv)0;
+                        Tv *D = reinterpret_cast<Tv *>(smem_raw + lay.offD);
+                        const Tv x = pcr_line<Tv>(rhs, D, D + n, F, n, K, tid, act, false);
+                        if (act) u[(size_t)ib * nr + tid] = x;
+                    }
                 }
-                if (!grid_barrier(ctl, gridDim.x)) return;
+                // request the next level's first red factors of this block
+                if (l > 0) {
+                    const int ln = l - 1;
+                    const int Pn = ln >= lb ? G : (int)gridDim.x;
+                    const int nqn = units_of(m.nz[ln]);
+                    if ((int)blockIdx.x < Pn && (int)blockIdx.x < nqn) {
+                        const Tv *facn = mixed ? (const Tv *)m.fac32[ln] : (const Tv *)m.fac64[ln];
+                        const int q = blockIdx.x;
+                        copy_async(R0, facn + (size_t)(2 * q) * FE, FE * (int)sizeof(Tv), tid, nt);
+                        if (lay.pair && (m.nz[ln] - 3) / 2 >= 1)
+                            copy_async(R1, facn + (size_t)(2 * q + 2) * FE, FE * (int)sizeof(Tv), tid, nt);
+                        have = true;
+                    }
+                    copy_commit();
+                }
             }
-        }
-        if (mixed) {
-            const float *du = m.u32[0];
-            for (int k = blockIdx.x * blockDim.x + tid; k < ng; k += gridDim.x * blockDim.x) {
-                const int i = k / nr, j = k % nr;
-                if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] += (double)du[k];
+            // levels in the group alone are separated by the group barrier;
+            // every other level boundary is a grid barrier
+            bool ok;
+            if (l > 0 && grp && l - 1 >= lb)
+                ok = in_group ? count_barrier(&ctl->gbar_count.v, (++ngroup) * G, ctl) : true;
+            else
+                ok = count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl);
+            if (!ok) {
+                copy_wait_all();
+                return;
             }
-            if (!grid_barrier(ctl, gridDim.x)) return;
         }
     }
 }
 
 // kernels whose dynamic shared memory can pass 48 KB on the largest meshes
+constexpr size_t kSolveSmemLimit = 220 * 1024;
+
 void raise_smem_limits() {
     static bool done = false;
     if (done) return;
-    const int lim = 220 * 1024;
+    const int lim = (int)kSolveSmemLimit;
     cudaFuncSetAttribute(k_factor_levels<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_factor_levels<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_chi_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -933,6 +1058,11 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(rho, m.f0, phi, phi_zL, V, nz, nr, fd.dz, fd.dr,
                                                warm ? 0 : 1);
     ++L;
+    // the level-0 correction starts at zero and stays zero on the boundary
+    if (mixed)
+        cudaMemsetAsync(m.u32[0], 0, sizeof(float) * ng, st);
+    else
+        cudaMemsetAsync(m.u64[0], 0, sizeof(double) * ng, st);
     MGCtl c0;
     memset(&c0, 0, sizeof(c0));
     c0.tol = tol;
@@ -940,28 +1070,62 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     cudaMemcpyAsync(m.ctl, &c0, sizeof(MGCtl), cudaMemcpyHostToDevice, st);
     // one cooperative launch for all cycles when the blocks fit on the GPU
     {
-        const size_t fbytes_v = (size_t)(2 * K + 1) * n * (mixed ? sizeof(float) : sizeof(double));
-        const size_t fbytes_d = (size_t)(2 * K + 1) * n * sizeof(double);
-        const size_t dbytes = 2 * (size_t)n * sizeof(double);
-        int dbl = dbytes + std::max(2 * fbytes_v, fbytes_d) <= 200 * 1024 ? 1 : 0;
-        const size_t sline = dbytes + (dbl ? std::max(2 * fbytes_v, fbytes_d) : fbytes_d);
-        const size_t schainp = (size_t)kChainWarps * 2 * nz * sizeof(double);
-        const size_t sp = std::max(sline, schainp);
-        int dev = 0, nsm = 0, per_sm = 0;
+        int dev = 0, nsm = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (mixed)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<float>, lt, sp);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<double>, lt, sp);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t limit = std::min<size_t>((size_t)std::max(optin - 2048, 0), kSolveSmemLimit);
+        SolveLayout lay{};
+        size_t sp = 0;
+        bool found = false;
+        const size_t es = mixed ? sizeof(float) : sizeof(double);
+        const size_t FE = (size_t)(2 * K + 1) * n;
+        // richest layout first: both reds at once, black factors and the
+        // residual tile in their own space; then less overlap, then one red
+        // line at a time
+        for (int v = 0; v < 6 && !found; ++v) {
+            const int pair = v < 3;
+            const int mode = v % 3;  // 0: separate B and T, 1: separate T, 2: T over R
+            if (pair && 2 * lt > 1024) continue;
+            size_t off = 0;
+            auto take = [&](size_t b) {
+                const size_t o = off;
+                off += (b + 15) & ~(size_t)15;
+                return (int)o;
+            };
+            lay.tw = 8;
+            lay.lt = lt;
+            lay.pair = pair;
+            lay.offD = take((size_t)(pair ? 2 : 1) * 2 * n * sizeof(double));
+            lay.offX = take((size_t)2 * n * es);
+            const size_t Tb = (size_t)2 * lay.tw * nz * sizeof(double);
+            size_t Rb = std::max((size_t)(pair ? 2 : 1) * FE * es, FE * sizeof(double));
+            if (mode == 2) Rb = std::max(Rb, Tb);
+            lay.offR0 = take(Rb);
+            lay.offR1 = pair ? lay.offR0 + (int)(FE * es) : lay.offR0;
+            lay.offB = mode == 0 ? take(FE * es) : lay.offR0;
+            lay.offT = mode == 2 ? lay.offR0 : take(Tb);
+            sp = off;
+            found = sp <= limit;
+        }
+        const int threads = lay.pair ? 2 * lt : lt;
+        int per_sm = 0;
+        if (found) {
+            if (mixed)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<float>, threads, sp);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<double>, threads, sp);
+        }
         const int grid = std::max(1, std::min(std::min(nsm, nsm * per_sm), (nz - 1) / 2));
-        if (grid >= 1 && per_sm >= 1) {
+        if (found && per_sm >= 1) {
             int first_cycle = 1;
             int Kv = K, nrv = nr;
             void *args[] = {(void *)&mp, (void *)&phi, (void *)&nrv, (void *)&Kv, (void *)&first_cycle,
-                            (void *)&dbl};
-            cudaError_t e = mixed ? cudaLaunchCooperativeKernel((void *)k_solve_persistent<float>, grid, lt, args, sp, st)
-                                  : cudaLaunchCooperativeKernel((void *)k_solve_persistent<double>, grid, lt, args, sp, st);
+                            (void *)&lay};
+            cudaError_t e = mixed ? cudaLaunchCooperativeKernel((void *)k_solve_persistent<float>, grid, threads,
+                                                                args, sp, st)
+                                  : cudaLaunchCooperativeKernel((void *)k_solve_persistent<double>, grid, threads,
+                                                                args, sp, st);
             ++L;
             if (e == cudaSuccess) {
                 MGCtl ch;

@@ -14,16 +14,14 @@ struct MGCtl {
     unsigned int blocks_in;
     int done, converged, zero_rhs, cycles, max_cycles, timeout;
     double tol, last_res, bnorm;
-    // two-level grid barrier of the one-launch solve: a counter per group of
-    // blocks, a top counter over the groups and the generation that waiting
-    // blocks poll, each on its own cache line
+    // barrier counters of the one-launch solve (whole grid; the coarse
+    // levels' group of blocks), each on its own cache line
     struct alignas(128) Line {
         unsigned int v;
         unsigned int pad[31];
     };
-    Line bar_group[32];
-    Line bar_top;
-    Line bar_gen;
+    Line bar_count;
+    Line gbar_count;
 };
 
 // returned by mg_fast_solve when a bounded device wait gave up
@@ -38,8 +36,10 @@ struct MGFast {
     double dz[kMaxLevels];
     double *chi[kMaxLevels], *cz[kMaxLevels], *cr[kMaxLevels];
     float *cz32[kMaxLevels], *cr32[kMaxLevels];
-    double *u64[kMaxLevels], *f64[kMaxLevels];  // FP64 V-cycle, levels >= 1
-    float *u32[kMaxLevels], *f32[kMaxLevels];   // FP32 V-cycle (mixed), levels >= 0
+    // V-cycle correction and right-hand side per level (level 0: the
+    // correction of phi and the residual), FP64 path / FP32 (mixed) path
+    double *u64[kMaxLevels], *f64[kMaxLevels];
+    float *u32[kMaxLevels], *f32[kMaxLevels];
     double *fac64[kMaxLevels];                  // line factors, FP64 path
     float *fac32[kMaxLevels];                   // line factors, FP32 V-cycle
     double *facc;                               // coarsest level's line factors (FP64)

@@ -408,7 +408,7 @@ void setup_device(pic_handle *h) {
             m.cr32[l] = (float *)dalloc(h, g * sizeof(float));
             m.u32[l] = (float *)dalloc(h, g * sizeof(float));
             m.f32[l] = (float *)dalloc(h, g * sizeof(float));
-        } else if (l > 0) {
+        } else {
             m.u64[l] = (double *)dalloc(h, g * sizeof(double));
             m.f64[l] = (double *)dalloc(h, g * sizeof(double));
         }
