@@ -1,24 +1,25 @@
 // mg.cu -- the multigrid field solve of the timestep (Sec. 2.5, Algorithm 1),
-// arranged for few launches and little FP64 work on GB300.
+// arranged for one launch and little FP64 work on GB300.
 //
-// Same method as the reference GPU multigrid in field.cu (and as the
-// oracle): finite-volume operator, z-only coarsening, V(0,1) cycles with a
-// red-black r-line sweep per level on the way up, [1/2 1 1/2] restriction
-// of volume-integrated residuals, linear prolongation in z.  What changes is
-// the arrangement:
-//  - the parallel-cyclic-reduction elimination factors of every r-line of
-//    every level are computed once per solve (the line matrices do not
-//    change between cycles); a line sweep is then two FMAs per unknown and
-//    step;
-//  - one kernel computes the fine residual and runs the whole restriction
-//    chain down one column per warp (restriction acts in z only);
+// Same method as the oracle and as the reference GPU multigrid in field.cu:
+// finite-volume operator, z-only coarsening, V(0,1) cycles with a red-black
+// r-line sweep per level on the way up, [1/2 1 1/2] restriction of
+// volume-integrated residuals, linear prolongation in z.  What changes is the
+// arrangement:
+//  - every r-line of every level is factored once per solve (the line
+//    matrices do not change between cycles) for a warp-level solver: Thomas
+//    on a chunk of the line per lane, the chunks' interface unknowns by
+//    parallel cyclic reduction over the lanes;
+//  - the whole solve is one cooperative launch: the residual and the
+//    restriction chain run over tiles of columns, convergence is decided on
+//    the device, and a block sweeps one black line with the two red lines
+//    beside it, so one barrier separates two levels;
 //  - prolongation is folded into the red sweep: red (odd) rows are
 //    recomputed whole by their line solve, so only the injection of the
 //    coarse correction into the black (even) neighbour rows is ever used;
-//  - convergence is decided on the device: the last block of the residual
-//    kernel compares max|r| with tol max|b| and raises a done flag that
-//    turns the remaining kernels of a batch into no-ops, so the host reads
-//    back once per batch of cycles.
+//  - the cycle works on the correction of phi; the mixed path keeps the
+//    correction, the coarse right-hand sides and the line factors in FP32
+//    and the residual in FP64 (iterative refinement).
 #include <math.h>
 #include <string.h>
 
@@ -33,10 +34,6 @@ namespace {
 // bit pattern of |x|: ordered like |x| for numbers, above them for a NaN
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
-}
-
-__device__ __forceinline__ void atomic_max_pos(unsigned long long *dst, double v) {
-    atomicMax(dst, (unsigned long long)__double_as_longlong(v));
 }
 
 // ---- set-up ----
@@ -113,18 +110,44 @@ __device__ __forceinline__ double recip(double x) {
     return r;
 }
 
-// PCR elimination factors, one r-line per block, over the lines of levels
-// [l0, l1).  Line system for row i: lower -d_j = -cr[i][j-1] (0 on the
-// axis), diagonal a+c+d+e, upper -e_j = -cr[i][j] (0 on the last unknown).
-// Step s = 2^k combines equation j with j -/+ s: alpha = -lo_j / diag_{j-s},
-// gamma = -up_j / diag_{j+s}.  Stored per line: [k][alpha(n), gamma(n)] for
-// k < K, then 1/diag (n).
+// ---- r-line factors for the warp line solve ----
+//
+// Line system of row i: lo_j x_{j-1} + dg_j x_j + up_j x_{j+1} = b_j with
+// lo_j = -cr[i][j-1] (0 on the axis), dg_j = a + c + d + e, up_j = -cr[i][j]
+// (0 on the last unknown).  One warp solves a line: lane p owns the chunk
+// j = pM .. pM + M - 1 (unknowns past n are x = 0 rows).  The chunk's last
+// unknown is its interface I_p; the M - 1 interior unknowns are
+//     y = z + I_{p-1} v + I_p w,
+// z the interior solution with zero neighbours (Thomas), v and w the
+// responses to the two neighbouring interfaces.  Substituting into the
+// interface equations leaves a tridiagonal system in I_0..I_31, which the
+// warp reduces by parallel cyclic reduction over lanes (shuffles).  Only the
+// right-hand side changes between cycles, so all of this except the
+// right-hand-side sweeps is computed once per solve.  Per line the factors
+// are, lane-minor ([arr][k][32]):
+//   ell (forward multipliers), invd (1/pivot), cp (up * invd), v, w
+//   (5 arrays of M), then loI, upI (interface couplings), the five PCR
+//   steps' alpha and gamma, and 1/diagonal of the reduced system.
+constexpr int kLine = 32;  // lanes per line
+
+__host__ __device__ constexpr int line_factor_elems(int M) { return 5 * M * kLine + 2 * kLine + 10 * kLine + kLine; }
+
+// chunk per lane: the least power of two M with 32 M >= n
+inline int line_chunk(int n) {
+    int M = 1;
+    while (kLine * M < n) M <<= 1;
+    return M;
+}
+
+// One warp per line over all lines of levels [l0, l1).  Computed in Ts.
 template <typename Ts>
-__global__ void k_factor_levels(const MGFast *__restrict__ mp, int l0, int l1, int nr, int K) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void k_factor_lines(const MGFast *__restrict__ mp, int l0, int l1, int nr, int M, int nlines) {
     const MGFast &m = *mp;
     const int n = nr - 1;
-    int g = blockIdx.x, l = l0;
+    const int p = threadIdx.x & 31;
+    int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= nlines) return;
+    int l = l0;
     while (l < l1 && g >= m.nz[l] - 2) {
         g -= m.nz[l] - 2;
         ++l;
@@ -134,50 +157,142 @@ __global__ void k_factor_levels(const MGFast *__restrict__ mp, int l0, int l1, i
     const Ts *cz = f64 ? (const Ts *)m.cz[l] : (const Ts *)m.cz32[l];
     const Ts *cr = f64 ? (const Ts *)m.cr[l] : (const Ts *)m.cr32[l];
     Ts *fac = (l == m.nlev - 1) ? (Ts *)m.facc : (f64 ? (Ts *)m.fac64[l] : (Ts *)m.fac32[l]);
-    Ts *A = reinterpret_cast<Ts *>(smem_raw);
-    Ts *B = A + n, *C = B + n, *A2 = C + n, *B2 = A2 + n, *C2 = B2 + n, *IB = C2 + n;
-    const int i = 1 + g;  // interior row
-    const size_t rowk = (size_t)i * nr;
-    Ts *f = fac + (size_t)g * (2 * K + 1) * n;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const size_t k = rowk + j;
-        const Ts a = cz[k - nr], c = cz[k], e = cr[k];
-        const Ts d = j > 0 ? cr[k - 1] : (Ts)0;
-        A[j] = -d;
-        B[j] = a + c + d + e;
-        C[j] = j < n - 1 ? -e : (Ts)0;
-    }
-    __syncthreads();
-    int step = 0;
-    for (int s = 1; s < n; s <<= 1, ++step) {
-        for (int j = threadIdx.x; j < n; j += blockDim.x) IB[j] = recip(B[j]);
-        __syncthreads();
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const Ts a = A[j], c = C[j];
-            Ts b = B[j], na = 0, nc = 0, al = 0, ga = 0;
-            if (j - s >= 0) {
-                al = -a * IB[j - s];
-                na = al * A[j - s];
-                b += al * C[j - s];
-            }
-            if (j + s < n) {
-                ga = -c * IB[j + s];
-                nc = ga * C[j + s];
-                b += ga * A[j + s];
-            }
-            A2[j] = na;
-            B2[j] = b;
-            C2[j] = nc;
-            f[(size_t)(2 * step) * n + j] = al;
-            f[(size_t)(2 * step + 1) * n + j] = ga;
+    Ts *F = fac + (size_t)g * line_factor_elems(M);
+    const size_t rowk = (size_t)(1 + g) * nr;
+    auto coef = [&](int k, Ts &lo, Ts &dg, Ts &up) {
+        const int j = p * M + k;
+        if (j >= n) {
+            lo = 0;
+            dg = 1;
+            up = 0;
+            return;
         }
-        __syncthreads();
-        Ts *t;
-        t = A; A = A2; A2 = t;
-        t = B; B = B2; B2 = t;
-        t = C; C = C2; C2 = t;
+        const size_t q = rowk + j;
+        const Ts a = cz[q - nr], c = cz[q], e = cr[q];
+        const Ts d = j > 0 ? cr[q - 1] : (Ts)0;
+        lo = -d;
+        dg = a + c + d + e;
+        up = j < n - 1 ? -e : (Ts)0;
+    };
+    auto at = [&](int arr, int k) -> Ts & { return F[((size_t)arr * M + k) * kLine + p]; };
+    const int MI = M - 1;
+    Ts A, B, C;  // reduced (interface) equation of this lane
+    Ts loI, dgI, upI;
+    coef(M - 1, loI, dgI, upI);
+    if (MI > 0) {
+        // interior Thomas factors
+        Ts lo, dg, up, upm = 0, invd = 0;
+        for (int k = 0; k < MI; ++k) {
+            coef(k, lo, dg, up);
+            Ts ell = 0, d = dg;
+            if (k > 0) {
+                ell = lo * invd;
+                d = dg - ell * upm;
+            }
+            invd = recip(d);
+            at(0, k) = ell;
+            at(1, k) = invd;
+            at(2, k) = up * invd;
+            upm = up;
+        }
+        // spikes: v answers -lo_0 at the first interior unknown, w answers
+        // -up_{MI-1} at the last (forward sweep, then backward)
+        Ts lo0, dg0, up0;
+        coef(0, lo0, dg0, up0);
+        Ts vp = -lo0;
+        at(3, 0) = vp;
+        for (int k = 1; k < MI; ++k) {
+            vp = -at(0, k) * vp;
+            at(3, k) = vp;
+        }
+        Ts loL, dgL, upL;
+        coef(MI - 1, loL, dgL, upL);
+        Ts vn = at(3, MI - 1) * at(1, MI - 1), wn = -upL * at(1, MI - 1);
+        at(3, MI - 1) = vn;
+        at(4, MI - 1) = wn;
+        for (int k = MI - 2; k >= 0; --k) {
+            vn = at(3, k) * at(1, k) - at(2, k) * vn;
+            wn = -at(2, k) * wn;
+            at(3, k) = vn;
+            at(4, k) = wn;
+        }
+        const Ts v0n = __shfl_down_sync(0xffffffffu, at(3, 0), 1);
+        const Ts w0n = __shfl_down_sync(0xffffffffu, at(4, 0), 1);
+        const Ts vL = at(3, MI - 1), wL = at(4, MI - 1);
+        A = loI * vL;
+        B = dgI + loI * wL + (p < kLine - 1 ? upI * v0n : (Ts)0);
+        C = p < kLine - 1 ? upI * w0n : (Ts)0;
+    } else {
+        A = loI;
+        B = dgI;
+        C = upI;
     }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) f[(size_t)(2 * K) * n + j] = recip(B[j]);
+    Ts *Gf = F + (size_t)5 * M * kLine;
+    Gf[p] = loI;
+    Gf[kLine + p] = upI;
+    // parallel cyclic reduction of the interface system over the lanes
+    for (int st = 0; st < 5; ++st) {
+        const int s = 1 << st;
+        const Ts Bm = __shfl_up_sync(0xffffffffu, B, s), Bp = __shfl_down_sync(0xffffffffu, B, s);
+        const Ts Am = __shfl_up_sync(0xffffffffu, A, s), Ap = __shfl_down_sync(0xffffffffu, A, s);
+        const Ts Cm = __shfl_up_sync(0xffffffffu, C, s), Cp = __shfl_down_sync(0xffffffffu, C, s);
+        Ts al = 0, ga = 0;
+        if (p >= s) al = -A * recip(Bm);
+        if (p + s < kLine) ga = -C * recip(Bp);
+        Gf[2 * kLine + st * kLine + p] = al;
+        Gf[7 * kLine + st * kLine + p] = ga;
+        const Ts nB = B + (p >= s ? al * Cm : (Ts)0) + (p + s < kLine ? ga * Ap : (Ts)0);
+        A = p >= s ? al * Am : (Ts)0;
+        C = p + s < kLine ? ga * Cp : (Ts)0;
+        B = nB;
+    }
+    Gf[12 * kLine + p] = recip(B);
+}
+
+// Warp solve of one line with factors F (shared memory): right-hand side in
+// Bs and solution out to the same place, both [k * 33 + p] (lane-minor with
+// a pad against bank conflicts).  All 32 lanes take part.
+constexpr int kRow = 33;
+
+template <typename Ts, int M>
+__device__ __forceinline__ void warp_line_solve(const Ts *__restrict__ F, Ts *Bs, int p) {
+    constexpr int MI = M - 1;
+    const Ts *Gf = F + 5 * M * kLine;
+    Ts r;
+    Ts z[MI > 0 ? MI : 1];
+    if constexpr (MI > 0) {
+        Ts zp = Bs[p];
+        z[0] = zp;
+#pragma unroll
+        for (int k = 1; k < MI; ++k) {
+            zp = Bs[k * kRow + p] - F[(0 * M + k) * kLine + p] * zp;
+            z[k] = zp;
+        }
+        Ts zn = z[MI - 1] * F[(1 * M + MI - 1) * kLine + p];
+        z[MI - 1] = zn;
+#pragma unroll
+        for (int k = MI - 2; k >= 0; --k) {
+            zn = z[k] * F[(1 * M + k) * kLine + p] - F[(2 * M + k) * kLine + p] * zn;
+            z[k] = zn;
+        }
+        const Ts z0n = __shfl_down_sync(0xffffffffu, z[0], 1);
+        r = Bs[(M - 1) * kRow + p] - Gf[p] * z[MI - 1] - Gf[kLine + p] * (p < kLine - 1 ? z0n : (Ts)0);
+    } else {
+        r = Bs[p];
+    }
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int s = 1 << st;
+        const Ts rm = __shfl_up_sync(0xffffffffu, r, s), rp = __shfl_down_sync(0xffffffffu, r, s);
+        r = r + Gf[(2 + st) * kLine + p] * rm + Gf[(7 + st) * kLine + p] * rp;
+    }
+    const Ts I = r * Gf[12 * kLine + p];
+    if constexpr (MI > 0) {
+        const Ts Ip = __shfl_up_sync(0xffffffffu, I, 1);  // lane 0: v is zero there
+#pragma unroll
+        for (int k = 0; k < MI; ++k) Bs[k * kRow + p] = z[k] + F[(3 * M + k) * kLine + p] * Ip + F[(4 * M + k) * kLine + p] * I;
+    }
+    Bs[(M - 1) * kRow + p] = I;
 }
 
 // right-hand side rho A_j dz / eps0 and the Dirichlet data of phi
@@ -202,303 +317,6 @@ __global__ void k_rhs_bc(const double *rho, double *f0, double *phi, const doubl
         phi[k] = 0.0;
 }
 
-// ---- the PCR line solve with precomputed factors (block per line) ----
-// One unknown per thread (n <= blockDim <= 1024).  A thread first loads all
-// its factors into registers -- independent loads, one memory round trip --
-// so the K reduction steps touch only shared memory.
-constexpr int kMaxK = 10;  // n <= 1024
-
-template <typename Ts>
-struct LineFac {
-    Ts f[2 * kMaxK + 1];
-};
-
-template <typename Ts>
-__device__ __forceinline__ LineFac<Ts> load_fac(const Ts *fac, int n, int K, int j) {
-    LineFac<Ts> r;
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-        r.f[2 * k] = (k < K && j < n) ? fac[(size_t)(2 * k) * n + j] : (Ts)0;
-        r.f[2 * k + 1] = (k < K && j < n) ? fac[(size_t)(2 * k + 1) * n + j] : (Ts)0;
-    }
-    r.f[2 * kMaxK] = j < n ? fac[(size_t)(2 * K) * n + j] : (Ts)0;
-    return r;
-}
-
-// d = this thread's right-hand side; returns the solution of unknown j
-template <typename Ts>
-__device__ __forceinline__ Ts pcr_solve(Ts d, Ts *D, Ts *D2, const LineFac<Ts> &fr, int n, int K) {
-    const int j = threadIdx.x;
-    if (j < n) D[j] = d;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-        if (k < K) {
-            const int s = 1 << k;
-            if (j < n) {
-                Ts v = D[j];
-                if (j - s >= 0) v += fr.f[2 * k] * D[j - s];
-                if (j + s < n) v += fr.f[2 * k + 1] * D[j + s];
-                D2[j] = v;
-                d = v;
-            }
-            __syncthreads();
-            Ts *t = D;
-            D = D2;
-            D2 = t;
-        }
-    }
-    return d * fr.f[2 * kMaxK];
-}
-
-// ---- per-cycle kernels ----
-
-// r = f - A phi on the fine level (FP64, all SMs), its max norm, and on the
-// first cycle max|b|; the mixed path also keeps r in FP32 as its level-0
-// right-hand side.  The last block decides convergence.
-__global__ void k_resid(const MGFast *__restrict__ mp, int nr, const double *phi, int first) {
-    const MGFast &m = *mp;
-    MGCtl *ctl = m.ctl;
-    if (ctl->done) return;
-    const int nz = m.nz[0], ng = nz * nr;
-    const double *cz = m.cz[0], *cr = m.cr[0];
-    double rmax = 0.0, bmax = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
-        const int i = k / nr, j = k % nr;
-        double r = 0.0;
-        if (i > 0 && i < nz - 1 && j < nr - 1) {
-            const double a = cz[k - nr], c = cz[k], e = cr[k], d = j > 0 ? cr[k - 1] : 0.0;
-            double Au = (a + c + d + e) * phi[k] - a * phi[k - nr] - c * phi[k + nr] - e * phi[k + 1];
-            if (j > 0) Au -= d * phi[k - 1];
-            r = m.f0[k] - Au;
-            rmax = fmax(rmax, fabs(r));
-            if (first) {
-                double b = m.f0[k];
-                if (i == 1) b += a * phi[k - nr];
-                if (i == nz - 2) b += c * phi[k + nr];
-                if (j == nr - 2) b += e * phi[k + 1];
-                bmax = fmax(bmax, fabs(b));
-            }
-        }
-        m.r[k] = r;
-        if (m.f32[0]) m.f32[0][k] = (float)r;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-    }
-    __shared__ double s_r[32], s_b[32];
-    __shared__ bool s_last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_r[warp] = rmax;
-        s_b[warp] = bmax;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double r = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            r = fmax(r, s_r[w]);
-            b = fmax(b, s_b[w]);
-        }
-        atomic_max_pos(&ctl->res_bits, r);
-        if (first) atomic_max_pos(&ctl->b_bits, b);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->blocks_in, 1u);
-        s_last = prev == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        const double rn = __longlong_as_double((long long)atomicAdd(&ctl->res_bits, 0ull));
-        const double bn = __longlong_as_double((long long)atomicAdd(&ctl->b_bits, 0ull));
-        ctl->last_res = rn;
-        ctl->bnorm = bn;
-        bool done = false;
-        if (bn == 0.0) {
-            done = true;
-            ctl->zero_rhs = 1;
-        } else if (ctl->tol > 0.0 && rn <= ctl->tol * bn) {
-            done = true;
-            ctl->converged = 1;
-        } else if (ctl->cycles >= ctl->max_cycles) {
-            done = true;
-            ctl->converged = ctl->tol > 0.0 ? 0 : 1;
-        }
-        ctl->res_bits = 0ull;
-        ctl->blocks_in = 0u;
-        if (done)
-            ctl->done = 1;
-        else
-            ctl->cycles += 1;
-    }
-}
-
-// restriction chain, one lane per column j < nr-1: level values go through
-// shared memory laid out [row][lane]; each level is
-// f_{l+1}[I] = f_l[2I-1]/2 + f_l[2I] + f_l[2I+1]/2 on interior rows
-template <typename Tv>
-__global__ void k_chain(const MGFast *__restrict__ mp, int nr) {
-    const MGFast &m = *mp;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (m.ctl->done) return;
-    const int lane = threadIdx.x;
-    const int j = blockIdx.x * 32 + lane;
-    const int n1 = m.nz[1], nz0 = m.nz[0];
-    double *col = reinterpret_cast<double *>(smem_raw);      // [nz0][32]
-    Tv *bufA = reinterpret_cast<Tv *>(col + (size_t)nz0 * 32);  // [n1][32]
-    Tv *bufB = bufA + (size_t)n1 * 32;
-    const bool on = j < nr - 1;
-    // the column of the fine residual: independent loads, then compute
-    {
-        const double *__restrict__ r = m.r;
-        for (int i = 0; i < nz0; ++i) col[i * 32 + lane] = on ? r[(size_t)i * nr + j] : 0.0;
-    }
-    for (int I = 0; I < n1; ++I) {
-        Tv v = 0;
-        if (I > 0 && I < n1 - 1)
-            v = (Tv)(0.5 * col[(2 * I - 1) * 32 + lane] + col[(2 * I) * 32 + lane] +
-                     0.5 * col[(2 * I + 1) * 32 + lane]);
-        bufA[I * 32 + lane] = v;
-        if (on) {
-            const size_t k = (size_t)I * nr + j;
-            if (m.nlev == 2)
-                m.fc64[k] = (double)v;
-            else if (sizeof(Tv) == 8)
-                m.f64[1][k] = (double)v;
-            else
-                m.f32[1][k] = (float)v;
-        }
-    }
-    Tv *src = bufA, *dst = bufB;
-    for (int l = 2; l < m.nlev; ++l) {
-        const int nzc = m.nz[l];
-        for (int I = 0; I < nzc; ++I) {
-            Tv v = 0;
-            if (I > 0 && I < nzc - 1)
-                v = (Tv)0.5 * src[(2 * I - 1) * 32 + lane] + src[(2 * I) * 32 + lane] +
-                    (Tv)0.5 * src[(2 * I + 1) * 32 + lane];
-            dst[I * 32 + lane] = v;
-            if (on) {
-                const size_t k = (size_t)I * nr + j;
-                if (l == m.nlev - 1)
-                    m.fc64[k] = (double)v;
-                else if (sizeof(Tv) == 8)
-                    m.f64[l][k] = (double)v;
-                else
-                    m.f32[l][k] = (float)v;
-            }
-        }
-        Tv *t = src;
-        src = dst;
-        dst = t;
-    }
-}
-
-// coarsest level: one interior row, FP64 factors, result stored in the
-// V-cycle's type
-template <typename Tv>
-__global__ void k_coarse(const MGFast *__restrict__ mp, int nr, int K) {
-    const MGFast &m = *mp;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (m.ctl->done) return;
-    const int n = nr - 1, L = m.nlev - 1, j = threadIdx.x;
-    double *D = reinterpret_cast<double *>(smem_raw);
-    const LineFac<double> fr = load_fac(m.facc, n, K, j);
-    const double rhs = j < n ? m.fc64[(size_t)nr + j] : 0.0;
-    const double x = pcr_solve<double>(rhs, D, D + n, fr, n, K);
-    Tv *u = sizeof(Tv) == 8 ? (Tv *)m.u64[L] : (Tv *)m.u32[L];
-    if (j < n) u[(size_t)nr + j] = (Tv)x;
-}
-
-// Red sweep of level l with the prolongation folded in: row i (odd) solves
-// with neighbours u_old[i-/+1] + injected coarse correction (even rows are
-// coarse rows (i-/+1)/2).  Level 0 of the FP64 path works on phi itself
-// (u_old = phi, Dirichlet values read from phi); every other level works on
-// a correction that starts at zero with zero Dirichlet values.
-template <typename Tv>
-__global__ void k_red(const MGFast *__restrict__ mp, int l, int nr, int K, Tv *u, const Tv *uc, const Tv *f,
-                      const Tv *cz, const Tv *cr, const Tv *fac, int on_phi) {
-    const MGFast &m = *mp;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (m.ctl->done) return;
-    const int n = nr - 1, nz = m.nz[l], nzc = m.nz[l + 1], j = threadIdx.x;
-    Tv *D = reinterpret_cast<Tv *>(smem_raw);
-    const int i = 1 + 2 * blockIdx.x;
-    const size_t rowk = (size_t)i * nr;
-    const LineFac<Tv> fr = load_fac(fac + (size_t)(i - 1) * (2 * K + 1) * n, n, K, j);
-    Tv rhs = 0;
-    if (j < n) {
-        const int Idn = (i - 1) / 2, Iup = (i + 1) / 2;
-        const size_t k = rowk + j;
-        Tv udn, uup;
-        if (i - 1 == 0)
-            udn = on_phi ? u[k - nr] : (Tv)0;
-        else
-            udn = (on_phi ? u[k - nr] : (Tv)0) + ((Idn > 0 && Idn < nzc - 1) ? uc[(size_t)Idn * nr + j] : (Tv)0);
-        if (i + 1 == nz - 1)
-            uup = on_phi ? u[k + nr] : (Tv)0;
-        else
-            uup = (on_phi ? u[k + nr] : (Tv)0) + ((Iup > 0 && Iup < nzc - 1) ? uc[(size_t)Iup * nr + j] : (Tv)0);
-        rhs = f[k] + cz[k - nr] * udn + cz[k] * uup;
-        if (j == n - 1 && on_phi) rhs += cr[k] * u[k + 1];
-    }
-    const Tv x = pcr_solve<Tv>(rhs, D, D + n, fr, n, K);
-    if (j < n) u[rowk + j] = x;
-}
-
-// Black sweep: row i (even, interior) solves with the new red rows i-/+1.
-template <typename Tv>
-__global__ void k_black(const MGFast *__restrict__ mp, int l, int nr, int K, Tv *u, const Tv *f, const Tv *cz,
-                        const Tv *cr, const Tv *fac, int on_phi) {
-    const MGFast &m = *mp;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (m.ctl->done) return;
-    const int n = nr - 1, j = threadIdx.x;
-    Tv *D = reinterpret_cast<Tv *>(smem_raw);
-    const int i = 2 + 2 * blockIdx.x;
-    const size_t rowk = (size_t)i * nr;
-    const LineFac<Tv> fr = load_fac(fac + (size_t)(i - 1) * (2 * K + 1) * n, n, K, j);
-    Tv rhs = 0;
-    if (j < n) {
-        const size_t k = rowk + j;
-        rhs = f[k] + cz[k - nr] * u[k - nr] + cz[k] * u[k + nr];
-        if (j == n - 1 && on_phi) rhs += cr[k] * u[k + 1];
-    }
-    const Tv x = pcr_solve<Tv>(rhs, D, D + n, fr, n, K);
-    if (j < n) u[rowk + j] = x;
-}
-
-// mixed path: phi += delta on interior nodes
-__global__ void k_correct(const MGFast *__restrict__ mp, double *phi, const float *du, int nz, int nr) {
-    const MGFast &m = *mp;
-    if (m.ctl->done) return;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nz * nr) return;
-    const int i = k / nr, j = k % nr;
-    if (i == 0 || i == nz - 1 || j == nr - 1) return;
-    phi[k] += (double)du[k];
-}
-
-// nz = 3: the one interior row of phi solved exactly with the fine right-hand side
-__global__ void k_single_row(const MGFast *__restrict__ mp, double *phi, int nr, int K) {
-    const MGFast &m = *mp;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (m.ctl->done) return;
-    const int n = nr - 1, j = threadIdx.x;
-    double *D = reinterpret_cast<double *>(smem_raw);
-    const LineFac<double> fr = load_fac(m.facc, n, K, j);
-    double rhs = 0.0;
-    if (j < n) {
-        const double *cz = m.cz[0], *cr = m.cr[0];
-        const size_t k = (size_t)nr + j;
-        rhs = m.f0[k] + cz[k - nr] * phi[k - nr] + cz[k] * phi[k + nr];
-        if (j == n - 1) rhs += cr[k] * phi[k + 1];
-    }
-    const double x = pcr_solve<double>(rhs, D, D + n, fr, n, K);
-    if (j < n) phi[(size_t)nr + j] = x;
-}
-
 // ---------------------------------------------------------------------------
 // The whole solve in one cooperative launch.  Blocks are co-resident (the
 // launch guarantees it), and phases are separated by a grid barrier whose
@@ -510,11 +328,11 @@ __global__ void k_single_row(const MGFast *__restrict__ mp, double *phi, int nr,
 //   2. convergence decision (every block reads the same maxima), then
 //      phi += delta;
 //   3. up the levels, one phase per level: the block owning black line
-//      i = 2q + 2 solves the red lines 2q + 1 and 2q + 3 beside it (the two
-//      halves of the block at once when they fit), keeps them in shared
-//      memory and solves the black line.  A red line shared by two blocks is
-//      computed by both from the same data, bit for bit, and stored by one.
-//      So one barrier separates two levels instead of two.
+//      i = 2q + 2 solves the red lines 2q + 1 and 2q + 3 beside it (two
+//      warps at once), keeps them in shared memory and solves the black
+//      line.  A red line shared by two blocks is computed by both from the
+//      same data, bit for bit, and stored by one.  So one barrier separates
+//      two levels instead of two.
 // The coarsest row is solved by block 0 in the phase of level L-1, which
 // block 0 sweeps alone.  Levels with at most kBarGroup black lines belong to
 // the first kBarGroup blocks, separated by a barrier among those blocks only;
@@ -561,111 +379,128 @@ __device__ __forceinline__ bool count_barrier(unsigned *count, unsigned target, 
     return s_ok != 0;
 }
 
-// Asynchronous copy of `bytes` (a multiple of the element size) from global
-// to shared memory by threads t = 0..nt-1 of the block: 16-byte pieces when
-// both ends and the length allow it, else 8- or 4-byte pieces.  The caller
-// commits the group.
-__device__ __forceinline__ void copy_async(void *dst, const void *src, int bytes, int t, int nt) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const char *s = static_cast<const char *>(src);
-    const unsigned long long a = (unsigned long long)s | d | (unsigned)bytes;
-    if ((a & 15) == 0) {
-        for (int o = t * 16; o < bytes; o += nt * 16)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + o), "l"(s + o) : "memory");
-    } else if ((a & 7) == 0) {
-        for (int o = t * 8; o < bytes; o += nt * 8)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + o), "l"(s + o) : "memory");
-    } else {
-        for (int o = t * 4; o < bytes; o += nt * 4)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + o), "l"(s + o) : "memory");
-    }
-}
-__device__ __forceinline__ void copy_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void copy_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// ---- factor lines into shared memory ----
+// A line's factors move in one bulk copy that completes on the region's
+// mbarrier (thread 0 issues it).  All threads of the block keep the same
+// state: the parity of the next completion and whether a copy is pending.
+struct Loader {
+    unsigned mbar;
+    unsigned phase;
+    int pending;
+};
 
-// PCR reduction of one line whose factors F were requested with cp.async:
-// unknown j of the line (active when act) with right-hand side d; returns
-// its solution.  Every thread of the block calls it (the two halves of a
-// block may reduce two lines at once).  keep_newest: the most recent copy
-// group may still be in flight (it belongs to a later line).
-template <typename Ts>
-__device__ __forceinline__ Ts pcr_line(Ts d, Ts *D, Ts *D2, const Ts *F, int n, int K, int j, bool act,
-                                       bool keep_newest) {
-    if (keep_newest)
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (act) D[j] = d;
-    __syncthreads();
-    int k = 0;
-    for (int s = 1; s < n; s <<= 1, ++k) {
-        if (act) {
-            Ts v = D[j];
-            if (j - s >= 0) v += F[(size_t)(2 * k) * n + j] * D[j - s];
-            if (j + s < n) v += F[(size_t)(2 * k + 1) * n + j] * D[j + s];
-            D2[j] = v;
-            d = v;
-        }
-        __syncthreads();
-        Ts *t = D;
-        D = D2;
-        D2 = t;
+__device__ __forceinline__ void ld_begin(Loader &q, unsigned bytes) {
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(q.mbar), "r"(bytes) : "memory");
     }
-    const Ts x = act ? d * F[(size_t)(2 * K) * n + j] : (Ts)0;
-    __syncthreads();  // F and D are reused by the next line
-    return x;
+    q.pending = 1;
+}
+
+// sizes and addresses are multiples of 16 bytes
+__device__ __forceinline__ void ld_copy(Loader &q, void *dst, const void *src, unsigned bytes) {
+    if (threadIdx.x == 0)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src), "r"(bytes), "r"(q.mbar)
+                     : "memory");
+}
+
+// wait for the region's copy (every thread of the block calls it); false,
+// for the whole block, when the bounded wait gave up
+__device__ __forceinline__ bool ld_wait(Loader &q) {
+    if (!q.pending) return true;
+    bool ok = false;
+    for (long long it = 0; it < kSpinLimit && !ok; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(q.mbar), "r"(q.phase)
+            : "memory");
+        ok = done != 0;
+    }
+    ok = !__syncthreads_or(!ok);
+    if (ok) {
+        q.pending = 0;
+        q.phase ^= 1u;
+    }
+    return ok;
 }
 
 // Shared-memory layout of the one-launch solve (byte offsets), set on the host.
 struct SolveLayout {
-    int offD;   // PCR scratch: per half 2n values of 8 bytes
-    int offX;   // the two red lines' solutions, kept for the black line's right-hand side
-    int offR0;  // factors of the first red line; the coarsest row's FP64 factors
-    int offR1;  // factors of the second red line (== offR0: reds one after the other)
-    int offB;   // factors of the black line (== offR0: requested after the reds)
-    int offT;   // residual / restriction tile (== offR0: no early request of the coarsest factors)
-    int tw;     // columns per residual tile
-    int lt;     // threads per line (power of two >= n)
-    int pair;   // the two halves of the block reduce the two red lines at once
+    int offBuf;  // three line buffers (right-hand side in, solution out), M * 33 values of 8 bytes each
+    int offW;    // the black line's two coupling coefficients, 32 M values of 8 bytes each
+    int offF;    // factors of the two red lines and the black line; the residual tile lies over them
+    int offC;    // factors of the coarsest row (FP64)
+    int tw;      // columns per residual tile
 };
 
 // black lines of a level with nz rows (at least one unit of work: nz = 3 has
 // a red line only)
 __device__ __forceinline__ int units_of(int nz) { return max((nz - 3) / 2, 1); }
 
-template <typename Tv>
-__global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restrict__ mp, double *phi, int nr, int K,
-                                   int first_cycle, SolveLayout lay) {
+constexpr int kSolveThreads = 256;
+
+template <typename Tv, int M>
+__global__ void __launch_bounds__(kSolveThreads, 1)
+    k_solve_persistent(const MGFast *__restrict__ mp, double *phi, int nr, int first_cycle, SolveLayout lay) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MGFast &m = *mp;
     MGCtl *ctl = m.ctl;
     const int n = nr - 1, nz0 = m.nz[0], ng = nz0 * nr, L = m.nlev - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    constexpr int NW = kLine * M;  // unknowns of a line with its padding
     const bool mixed = sizeof(Tv) == 4;
     Tv *delta = mixed ? (Tv *)m.u32[0] : (Tv *)m.u64[0];  // level-0 correction (zero on the boundary)
-    const bool cpre = lay.offT != lay.offR0;                // coarsest factors requested early
-    const bool bsep = lay.offB != lay.offR0;
-    const int FE = (2 * K + 1) * n;                         // factor elements of a line
+    constexpr int LFE = line_factor_elems(M);
+    const unsigned FBv = (unsigned)(LFE * sizeof(Tv)), FBd = (unsigned)(LFE * sizeof(double));
     // levels whose work fits in G blocks are swept by the first G blocks only
     const int G = min(kBarGroup, (int)gridDim.x);
     int lb = L;
     while (lb > 0 && units_of(m.nz[lb - 1]) <= G) --lb;
     const bool in_group = (int)blockIdx.x < G;
     __shared__ unsigned long long s_r[32], s_b[32];
+    __shared__ __align__(8) unsigned long long s_mbar[3];
     __shared__ int s_decide;
+    if (tid == 0) {
+        for (int b = 0; b < 3; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((unsigned)__cvta_generic_to_shared(&s_mbar[b]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // red factors; black factors; coarsest-row factors
+    Loader qR{(unsigned)__cvta_generic_to_shared(&s_mbar[0]), 0u, 0};
+    Loader qB{(unsigned)__cvta_generic_to_shared(&s_mbar[1]), 0u, 0};
+    Loader qC{(unsigned)__cvta_generic_to_shared(&s_mbar[2]), 0u, 0};
+    // leave with no copy in flight (bounded waits); fail: a wait gave up
+    auto leave = [&](bool fail) {
+        if (fail && tid == 0) atomicExch(&ctl->timeout, 1);
+        ld_wait(qR);
+        ld_wait(qB);
+        ld_wait(qC);
+    };
     int first = first_cycle;
     unsigned ngrid = 0, ngroup = 0;  // barriers of each kind passed
-    Tv *X = reinterpret_cast<Tv *>(smem_raw + lay.offX);
-    Tv *R0 = reinterpret_cast<Tv *>(smem_raw + lay.offR0);
-    Tv *R1 = reinterpret_cast<Tv *>(smem_raw + lay.offR1);
-    Tv *FBk = reinterpret_cast<Tv *>(smem_raw + lay.offB);
-    const int half = lay.pair ? (tid >= lay.lt) : 0;
-    const int jl = lay.pair ? tid - half * lay.lt : tid;  // unknown of this thread's line
-    Tv *Dh = reinterpret_cast<Tv *>(smem_raw + lay.offD + (size_t)half * 2 * n * sizeof(double));
+    Tv *Bf0 = reinterpret_cast<Tv *>(smem_raw + lay.offBuf);
+    Tv *Bf1 = reinterpret_cast<Tv *>(smem_raw + lay.offBuf + M * kRow * 8);
+    Tv *Bf2 = reinterpret_cast<Tv *>(smem_raw + lay.offBuf + 2 * M * kRow * 8);
+    double *BC = reinterpret_cast<double *>(smem_raw + lay.offBuf);
+    Tv *W0 = reinterpret_cast<Tv *>(smem_raw + lay.offW);
+    Tv *W1 = W0 + NW;
+    Tv *R0 = reinterpret_cast<Tv *>(smem_raw + lay.offF);
+    Tv *R1 = R0 + LFE;
+    Tv *FBk = R1 + LFE;
+    double *FC = reinterpret_cast<double *>(smem_raw + lay.offC);
+    // position of unknown j in a line buffer
+    auto at = [](int j) { return (j % M) * kRow + j / M; };
     for (int cyc = 0;; ++cyc) {
         // ---- residual of phi + delta, its norms, and the restriction chain ----
-        if (cpre && blockIdx.x == 0 && L > 0) copy_async(R0, m.facc, FE * 8, tid, nt);
-        copy_commit();
+        if (blockIdx.x == 0 && L > 0) {
+            ld_begin(qC, FBd);
+            ld_copy(qC, FC, m.facc, FBd);
+        }
         // maxima as bit patterns of |x| (ordered like the values; a NaN
         // compares above every number), so the reductions are integer work
         unsigned long long rmax = 0ull, bmax = 0ull;
@@ -673,7 +508,7 @@ __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restr
             const double *cz = m.cz[0], *cr = m.cr[0];
             const int tw = lay.tw;
             // the restriction chain runs in the V-cycle's type
-            Tv *T0 = reinterpret_cast<Tv *>(smem_raw + lay.offT);
+            Tv *T0 = reinterpret_cast<Tv *>(smem_raw + lay.offF);
             Tv *T1 = T0 + (size_t)tw * nz0;
             Tv *f0v = mixed ? (Tv *)m.f32[0] : (Tv *)m.f64[0];
             const int ntile = (n + tw - 1) / tw;
@@ -754,7 +589,7 @@ __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restr
             }
         }
         if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
-            copy_wait_all();
+            leave(false);
             return;
         }
         // ---- decision: every block reads the same maxima ----
@@ -786,7 +621,7 @@ __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restr
                 const int i = k / nr, j = k % nr;
                 if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] = 0.0;
             }
-            copy_wait_all();
+            leave(false);
             return;
         }
         // the pending correction goes into phi (also on the way out); nothing
@@ -797,35 +632,44 @@ __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restr
                 if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] += (double)delta[k];
             }
         if (decide != 0) {
-            copy_wait_all();
+            leave(false);
             return;
         }
         if (L == 0) {
             // nz = 3: the single interior row of phi, exactly
             if (blockIdx.x == 0) {
-                double *D = reinterpret_cast<double *>(smem_raw + lay.offD);
-                double *F = reinterpret_cast<double *>(smem_raw + lay.offR0);
-                copy_async(F, m.facc, FE * 8, tid, nt);
-                copy_commit();
-                double rhs = 0.0;
-                const bool act = tid < n;
-                if (act) {
-                    const double *cz = m.cz[0], *cr = m.cr[0];
-                    const size_t k = (size_t)nr + tid;
-                    rhs = m.f0[k] + cz[k - nr] * phi[k - nr] + cz[k] * phi[k + nr];
-                    if (tid == n - 1) rhs += cr[k] * phi[k + 1];
+                ld_begin(qC, FBd);
+                ld_copy(qC, FC, m.facc, FBd);
+                const double *cz = m.cz[0], *cr = m.cr[0];
+                for (int j = tid; j < NW; j += nt) {
+                    double rhs = 0.0;
+                    if (j < n) {
+                        const size_t k = (size_t)nr + j;
+                        rhs = m.f0[k] + cz[k - nr] * phi[k - nr] + cz[k] * phi[k + nr];
+                        if (j == n - 1) rhs += cr[k] * phi[k + 1];
+                    }
+                    BC[at(j)] = rhs;
                 }
-                const double x = pcr_line<double>(rhs, D, D + n, F, n, K, tid, act, false);
-                if (act) phi[(size_t)nr + tid] = x;
+                __syncthreads();
+                if (!ld_wait(qC)) {
+                    leave(true);
+                    return;
+                }
+                if (warp == 0) warp_line_solve<double, M>(FC, BC, lane);
+                __syncthreads();
+                for (int j = tid; j < n; j += nt) phi[(size_t)nr + j] = BC[at(j)];
             }
-            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) return;
+            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
+                leave(false);
+                return;
+            }
             continue;
         }
         // level 0's sweeps rewrite delta: when they run in the group alone,
         // every block's update of phi has to be in first
         if (lb == 0)
             if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
-                copy_wait_all();
+                leave(false);
                 return;
             }
         // ---- up: per level, each black line with the two red lines beside it ----
@@ -834,119 +678,114 @@ __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restr
             const bool grp = l >= lb;
             const int P = grp ? G : (int)gridDim.x;
             const int nzl = m.nz[l], nzc = m.nz[l + 1];
-            const int NB = (nzl - 3) / 2;  // black lines
-            const int nq = units_of(nzl);
+            const int NB = (nzl - 3) / 2;  // black lines (>= 1: nzl >= 5 here)
             Tv *u = mixed ? (Tv *)m.u32[l] : (Tv *)m.u64[l];
             const Tv *uc = mixed ? (const Tv *)m.u32[l + 1] : (const Tv *)m.u64[l + 1];
             const Tv *f = mixed ? (const Tv *)m.f32[l] : (const Tv *)m.f64[l];
             const Tv *cz = mixed ? (const Tv *)m.cz32[l] : (const Tv *)m.cz[l];
             const Tv *fac = mixed ? (const Tv *)m.fac32[l] : (const Tv *)m.fac64[l];
+            bool fail = false;
             if ((int)blockIdx.x < P) {
                 if (l == L - 1 && blockIdx.x == 0) {
-                    // the coarsest row (FP64 factors), then level L-1 in this block alone
-                    double *D = reinterpret_cast<double *>(smem_raw + lay.offD);
-                    double *F = reinterpret_cast<double *>(smem_raw + lay.offR0);
-                    if (!cpre) copy_async(F, m.facc, FE * 8, tid, nt);
-                    copy_commit();
-                    const bool act = tid < n;
-                    const double rhs = act ? m.fc64[(size_t)nr + tid] : 0.0;
-                    const double x = pcr_line<double>(rhs, D, D + n, F, n, K, tid, act, false);
+                    // the coarsest row (FP64 factors, requested with the residual),
+                    // then level L-1 in this block alone
+                    for (int j = tid; j < NW; j += nt) BC[at(j)] = j < n ? m.fc64[(size_t)nr + j] : 0.0;
+                    __syncthreads();
+                    if (!ld_wait(qC)) {
+                        leave(true);
+                        return;
+                    }
+                    if (warp == 0) warp_line_solve<double, M>(FC, BC, lane);
+                    __syncthreads();
                     Tv *ucw = mixed ? (Tv *)m.u32[L] : (Tv *)m.u64[L];
-                    if (act) ucw[(size_t)nr + tid] = (Tv)x;
+                    for (int j = tid; j < n; j += nt) ucw[(size_t)nr + j] = (Tv)BC[at(j)];
                     __syncthreads();
                     have = false;
                 }
-                for (int q = blockIdx.x; q < nq; q += P) {
+                for (int q = blockIdx.x; q < NB; q += P) {
                     const int ra = 2 * q + 1, rb = 2 * q + 3, ib = 2 * q + 2;
-                    const bool hasb = NB >= 1;
                     // factor requests: the reds (unless already in), then the black
                     if (!(have && q == (int)blockIdx.x)) {
-                        if (lay.pair) {
-                            copy_async(R0, fac + (size_t)(ra - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
-                            if (hasb) copy_async(R1, fac + (size_t)(rb - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
-                        } else {
-                            copy_async(R0, fac + (size_t)(ra - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
-                        }
+                        ld_begin(qR, 2 * FBv);
+                        ld_copy(qR, R0, fac + (size_t)(ra - 1) * LFE, FBv);
+                        ld_copy(qR, R1, fac + (size_t)(rb - 1) * LFE, FBv);
                     }
-                    copy_commit();
-                    if (hasb && bsep) copy_async(FBk, fac + (size_t)(ib - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
-                    copy_commit();
+                    ld_begin(qB, FBv);
+                    ld_copy(qB, FBk, fac + (size_t)(ib - 1) * LFE, FBv);
                     have = false;
-                    // the black line's own inputs do not depend on the reds: load them first
-                    Tv fb = 0, cb0 = 0, cb1 = 0;
-                    if (hasb && tid < n) {
-                        const size_t k = (size_t)ib * nr + tid;
-                        fb = f[k];
-                        cb0 = cz[k - nr];
-                        cb1 = cz[k];
+                    // right-hand sides: reds get f plus the coarse correction
+                    // injected at rows i -/+ 1; the black line keeps its own f
+                    // and couplings for later
+                    for (int j = tid; j < NW; j += nt) {
+                        Tv r0 = 0, r1 = 0, fb = 0, c0 = 0, c1 = 0;
+                        if (j < n) {
+                            const int Ia = (ra - 1) / 2, Ib = (rb + 1) / 2;  // coarse rows below ra, above rb
+                            const int Im = (ra + 1) / 2;                     // coarse row between (= row ib)
+                            const Tv ua = (Ia > 0 && Ia < nzc - 1) ? uc[(size_t)Ia * nr + j] : (Tv)0;
+                            const Tv um = (Im > 0 && Im < nzc - 1) ? uc[(size_t)Im * nr + j] : (Tv)0;
+                            const Tv ub = (Ib > 0 && Ib < nzc - 1) ? uc[(size_t)Ib * nr + j] : (Tv)0;
+                            const size_t ka = (size_t)ra * nr + j, kb = (size_t)rb * nr + j, kk = (size_t)ib * nr + j;
+                            r0 = f[ka] + cz[ka - nr] * ua + cz[ka] * um;
+                            r1 = f[kb] + cz[kb - nr] * um + cz[kb] * ub;
+                            fb = f[kk];
+                            c0 = cz[kk - nr];
+                            c1 = cz[kk];
+                        }
+                        const int pj = at(j);
+                        Bf0[pj] = r0;
+                        Bf1[pj] = r1;
+                        Bf2[pj] = fb;
+                        W0[j] = c0;
+                        W1[j] = c1;
                     }
-                    // red right-hand sides: f plus the coarse correction injected at rows i -/+ 1
-                    auto red_rhs = [&](int i, int j) -> Tv {
-                        const size_t k = (size_t)i * nr + j;
-                        const int Idn = (i - 1) / 2, Iup = (i + 1) / 2;
-                        const Tv udn = (Idn > 0 && Idn < nzc - 1) ? uc[(size_t)Idn * nr + j] : (Tv)0;
-                        const Tv uup = (Iup > 0 && Iup < nzc - 1) ? uc[(size_t)Iup * nr + j] : (Tv)0;
-                        return f[k] + cz[k - nr] * udn + cz[k] * uup;
-                    };
-                    if (lay.pair) {
-                        const int i = half ? rb : ra;
-                        const bool act = jl < n && (half == 0 || hasb);
-                        const Tv rhs = act ? red_rhs(i, jl) : (Tv)0;
-                        const Tv x = pcr_line<Tv>(rhs, Dh, Dh + n, half ? R1 : R0, n, K, jl, act, true);
-                        if (act) {
-                            X[half * n + jl] = x;
-                            // red rb is also the next black's red ra: one block writes it
-                            if (half == 0 || q == NB - 1) u[(size_t)i * nr + jl] = x;
-                        }
-                    } else {
-                        const bool act = tid < n;
-                        Tv rhs = act ? red_rhs(ra, tid) : (Tv)0;
-                        Tv x = pcr_line<Tv>(rhs, Dh, Dh + n, R0, n, K, tid, act, true);
-                        if (act) {
-                            X[tid] = x;
-                            u[(size_t)ra * nr + tid] = x;
-                        }
-                        if (hasb) {
-                            copy_async(R0, fac + (size_t)(rb - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
-                            copy_commit();
-                            rhs = act ? red_rhs(rb, tid) : (Tv)0;
-                            x = pcr_line<Tv>(rhs, Dh, Dh + n, R0, n, K, tid, act, false);
-                            if (act) {
-                                X[n + tid] = x;
-                                if (q == NB - 1) u[(size_t)rb * nr + tid] = x;
-                            }
+                    __syncthreads();
+                    if (!ld_wait(qR)) {
+                        fail = true;
+                        break;
+                    }
+                    if (warp == 0)
+                        warp_line_solve<Tv, M>(R0, Bf0, lane);
+                    else if (warp == 1)
+                        warp_line_solve<Tv, M>(R1, Bf1, lane);
+                    __syncthreads();
+                    for (int j = tid; j < NW; j += nt) {
+                        const int pj = at(j);
+                        const Tv x0 = Bf0[pj], x1 = Bf1[pj];
+                        if (j < n) {
+                            u[(size_t)ra * nr + j] = x0;
+                            // red rb is also the next black's red ra: one block stores it
+                            if (q == NB - 1) u[(size_t)rb * nr + j] = x1;
+                            Bf2[pj] = Bf2[pj] + W0[j] * x0 + W1[j] * x1;
                         }
                     }
-                    if (hasb) {
-                        __syncthreads();  // X complete
-                        Tv *F = FBk;
-                        if (!bsep) {
-                            copy_async(R0, fac + (size_t)(ib - 1) * FE, FE * (int)sizeof(Tv), tid, nt);
-                            copy_commit();
-                            F = R0;
-                        }
-                        const bool act = tid < n;
-                        const Tv rhs = act ? fb + cb0 * X[tid] + cb1 * X[n + tid] : (Tv)0;
-                        Tv *D = reinterpret_cast<Tv *>(smem_raw + lay.offD);
-                        const Tv x = pcr_line<Tv>(rhs, D, D + n, F, n, K, tid, act, false);
-                        if (act) u[(size_t)ib * nr + tid] = x;
+                    __syncthreads();
+                    if (!ld_wait(qB)) {
+                        fail = true;
+                        break;
                     }
+                    if (warp == 0) warp_line_solve<Tv, M>(FBk, Bf2, lane);
+                    __syncthreads();
+                    for (int j = tid; j < n; j += nt) u[(size_t)ib * nr + j] = Bf2[at(j)];
+                    __syncthreads();  // buffers and factor regions are reused
                 }
                 // request the next level's first red factors of this block
-                if (l > 0) {
+                if (!fail && l > 0) {
                     const int ln = l - 1;
                     const int Pn = ln >= lb ? G : (int)gridDim.x;
-                    const int nqn = units_of(m.nz[ln]);
-                    if ((int)blockIdx.x < Pn && (int)blockIdx.x < nqn) {
+                    const int nbn = (m.nz[ln] - 3) / 2;
+                    if ((int)blockIdx.x < Pn && (int)blockIdx.x < nbn) {
                         const Tv *facn = mixed ? (const Tv *)m.fac32[ln] : (const Tv *)m.fac64[ln];
                         const int q = blockIdx.x;
-                        copy_async(R0, facn + (size_t)(2 * q) * FE, FE * (int)sizeof(Tv), tid, nt);
-                        if (lay.pair && (m.nz[ln] - 3) / 2 >= 1)
-                            copy_async(R1, facn + (size_t)(2 * q + 2) * FE, FE * (int)sizeof(Tv), tid, nt);
+                        ld_begin(qR, 2 * FBv);
+                        ld_copy(qR, R0, facn + (size_t)(2 * q) * LFE, FBv);
+                        ld_copy(qR, R1, facn + (size_t)(2 * q + 2) * LFE, FBv);
                         have = true;
                     }
-                    copy_commit();
                 }
+            }
+            if (fail) {
+                leave(true);
+                return;
             }
             // levels in the group alone are separated by the group barrier;
             // every other level boundary is a grid barrier
@@ -956,10 +795,35 @@ __global__ void __launch_bounds__(1024) k_solve_persistent(const MGFast *__restr
             else
                 ok = count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl);
             if (!ok) {
-                copy_wait_all();
+                leave(false);
                 return;
             }
         }
+    }
+}
+
+}  // namespace
+
+size_t mg_line_factor_elems(int nr) { return (size_t)line_factor_elems(line_chunk(nr - 1)); }
+
+int mg_line_chunk(int nr) { return line_chunk(nr - 1); }
+
+namespace {
+
+template <typename Tv, int M>
+void *solve_fn() {
+    return (void *)k_solve_persistent<Tv, M>;
+}
+
+template <typename Tv>
+void *solve_kernel(int M) {
+    switch (M) {
+        case 1: return solve_fn<Tv, 1>();
+        case 2: return solve_fn<Tv, 2>();
+        case 4: return solve_fn<Tv, 4>();
+        case 8: return solve_fn<Tv, 8>();
+        case 16: return solve_fn<Tv, 16>();
+        default: return solve_fn<Tv, 32>();
     }
 }
 
@@ -970,57 +834,23 @@ void raise_smem_limits() {
     static bool done = false;
     if (done) return;
     const int lim = (int)kSolveSmemLimit;
-    cudaFuncSetAttribute(k_factor_levels<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_factor_levels<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     cudaFuncSetAttribute(k_chi_levels, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_solve_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_solve_persistent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    for (int M = 1; M <= 32; M <<= 1) {
+        cudaFuncSetAttribute(solve_kernel<float>(M), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(solve_kernel<double>(M), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    }
     done = true;
 }
 
-int line_threads(int n) {
-    int t = 32;
-    while (t < n && t < 1024) t <<= 1;
-    return t;
-}
-
-int pcr_steps(int n) {
-    int K = 0;
-    for (int s = 1; s < n; s <<= 1) ++K;
-    return K;
-}
-
 }  // namespace
-
-size_t mg_fast_factor_elems(int nz, int nr, bool mixed, size_t *n32) {
-    const int n = nr - 1, K = pcr_steps(n);
-    size_t e64 = 0, e32 = 0;
-    int nl = 0;
-    for (int z = nz;; z = (z + 1) / 2) {
-        const size_t lines = (size_t)(z - 2);
-        const bool coarsest = (z == 3);
-        const size_t e = lines * (2 * K + 1) * n;
-        if (coarsest || !mixed)
-            e64 += e;
-        else
-            e32 += e;
-        ++nl;
-        if (z == 3) break;
-    }
-    if (n32) *n32 = e32;
-    return e64;
-}
 
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, cudaStream_t st) {
     const int nz = fd.nz, nr = fd.nr, n = nr - 1, ng = nz * nr;
-    const int K = pcr_steps(n);
+    const int M = line_chunk(n);
     const int nlev = m.nlev;
     int L = 0;
-    const int lt = line_threads(n);
     raise_smem_limits();
     MGFast *mp = m.self;
     cudaMemcpyAsync(mp, &m, sizeof(MGFast), cudaMemcpyHostToDevice, st);
@@ -1037,21 +867,21 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     ++L;
     {
         // line factors: FP64 for the FP64 path and for the coarsest level,
-        // FP32 for the mixed path's other levels
+        // FP32 for the mixed path's other levels; one warp per line
         int lines_all = 0, lines_fine = 0;
         for (int l = 0; l < nlev; ++l) {
             lines_all += m.nz[l] - 2;
             if (l < nlev - 1) lines_fine += m.nz[l] - 2;
         }
         if (!mixed) {
-            k_factor_levels<double><<<lines_all, lt, 7 * n * sizeof(double), st>>>(mp, 0, nlev, nr, K);
+            k_factor_lines<double><<<(lines_all + 7) / 8, 256, 0, st>>>(mp, 0, nlev, nr, M, lines_all);
             ++L;
         } else {
             if (lines_fine > 0) {
-                k_factor_levels<float><<<lines_fine, lt, 7 * n * sizeof(float), st>>>(mp, 0, nlev - 1, nr, K);
+                k_factor_lines<float><<<(lines_fine + 7) / 8, 256, 0, st>>>(mp, 0, nlev - 1, nr, M, lines_fine);
                 ++L;
             }
-            k_factor_levels<double><<<1, lt, 7 * n * sizeof(double), st>>>(mp, nlev - 1, nlev, nr, K);
+            k_factor_lines<double><<<1, 32, 0, st>>>(mp, nlev - 1, nlev, nr, M, 1);
             ++L;
         }
     }
@@ -1068,162 +898,51 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     c0.tol = tol;
     c0.max_cycles = max_cycles;
     cudaMemcpyAsync(m.ctl, &c0, sizeof(MGCtl), cudaMemcpyHostToDevice, st);
-    // one cooperative launch for all cycles when the blocks fit on the GPU
-    {
-        int dev = 0, nsm = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        const size_t limit = std::min<size_t>((size_t)std::max(optin - 2048, 0), kSolveSmemLimit);
-        SolveLayout lay{};
-        size_t sp = 0;
-        bool found = false;
-        const size_t es = mixed ? sizeof(float) : sizeof(double);
-        const size_t FE = (size_t)(2 * K + 1) * n;
-        // richest layout first: both reds at once, black factors and the
-        // residual tile in their own space; then less overlap, then one red
-        // line at a time
-        for (int v = 0; v < 6 && !found; ++v) {
-            const int pair = v < 3;
-            const int mode = v % 3;  // 0: separate B and T, 1: separate T, 2: T over R
-            if (pair && 2 * lt > 1024) continue;
-            size_t off = 0;
-            auto take = [&](size_t b) {
-                const size_t o = off;
-                off += (b + 15) & ~(size_t)15;
-                return (int)o;
-            };
-            lay.tw = 8;
-            lay.lt = lt;
-            lay.pair = pair;
-            lay.offD = take((size_t)(pair ? 2 : 1) * 2 * n * sizeof(double));
-            lay.offX = take((size_t)2 * n * es);
-            const size_t Tb = (size_t)2 * lay.tw * nz * sizeof(double);
-            size_t Rb = std::max((size_t)(pair ? 2 : 1) * FE * es, FE * sizeof(double));
-            if (mode == 2) Rb = std::max(Rb, Tb);
-            lay.offR0 = take(Rb);
-            lay.offR1 = pair ? lay.offR0 + (int)(FE * es) : lay.offR0;
-            lay.offB = mode == 0 ? take(FE * es) : lay.offR0;
-            lay.offT = mode == 2 ? lay.offR0 : take(Tb);
-            sp = off;
-            found = sp <= limit;
-        }
-        const int threads = lay.pair ? 2 * lt : lt;
-        int per_sm = 0;
-        if (found) {
-            if (mixed)
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<float>, threads, sp);
-            else
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<double>, threads, sp);
-        }
-        const int grid = std::max(1, std::min(std::min(nsm, nsm * per_sm), (nz - 1) / 2));
-        if (found && per_sm >= 1) {
-            int first_cycle = 1;
-            int Kv = K, nrv = nr;
-            void *args[] = {(void *)&mp, (void *)&phi, (void *)&nrv, (void *)&Kv, (void *)&first_cycle,
-                            (void *)&lay};
-            cudaError_t e = mixed ? cudaLaunchCooperativeKernel((void *)k_solve_persistent<float>, grid, threads,
-                                                                args, sp, st)
-                                  : cudaLaunchCooperativeKernel((void *)k_solve_persistent<double>, grid, threads,
-                                                                args, sp, st);
-            ++L;
-            if (e == cudaSuccess) {
-                MGCtl ch;
-                cudaMemcpyAsync(&ch, m.ctl, sizeof(MGCtl), cudaMemcpyDeviceToHost, st);
-                cudaStreamSynchronize(st);
-                if (launches) *launches += L;
-                if (ch.timeout) {
-                    if (rel_res) *rel_res = 0.0;
-                    return kSolveTimeout;
-                }
-                if (ch.zero_rhs) {
-                    if (rel_res) *rel_res = 0.0;
-                    return 0;
-                }
-                if (rel_res) *rel_res = ch.bnorm > 0 ? ch.last_res / ch.bnorm : 0.0;
-                return ch.converged ? ch.cycles : -ch.cycles - 1;
-            }
-            cudaGetLastError();  // fall back to one launch per phase
-        }
+    // all cycles in one cooperative launch
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    const size_t LFE = (size_t)line_factor_elems(M);
+    SolveLayout lay{};
+    lay.tw = 8;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off += (b + 127) & ~(size_t)127;
+        return (int)o;
+    };
+    lay.offBuf = take((size_t)3 * M * kRow * sizeof(double));
+    lay.offW = take((size_t)2 * kLine * M * sizeof(double));
+    lay.offF = take(std::max((size_t)3 * LFE * es, (size_t)2 * lay.tw * nz * es));
+    lay.offC = take(LFE * sizeof(double));
+    const size_t sp = off;
+    void *fn = mixed ? solve_kernel<float>(M) : solve_kernel<double>(M);
+    int per_sm = 0;
+    if (sp <= kSolveSmemLimit) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSolveThreads, sp);
+    if (per_sm < 1) {
+        if (launches) *launches += L;
+        return kSolveNoLaunch;
     }
-    const int gres = std::max(1, std::min((ng + 255) / 256, 152 * 2));
-    const int gchain = (n + 31) / 32;
-    const size_t schain = nlev > 1 ? (size_t)nz * 32 * sizeof(double) +
-                                         (size_t)2 * m.nz[1] * 32 * (mixed ? sizeof(float) : sizeof(double))
-                                   : 0;
-    bool first = true;
+    const int grid = std::max(1, std::min(nsm * per_sm, std::min(nsm, (nz - 1) / 2)));
+    int first_cycle = 1, nrv = nr;
+    void *args[] = {(void *)&mp, (void *)&phi, (void *)&nrv, (void *)&first_cycle, (void *)&lay};
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kSolveThreads, args, sp, st);
+    ++L;
+    if (launches) *launches += L;
+    if (e != cudaSuccess) return kSolveNoLaunch;
     MGCtl ch;
-    int batch = 4;
-    for (;;) {
-        for (int b = 0; b < batch; ++b) {
-            k_resid<<<gres, 256, 0, st>>>(mp, nr, phi, first ? 1 : 0);
-            ++L;
-            first = false;
-            if (nlev > 1) {
-                if (mixed)
-                    k_chain<float><<<gchain, 32, schain, st>>>(mp, nr);
-                else
-                    k_chain<double><<<gchain, 32, schain, st>>>(mp, nr);
-                ++L;
-            }
-            if (nlev == 1) {
-                k_single_row<<<1, lt, 2 * n * sizeof(double), st>>>(mp, phi, nr, K);
-                ++L;
-                continue;
-            }
-            if (mixed)
-                k_coarse<float><<<1, lt, 2 * n * sizeof(double), st>>>(mp, nr, K);
-            else
-                k_coarse<double><<<1, lt, 2 * n * sizeof(double), st>>>(mp, nr, K);
-            ++L;
-            for (int l = nlev - 2; l >= 0; --l) {
-                const int nzl = m.nz[l];
-                const int nred = (nzl - 1) / 2, nblack = (nzl - 3) / 2;
-                if (!mixed) {
-                    double *u = l == 0 ? phi : m.u64[l];
-                    const double *f = l == 0 ? m.f0 : m.f64[l];
-                    k_red<double><<<nred, lt, 2 * n * sizeof(double), st>>>(
-                        mp, l, nr, K, u, m.u64[l + 1], f, m.cz[l], m.cr[l], m.fac64[l], l == 0);
-                    if (nblack > 0)
-                        k_black<double><<<nblack, lt, 2 * n * sizeof(double), st>>>(
-                            mp, l, nr, K, u, f, m.cz[l], m.cr[l], m.fac64[l], l == 0);
-                } else {
-                    k_red<float><<<nred, lt, 2 * n * sizeof(float), st>>>(
-                        mp, l, nr, K, m.u32[l], m.u32[l + 1], m.f32[l], m.cz32[l], m.cr32[l],
-                        m.fac32[l], 0);
-                    if (nblack > 0)
-                        k_black<float><<<nblack, lt, 2 * n * sizeof(float), st>>>(
-                            mp, l, nr, K, m.u32[l], m.f32[l], m.cz32[l], m.cr32[l], m.fac32[l], 0);
-                }
-                L += nblack > 0 ? 2 : 1;
-            }
-            if (mixed) {
-                k_correct<<<(ng + 255) / 256, 256, 0, st>>>(mp, phi, m.u32[0], nz, nr);
-                ++L;
-            }
-        }
-        cudaMemcpyAsync(&ch, m.ctl, sizeof(MGCtl), cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
-        if (ch.done) break;
-        // the residual falls by roughly a constant factor per cycle: size the
-        // next batch by the cycles still needed
-        batch = 2;
-        if (ch.cycles >= 2 && ch.last_res > 0 && ch.tol > 0) {
-            const double need = log(ch.tol * ch.bnorm / ch.last_res);
-            const double per = log(0.12);
-            const int est = (int)ceil(need / per);
-            batch = std::max(1, std::min(est + 1, 6));
-        }
+    cudaMemcpyAsync(&ch, m.ctl, sizeof(MGCtl), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    if (ch.timeout) {
+        if (rel_res) *rel_res = 0.0;
+        return kSolveTimeout;
     }
     if (ch.zero_rhs) {
-        k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(rho, m.f0, phi, phi_zL, V, nz, nr, fd.dz, fd.dr, 1);
-        ++L;
         if (rel_res) *rel_res = 0.0;
-        if (launches) *launches += L;
         return 0;
     }
     if (rel_res) *rel_res = ch.bnorm > 0 ? ch.last_res / ch.bnorm : 0.0;
-    if (launches) *launches += L;
     return ch.converged ? ch.cycles : -ch.cycles - 1;
 }
 

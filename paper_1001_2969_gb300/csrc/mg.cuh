@@ -24,8 +24,10 @@ struct MGCtl {
     Line gbar_count;
 };
 
-// returned by mg_fast_solve when a bounded device wait gave up
+// returned by mg_fast_solve when a bounded device wait gave up, and when
+// the one-launch solve cannot be launched (shared memory, co-residency)
 constexpr int kSolveTimeout = -1000000;
+constexpr int kSolveNoLaunch = -1000001;
 
 constexpr int kMaxLevels = 16;
 
@@ -50,8 +52,9 @@ struct MGFast {
     MGFast *self;  // device copy of this struct (kernels read it through a pointer)
 };
 
-// elements of FP64 (returned) and FP32 (*n32) line-factor storage of a mesh
-size_t mg_fast_factor_elems(int nz, int nr, bool mixed, size_t *n32);
+// line-factor elements of one r-line of a mesh with nr nodes per row
+// (the same count in FP32 and FP64)
+size_t mg_line_factor_elems(int nr);
 
 // solve into phi; returns the cycles (>= 0, converged) or -cycles-1
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,

@@ -391,9 +391,7 @@ void setup_device(pic_handle *h) {
     // V-cycle's correction and right-hand side, and the r-line factors
     MGFast &m = h->mgf;
     memset(&m, 0, sizeof(m));
-    const int nline = h->nr - 1;
-    int K = 0;
-    for (int s = 1; s < nline; s <<= 1) ++K;
+    const size_t line_fe = mg_line_factor_elems(h->nr);
     int nl = 0;
     for (int z = h->nz;; z = (z + 1) / 2) {
         const int l = nl++;
@@ -412,7 +410,7 @@ void setup_device(pic_handle *h) {
             m.u64[l] = (double *)dalloc(h, g * sizeof(double));
             m.f64[l] = (double *)dalloc(h, g * sizeof(double));
         }
-        const size_t fe = (size_t)(z - 2) * (2 * K + 1) * nline;
+        const size_t fe = (size_t)(z - 2) * line_fe;
         if (z == 3)
             m.facc = (double *)dalloc(h, fe * sizeof(double));
         else if (!h->mixed)
@@ -574,6 +572,10 @@ pic_status one_step(pic_handle *h) {
         if (r == kSolveTimeout) {
             h->launches += L;
             return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
+        }
+        if (r == kSolveNoLaunch) {
+            h->launches += L;
+            return fail(h, PIC_ERR_CUDA, "multigrid solve could not be launched");
         }
         h->last_cycles = r >= 0 ? r : -r - 1;
         h->last_res = res;
@@ -864,6 +866,7 @@ pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, 
                                 h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, h->st);
     h->launches += L;
     if (r == kSolveTimeout) return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
+    if (r == kSolveNoLaunch) return fail(h, PIC_ERR_CUDA, "multigrid solve could not be launched");
     cudaMemcpyAsync(phi, h->tmp_grid[2], gb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st);
     cudaStreamSynchronize(h->st);
     if (info) {
