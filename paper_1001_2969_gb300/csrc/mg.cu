@@ -156,7 +156,8 @@ __global__ void k_factor_lines(const MGFast *__restrict__ mp, int l0, int l1, in
     const bool f64 = sizeof(Ts) == 8;
     const Ts *cz = f64 ? (const Ts *)m.cz[l] : (const Ts *)m.cz32[l];
     const Ts *cr = f64 ? (const Ts *)m.cr[l] : (const Ts *)m.cr32[l];
-    Ts *fac = (l == m.nlev - 1) ? (Ts *)m.facc : (f64 ? (Ts *)m.fac64[l] : (Ts *)m.fac32[l]);
+    Ts *fac = (l == m.nlev - 1) ? (f64 ? (Ts *)m.facc : (Ts *)m.facc32)
+                                : (f64 ? (Ts *)m.fac64[l] : (Ts *)m.fac32[l]);
     Ts *F = fac + (size_t)g * line_factor_elems(M);
     const size_t rowk = (size_t)(1 + g) * nr;
     auto coef = [&](int k, Ts &lo, Ts &dg, Ts &up) {
@@ -296,17 +297,21 @@ __device__ __forceinline__ void warp_line_solve(const Ts *__restrict__ F, Ts *Bs
 }
 
 // right-hand side rho A_j dz / eps0 and the Dirichlet data of phi
-__global__ void k_rhs_bc(const double *rho, double *f0, double *phi, const double *phi_zL,
+__global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, double *phi, const double *phi_zL,
                          double V, int nz, int nr, double dz, double dr, int cold) {
+    const MGFast &m = *mp;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nz * nr) return;
     const int i = k / nr, j = k % nr;
-    double v = 0.0;
+    double v = 0.0, dg = 0.0;
     if (i > 0 && i < nz - 1 && j < nr - 1) {
         const double rp = (j + 0.5) * dr, rm = j > 0 ? (j - 0.5) * dr : 0.0;
         v = rho[k] * (kPi * (rp * rp - rm * rm)) * dz / kEps0;
+        const double *cz = m.cz[0], *cr = m.cr[0];
+        dg = cz[k - nr] + cz[k] + (j > 0 ? cr[k - 1] : 0.0) + cr[k];
     }
-    f0[k] = v;
+    m.f0[k] = v;
+    m.dg0[k] = dg;
     if (i == 0)
         phi[k] = (j == nr - 1) ? 0.0 : V;
     else if (i == nz - 1)
@@ -483,6 +488,13 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
     };
     int first = first_cycle;
     unsigned ngrid = 0, ngroup = 0;  // barriers of each kind passed
+    // the iterate alternates between phi and its copy (L > 0): the residual
+    // phase reads cur + delta and stores it as nxt, the next cycle's iterate
+    const bool dbuf = L > 0;
+    double *cur = phi, *nxt = m.phi2;
+    // coarsest-row factors in the V-cycle's type (nz = 3: phi's own row, FP64)
+    const Tv *facc_v = mixed ? (const Tv *)m.facc32 : (const Tv *)m.facc;
+    const unsigned FBc = (unsigned)(LFE * sizeof(Tv));
     Tv *Bf0 = reinterpret_cast<Tv *>(smem_raw + lay.offBuf);
     Tv *Bf1 = reinterpret_cast<Tv *>(smem_raw + lay.offBuf + M * kRow * 8);
     Tv *Bf2 = reinterpret_cast<Tv *>(smem_raw + lay.offBuf + 2 * M * kRow * 8);
@@ -492,21 +504,24 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
     Tv *R0 = reinterpret_cast<Tv *>(smem_raw + lay.offF);
     Tv *R1 = R0 + LFE;
     Tv *FBk = R1 + LFE;
-    double *FC = reinterpret_cast<double *>(smem_raw + lay.offC);
+    Tv *FC = reinterpret_cast<Tv *>(smem_raw + lay.offC);
+    double *FC64 = reinterpret_cast<double *>(smem_raw + lay.offC);
     // position of unknown j in a line buffer
     auto at = [](int j) { return (j % M) * kRow + j / M; };
     for (int cyc = 0;; ++cyc) {
         // ---- residual of phi + delta, its norms, and the restriction chain ----
         if (blockIdx.x == 0 && L > 0) {
-            ld_begin(qC, FBd);
-            ld_copy(qC, FC, m.facc, FBd);
+            ld_begin(qC, FBc);
+            ld_copy(qC, FC, facc_v, FBc);
         }
         // maxima as bit patterns of |x| (ordered like the values; a NaN
         // compares above every number), so the reductions are integer work
         unsigned long long rmax = 0ull, bmax = 0ull;
         {
             const double *cz = m.cz[0], *cr = m.cr[0];
-            const int tw = lay.tw;
+            const int tw = lay.tw, sw = tw + 2;
+            // phi + delta of the tile and its two neighbour columns, all rows
+            double *S = reinterpret_cast<double *>(smem_raw + lay.offBuf);
             // the restriction chain runs in the V-cycle's type
             Tv *T0 = reinterpret_cast<Tv *>(smem_raw + lay.offF);
             Tv *T1 = T0 + (size_t)tw * nz0;
@@ -514,26 +529,35 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
             const int ntile = (n + tw - 1) / tw;
             for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
                 const int j0 = t * tw;
+                for (int e = tid; e < sw * nz0; e += nt) {
+                    const int c = e % sw - 1, i = e / sw, j = j0 + c;
+                    double v = 0.0;
+                    if (j >= 0 && j < nr) {
+                        const size_t k = (size_t)i * nr + j;
+                        v = cur[k] + (double)delta[k];
+                        // the iterate of the next cycle, stored by the tile that owns the node
+                        if (dbuf && c >= 0 && c < tw && j < n && i > 0 && i < nz0 - 1) nxt[k] = v;
+                    }
+                    S[(size_t)(c + 1) * nz0 + i] = v;
+                }
+                __syncthreads();
                 // interior rows only: the chain never reads a level's boundary rows
                 for (int e = tid; e < tw * (nz0 - 2); e += nt) {
                     const int c = e % tw, i = 1 + e / tw, j = j0 + c;
                     double r = 0.0;
                     if (j < n) {
                         const size_t k = (size_t)i * nr + j;
-                        const double pc = phi[k] + (double)delta[k], ps = phi[k - nr] + (double)delta[k - nr];
-                        const double pn = phi[k + nr] + (double)delta[k + nr], pe = phi[k + 1] + (double)delta[k + 1];
-                        const double pw = j > 0 ? phi[k - 1] + (double)delta[k - 1] : 0.0;
+                        const double *Sc = S + (size_t)(c + 1) * nz0 + i;
                         const double a = cz[k - nr], cc = cz[k], ee = cr[k], d = j > 0 ? cr[k - 1] : 0.0;
-                        double Au = (a + cc + d + ee) * pc - a * ps - cc * pn - ee * pe;
-                        if (j > 0) Au -= d * pw;
+                        const double Au = m.dg0[k] * Sc[0] - a * Sc[-1] - cc * Sc[1] - ee * Sc[nz0] - d * Sc[-nz0];
                         const double f = m.f0[k];
                         r = f - Au;
                         rmax = max(rmax, abs_bits(r));
                         if (first) {
                             double bb = f;
-                            if (i == 1) bb += a * phi[k - nr];
-                            if (i == nz0 - 2) bb += cc * phi[k + nr];
-                            if (j == nr - 2) bb += ee * phi[k + 1];
+                            if (i == 1) bb += a * Sc[-1];
+                            if (i == nz0 - 2) bb += cc * Sc[1];
+                            if (j == nr - 2) bb += ee * Sc[nz0];
                             bmax = max(bmax, abs_bits(bb));
                         }
                         if (L > 0) f0v[k] = (Tv)r;
@@ -624,22 +648,26 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
             leave(false);
             return;
         }
-        // the pending correction goes into phi (also on the way out); nothing
-        // reads phi again before the next residual
-        if (L > 0)
-            for (int k = blockIdx.x * nt + tid; k < ng; k += gridDim.x * nt) {
-                const int i = k / nr, j = k % nr;
-                if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] += (double)delta[k];
-            }
         if (decide != 0) {
+            // the answer is the iterate the residual phase just stored
+            if (dbuf && nxt != phi)
+                for (int k = blockIdx.x * nt + tid; k < ng; k += gridDim.x * nt) {
+                    const int i = k / nr, j = k % nr;
+                    if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] = nxt[k];
+                }
             leave(false);
             return;
+        }
+        if (dbuf) {
+            double *t = cur;
+            cur = nxt;
+            nxt = t;
         }
         if (L == 0) {
             // nz = 3: the single interior row of phi, exactly
             if (blockIdx.x == 0) {
                 ld_begin(qC, FBd);
-                ld_copy(qC, FC, m.facc, FBd);
+                ld_copy(qC, FC64, m.facc, FBd);
                 const double *cz = m.cz[0], *cr = m.cr[0];
                 for (int j = tid; j < NW; j += nt) {
                     double rhs = 0.0;
@@ -655,7 +683,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
                     leave(true);
                     return;
                 }
-                if (warp == 0) warp_line_solve<double, M>(FC, BC, lane);
+                if (warp == 0) warp_line_solve<double, M>(FC64, BC, lane);
                 __syncthreads();
                 for (int j = tid; j < n; j += nt) phi[(size_t)nr + j] = BC[at(j)];
             }
@@ -689,16 +717,16 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
                 if (l == L - 1 && blockIdx.x == 0) {
                     // the coarsest row (FP64 factors, requested with the residual),
                     // then level L-1 in this block alone
-                    for (int j = tid; j < NW; j += nt) BC[at(j)] = j < n ? m.fc64[(size_t)nr + j] : 0.0;
+                    for (int j = tid; j < NW; j += nt) Bf0[at(j)] = j < n ? (Tv)m.fc64[(size_t)nr + j] : (Tv)0;
                     __syncthreads();
                     if (!ld_wait(qC)) {
                         leave(true);
                         return;
                     }
-                    if (warp == 0) warp_line_solve<double, M>(FC, BC, lane);
+                    if (warp == 0) warp_line_solve<Tv, M>(FC, Bf0, lane);
                     __syncthreads();
                     Tv *ucw = mixed ? (Tv *)m.u32[L] : (Tv *)m.u64[L];
-                    for (int j = tid; j < n; j += nt) ucw[(size_t)nr + j] = (Tv)BC[at(j)];
+                    for (int j = tid; j < n; j += nt) ucw[(size_t)nr + j] = Bf0[at(j)];
                     __syncthreads();
                     have = false;
                 }
@@ -866,28 +894,26 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
                                                          total);
     ++L;
     {
-        // line factors: FP64 for the FP64 path and for the coarsest level,
-        // FP32 for the mixed path's other levels; one warp per line
-        int lines_all = 0, lines_fine = 0;
-        for (int l = 0; l < nlev; ++l) {
-            lines_all += m.nz[l] - 2;
-            if (l < nlev - 1) lines_fine += m.nz[l] - 2;
-        }
+        // line factors in the V-cycle's type; one warp per line
+        int lines_all = 0;
+        for (int l = 0; l < nlev; ++l) lines_all += m.nz[l] - 2;
         if (!mixed) {
             k_factor_lines<double><<<(lines_all + 7) / 8, 256, 0, st>>>(mp, 0, nlev, nr, M, lines_all);
             ++L;
+        } else if (nlev > 1) {
+            k_factor_lines<float><<<(lines_all + 7) / 8, 256, 0, st>>>(mp, 0, nlev, nr, M, lines_all);
+            ++L;
         } else {
-            if (lines_fine > 0) {
-                k_factor_lines<float><<<(lines_fine + 7) / 8, 256, 0, st>>>(mp, 0, nlev - 1, nr, M, lines_fine);
-                ++L;
-            }
-            k_factor_lines<double><<<1, 32, 0, st>>>(mp, nlev - 1, nlev, nr, M, 1);
+            // nz = 3: the single row is phi's own, solved in FP64
+            k_factor_lines<double><<<1, 32, 0, st>>>(mp, 0, 1, nr, M, 1);
             ++L;
         }
     }
-    k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(rho, m.f0, phi, phi_zL, V, nz, nr, fd.dz, fd.dr,
+    k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(mp, rho, phi, phi_zL, V, nz, nr, fd.dz, fd.dr,
                                                warm ? 0 : 1);
     ++L;
+    // the solve alternates between phi and a copy (both carry the boundary values)
+    cudaMemcpyAsync(m.phi2, phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st);
     // the level-0 correction starts at zero and stays zero on the boundary
     if (mixed)
         cudaMemsetAsync(m.u32[0], 0, sizeof(float) * ng, st);
@@ -912,7 +938,11 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
         off += (b + 127) & ~(size_t)127;
         return (int)o;
     };
-    lay.offBuf = take((size_t)3 * M * kRow * sizeof(double));
+    // line buffers and couplings; during the residual phase the same space
+    // holds phi + delta of a tile of columns with its two neighbours
+    const size_t bufw = (size_t)3 * M * kRow * sizeof(double) + (size_t)2 * kLine * M * sizeof(double);
+    const size_t stage = (size_t)(lay.tw + 2) * nz * sizeof(double);
+    lay.offBuf = take(std::max(bufw, stage) - (size_t)2 * kLine * M * sizeof(double));
     lay.offW = take((size_t)2 * kLine * M * sizeof(double));
     lay.offF = take(std::max((size_t)3 * LFE * es, (size_t)2 * lay.tw * nz * es));
     lay.offC = take(LFE * sizeof(double));

@@ -45,9 +45,11 @@ struct MGFast {
     double *fac64[kMaxLevels];                  // line factors, FP64 path
     float *fac32[kMaxLevels];                   // line factors, FP32 V-cycle
     double *facc;                               // coarsest level's line factors (FP64)
-    double *fc64;                               // coarsest level's right-hand side (FP64)
+    float *facc32;                              // coarsest level's line factors, FP32 V-cycle
+    double *fc64;                               // coarsest level's right-hand side
     double *f0;                                 // fine right-hand side
-    double *r;                                  // fine residual (FP64)
+    double *dg0;                                // fine operator's diagonal
+    double *phi2;                               // second copy of phi (the solve alternates)
     MGCtl *ctl;
     MGFast *self;  // device copy of this struct (kernels read it through a pointer)
 };

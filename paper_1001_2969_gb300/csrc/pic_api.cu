@@ -411,9 +411,10 @@ void setup_device(pic_handle *h) {
             m.f64[l] = (double *)dalloc(h, g * sizeof(double));
         }
         const size_t fe = (size_t)(z - 2) * line_fe;
-        if (z == 3)
+        if (z == 3) {
             m.facc = (double *)dalloc(h, fe * sizeof(double));
-        else if (!h->mixed)
+            if (h->mixed) m.facc32 = (float *)dalloc(h, fe * sizeof(float));
+        } else if (!h->mixed)
             m.fac64[l] = (double *)dalloc(h, fe * sizeof(double));
         else
             m.fac32[l] = (float *)dalloc(h, fe * sizeof(float));
@@ -422,7 +423,8 @@ void setup_device(pic_handle *h) {
     m.nlev = nl;
     m.fc64 = (double *)dalloc(h, (size_t)3 * h->nr * sizeof(double));
     m.f0 = (double *)dalloc(h, gb);
-    m.r = (double *)dalloc(h, gb);
+    m.dg0 = (double *)dalloc(h, gb);
+    m.phi2 = (double *)dalloc(h, gb);
     m.ctl = (MGCtl *)dalloc(h, sizeof(MGCtl));
     m.self = (MGFast *)dalloc(h, sizeof(MGFast));
     // births radix scratch
