@@ -446,6 +446,8 @@ struct SolveLayout {
 __device__ __forceinline__ int units_of(int nz) { return max((nz - 3) / 2, 1); }
 
 constexpr int kSolveThreads = 256;
+constexpr int kU = 4;   // elements per thread and batch in the residual phase
+constexpr int kUL = 4;  // unknowns per thread and batch of a level's right-hand sides
 
 template <typename Tv, int M>
 __global__ void __launch_bounds__(kSolveThreads, 1)
@@ -529,28 +531,61 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
             const int ntile = (n + tw - 1) / tw;
             for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
                 const int j0 = t * tw;
-                for (int e = tid; e < sw * nz0; e += nt) {
-                    const int c = e % sw - 1, i = e / sw, j = j0 + c;
-                    double v = 0.0;
-                    if (j >= 0 && j < nr) {
-                        const size_t k = (size_t)i * nr + j;
-                        v = cur[k] + (double)delta[k];
-                        // the iterate of the next cycle, stored by the tile that owns the node
-                        if (dbuf && c >= 0 && c < tw && j < n && i > 0 && i < nz0 - 1) nxt[k] = v;
+                // batches of kU elements per thread: all loads first (stores to
+                // global memory would otherwise hold back the next loads)
+                for (int e0 = tid; e0 < sw * nz0; e0 += kU * nt) {
+                    double pv[kU];
+                    Tv dv[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int e = e0 + u * nt, c = e % sw - 1, i = e / sw, j = j0 + c;
+                        pv[u] = 0.0;
+                        dv[u] = 0;
+                        if (e < sw * nz0 && j >= 0 && j < nr) {
+                            const size_t k = (size_t)i * nr + j;
+                            pv[u] = cur[k];
+                            dv[u] = delta[k];
+                        }
                     }
-                    S[(size_t)(c + 1) * nz0 + i] = v;
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int e = e0 + u * nt, c = e % sw - 1, i = e / sw, j = j0 + c;
+                        if (e >= sw * nz0) break;
+                        const double v = pv[u] + (double)dv[u];
+                        // the iterate of the next cycle, stored by the tile that owns the node
+                        if (dbuf && c >= 0 && c < tw && j < n && i > 0 && i < nz0 - 1) nxt[(size_t)i * nr + j] = v;
+                        S[(size_t)(c + 1) * nz0 + i] = v;
+                    }
                 }
                 __syncthreads();
                 // interior rows only: the chain never reads a level's boundary rows
-                for (int e = tid; e < tw * (nz0 - 2); e += nt) {
-                    const int c = e % tw, i = 1 + e / tw, j = j0 + c;
+                for (int e0 = tid; e0 < tw * (nz0 - 2); e0 += kU * nt) {
+                    double ca[kU], cb[kU], ce[kU], cd[kU], dgv[kU], fv[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        const int e = e0 + u * nt, c = e % tw, i = 1 + e / tw, j = j0 + c;
+                        ca[u] = cb[u] = ce[u] = cd[u] = dgv[u] = fv[u] = 0.0;
+                        if (e < tw * (nz0 - 2) && j < n) {
+                            const size_t k = (size_t)i * nr + j;
+                            ca[u] = cz[k - nr];
+                            cb[u] = cz[k];
+                            ce[u] = cr[k];
+                            cd[u] = j > 0 ? cr[k - 1] : 0.0;
+                            dgv[u] = m.dg0[k];
+                            fv[u] = m.f0[k];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                    const int e = e0 + u * nt, c = e % tw, i = 1 + e / tw, j = j0 + c;
+                    if (e >= tw * (nz0 - 2)) break;
                     double r = 0.0;
                     if (j < n) {
                         const size_t k = (size_t)i * nr + j;
                         const double *Sc = S + (size_t)(c + 1) * nz0 + i;
-                        const double a = cz[k - nr], cc = cz[k], ee = cr[k], d = j > 0 ? cr[k - 1] : 0.0;
-                        const double Au = m.dg0[k] * Sc[0] - a * Sc[-1] - cc * Sc[1] - ee * Sc[nz0] - d * Sc[-nz0];
-                        const double f = m.f0[k];
+                        const double a = ca[u], cc = cb[u], ee = ce[u], d = cd[u];
+                        const double Au = dgv[u] * Sc[0] - a * Sc[-1] - cc * Sc[1] - ee * Sc[nz0] - d * Sc[-nz0];
+                        const double f = fv[u];
                         r = f - Au;
                         rmax = max(rmax, abs_bits(r));
                         if (first) {
@@ -563,6 +598,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
                         if (L > 0) f0v[k] = (Tv)r;
                     }
                     T0[(size_t)c * nz0 + i] = (Tv)r;
+                    }
                 }
                 __syncthreads();
                 Tv *src = T0, *dst = T1;
@@ -744,27 +780,41 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
                     // right-hand sides: reds get f plus the coarse correction
                     // injected at rows i -/+ 1; the black line keeps its own f
                     // and couplings for later
-                    for (int j = tid; j < NW; j += nt) {
-                        Tv r0 = 0, r1 = 0, fb = 0, c0 = 0, c1 = 0;
-                        if (j < n) {
-                            const int Ia = (ra - 1) / 2, Ib = (rb + 1) / 2;  // coarse rows below ra, above rb
-                            const int Im = (ra + 1) / 2;                     // coarse row between (= row ib)
-                            const Tv ua = (Ia > 0 && Ia < nzc - 1) ? uc[(size_t)Ia * nr + j] : (Tv)0;
-                            const Tv um = (Im > 0 && Im < nzc - 1) ? uc[(size_t)Im * nr + j] : (Tv)0;
-                            const Tv ub = (Ib > 0 && Ib < nzc - 1) ? uc[(size_t)Ib * nr + j] : (Tv)0;
-                            const size_t ka = (size_t)ra * nr + j, kb = (size_t)rb * nr + j, kk = (size_t)ib * nr + j;
-                            r0 = f[ka] + cz[ka - nr] * ua + cz[ka] * um;
-                            r1 = f[kb] + cz[kb - nr] * um + cz[kb] * ub;
-                            fb = f[kk];
-                            c0 = cz[kk - nr];
-                            c1 = cz[kk];
+                    const int Ia = (ra - 1) / 2, Ib = (rb + 1) / 2;  // coarse rows below ra, above rb
+                    const int Im = (ra + 1) / 2;                     // coarse row between (= row ib)
+                    const bool va = Ia > 0 && Ia < nzc - 1, vm = Im > 0 && Im < nzc - 1, vb = Ib > 0 && Ib < nzc - 1;
+                    for (int j0 = tid; j0 < NW; j0 += kUL * nt) {
+                        // rows ra, ib = ra + 1, rb = ra + 2: cz[ib - 1] = cz[ra], cz[ib] = cz[rb - 1]
+                        Tv ua[kUL], um[kUL], ub[kUL], fa[kUL], fbv[kUL], fk[kUL], z0[kUL], z1[kUL], z2[kUL], z3[kUL];
+#pragma unroll
+                        for (int u = 0; u < kUL; ++u) {
+                            const int j = j0 + u * nt;
+                            ua[u] = um[u] = ub[u] = fa[u] = fbv[u] = fk[u] = z0[u] = z1[u] = z2[u] = z3[u] = 0;
+                            if (j < n) {
+                                const size_t ka = (size_t)ra * nr + j;
+                                if (va) ua[u] = uc[(size_t)Ia * nr + j];
+                                if (vm) um[u] = uc[(size_t)Im * nr + j];
+                                if (vb) ub[u] = uc[(size_t)Ib * nr + j];
+                                fa[u] = f[ka];
+                                fk[u] = f[ka + nr];
+                                fbv[u] = f[ka + 2 * nr];
+                                z0[u] = cz[ka - nr];
+                                z1[u] = cz[ka];
+                                z2[u] = cz[ka + nr];
+                                z3[u] = cz[ka + 2 * nr];
+                            }
                         }
-                        const int pj = at(j);
-                        Bf0[pj] = r0;
-                        Bf1[pj] = r1;
-                        Bf2[pj] = fb;
-                        W0[j] = c0;
-                        W1[j] = c1;
+#pragma unroll
+                        for (int u = 0; u < kUL; ++u) {
+                            const int j = j0 + u * nt;
+                            if (j >= NW) break;
+                            const int pj = at(j);
+                            Bf0[pj] = fa[u] + z0[u] * ua[u] + z1[u] * um[u];
+                            Bf1[pj] = fbv[u] + z2[u] * um[u] + z3[u] * ub[u];
+                            Bf2[pj] = fk[u];
+                            W0[j] = z1[u];
+                            W1[j] = z2[u];
+                        }
                     }
                     __syncthreads();
                     if (!ld_wait(qR)) {
