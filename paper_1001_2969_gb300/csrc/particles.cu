@@ -464,22 +464,54 @@ __device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, ui
     }
 }
 
+// cp.async of 4, 8 or 16 bytes (global -> shared; both ends aligned to the size)
+__device__ __forceinline__ void cpa16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
 constexpr int kThreads = 256;
 constexpr int kPPT = 4;
 constexpr int kChunk = kThreads * kPPT;
 static_assert(kChunk == kStepChunk, "chunk size");
 constexpr int kHalo = 3;
-constexpr int kWinBytes = 16384;
+// deposit window of a block: smaller with the prefetch staging beside it
+template <bool PF>
+__host__ __device__ constexpr int win_bytes() {
+    return PF ? 8192 : 16384;
+}
 
 // The fused particle pass (Sec. 2.1 merged cycle).  Each block walks chunks
 // of kChunk particles of the cell-sorted input; chunk positions are close
 // in space, so the deposit goes to a shared-memory window around the
 // chunk's cells and is flushed with one global atomic per touched node.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
+// PF: the chunk's particles come into shared memory by cp.async a chunk at
+// a time (latency-bound passes gain; passes bound by issue and shared-memory
+// traffic, like the electrons' with their collisions, lose)
+template <typename T, bool PF>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using V = typename V4<T>::type;
+    constexpr int kWinBytes = win_bytes<PF>();
     T *win = reinterpret_cast<T *>(smem_raw);
-    T *s_eedf = reinterpret_cast<T *>(smem_raw + kWinBytes);
+    // the chunk's particles, fetched into shared memory ahead of their use
+    // (PF): [kPPT][kThreads] of q0, q1, id, cell
+    V *st_q0 = reinterpret_cast<V *>(smem_raw + kWinBytes);
+    V *st_q1 = st_q0 + kChunk;
+    uint64_t *st_id = reinterpret_cast<uint64_t *>(st_q1 + kChunk);
+    int32_t *st_cell = reinterpret_cast<int32_t *>(st_id + kChunk);
+    T *s_eedf = PF ? reinterpret_cast<T *>(st_cell + kChunk) : reinterpret_cast<T *>(smem_raw + kWinBytes);
     __shared__ BlockTally bt;
     __shared__ int s_w[4];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -491,10 +523,48 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
     const int n = *a.n_alive;
     const int nmain = *a.n_main_src;
     const int nchunks = (n + kChunk - 1) / kChunk;
+    // this thread's perm entries of its next chunk, read a chunk ahead
+    int pn[kPPT];
+    if (PF) {
+#pragma unroll
+        for (int m = 0; m < kPPT; ++m) {
+            const int k = blockIdx.x * kChunk + m * kThreads + tid;
+            pn[m] = k < n ? a.perm[k] : 0;
+        }
+    }
     for (int ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
         const int base = ck * kChunk;
         const int end = min(base + kChunk, n);
         __syncthreads();
+        // request the chunk's particles, then read the next chunk's perm entries
+        if (PF) {
+#pragma unroll
+        for (int m = 0; m < kPPT; ++m) {
+            const int k = base + m * kThreads + tid;
+            if (k < end) {
+                const int pidx = pn[m];
+                const bool from_main = pidx < nmain;
+                const PBuf<T> &src = from_main ? a.src_main : a.src_births;
+                const int si = from_main ? pidx : pidx - nmain;
+                const int slot = m * kThreads + tid;
+                for (int h = 0; h < (int)(sizeof(V) / 16); ++h) {
+                    cpa16(reinterpret_cast<char *>(st_q0 + slot) + 16 * h, reinterpret_cast<const char *>(src.q0 + si) + 16 * h);
+                    cpa16(reinterpret_cast<char *>(st_q1 + slot) + 16 * h, reinterpret_cast<const char *>(src.q1 + si) + 16 * h);
+                }
+                cpa8(st_id + slot, src.id + si);
+                cpa4(st_cell + slot, src.cell + si);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        {
+            const int nb = (ck + gridDim.x) * kChunk;
+#pragma unroll
+            for (int m = 0; m < kPPT; ++m) {
+                const int k = nb + m * kThreads + tid;
+                pn[m] = k < n ? a.perm[k] : 0;
+            }
+        }
+        }
         if (tid == 0) {
             const int pa = a.perm[base], pb = a.perm[end - 1];
             const int ca = pa < nmain ? a.src_main.cell[pa] : a.src_births.cell[pa - nmain];
@@ -519,6 +589,8 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
         __syncthreads();
         const int wi0 = s_w[0], wj0 = s_w[1], wz = s_w[2], wr = s_w[3];
         for (int k = tid; k < wz * wr; k += blockDim.x) win[k] = (T)0;
+        // each thread reads back only the slots it requested itself
+        if (PF) asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
 #pragma unroll 1
         for (int m = 0; m < kPPT; ++m) {
@@ -526,12 +598,22 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
             int out_cell = -1;
             T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
             if (k < end) {
-                const int pidx = a.perm[k];
-                const bool from_main = pidx < nmain;
-                const PBuf<T> &src = from_main ? a.src_main : a.src_births;
-                const int si = from_main ? pidx : pidx - nmain;
-                PS<T> p = load_p_fast(src, si, a.ncz, a.inv_ncz);
-                const uint64_t id = src.id[si];
+                PS<T> p;
+                uint64_t id;
+                if (PF) {
+                    const int slot = m * kThreads + tid;
+                    ld4(st_q0 + slot, p.oz, p.orr, p.vr, p.vt);
+                    ld4(st_q1 + slot, p.vz, p.ar, p.az, p.w);
+                    decode_cell(st_cell[slot], a.ncz, a.inv_ncz, p.i, p.j);
+                    id = st_id[slot];
+                } else {
+                    const int pidx = a.perm[k];
+                    const bool from_main = pidx < nmain;
+                    const PBuf<T> &src = from_main ? a.src_main : a.src_births;
+                    const int si = from_main ? pidx : pidx - nmain;
+                    p = load_p_fast(src, si, a.ncz, a.inv_ncz);
+                    id = src.id[si];
+                }
                 // gather E at x~ with the deposit's shape factors (Sec. 2.4)
                 T s0, s1;
                 shape_r(a.weighting, p.j, p.orr, s0, s1);
@@ -687,10 +769,20 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<T> a) {
 
 template <typename T>
 void launch_step(const StepArgs<T> &a, int grid, cudaStream_t st) {
-    const size_t smem = kWinBytes + (size_t)(a.eedf ? a.eedf_bins : 0) * sizeof(T);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_step<T><<<grid, kThreads, smem, st>>>(a);
+    // the ions' pass is latency-bound: it takes the prefetching variant
+    const bool pf = a.s == 1;
+    const size_t stage = (size_t)kChunk * (2 * sizeof(typename V4<T>::type) + sizeof(uint64_t) + sizeof(int32_t));
+    const size_t eedf = (size_t)(a.eedf ? a.eedf_bins : 0) * sizeof(T);
+    if (pf) {
+        const size_t smem = win_bytes<true>() + stage + eedf;
+        cudaFuncSetAttribute(k_step<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_step<T, true><<<grid, kThreads, smem, st>>>(a);
+    } else {
+        const size_t smem = win_bytes<false>() + eedf;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_step<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_step<T, false><<<grid, kThreads, smem, st>>>(a);
+    }
 }
 
 // ---------------------------------------------------------------------------
