@@ -26,9 +26,10 @@
 namespace pic {
 
 __global__ void k_finalize(const double *Ne, const double *Ni, const double *V, double q0,
-                           double q1, double c0, double c1, double *rho, double *chi, int ng) {
+                           double q1, double c0, double c1, double *rho, double *chi, int ng,
+                           const StepCtl *ctl) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ng) return;
+    if (k >= ng || (ctl && ctl->halt)) return;
     const double ne = Ne[k] / V[k], ni = Ni[k] / V[k];
     rho[k] = q0 * ne + q1 * ni;
     // chi = dt^2/(2 eps0) sum_s q_s^2 n_s / m_s ; c_s = q_s^2 dt^2 / (2 eps0 m_s)
@@ -36,8 +37,9 @@ __global__ void k_finalize(const double *Ne, const double *Ni, const double *V, 
 }
 
 void launch_finalize(const double *Ne, const double *Ni, const double *V, double q0, double q1,
-                     double c0, double c1, double *rho, double *chi, int ng, cudaStream_t st) {
-    k_finalize<<<(ng + 255) / 256, 256, 0, st>>>(Ne, Ni, V, q0, q1, c0, c1, rho, chi, ng);
+                     double c0, double c1, double *rho, double *chi, int ng, const StepCtl *ctl,
+                     cudaStream_t st) {
+    k_finalize<<<(ng + 255) / 256, 256, 0, st>>>(Ne, Ni, V, q0, q1, c0, c1, rho, chi, ng, ctl);
 }
 
 // ---- level set-up ----
@@ -411,9 +413,9 @@ int mg_solve(const FieldDims &fd, MGWork &mg, const double *rho, const double *c
 // and on r = R, E_r = 0 on the axis
 template <typename T>
 __global__ void k_efield(const double *phi, double *Ez, double *Er, typename V2<T>::type *E2,
-                         int nz, int nr, double dz, double dr) {
+                         int nz, int nr, double dz, double dr, const StepCtl *ctl) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nz * nr) return;
+    if (k >= nz * nr || (ctl && ctl->halt)) return;
     const int i = k / nr, j = k % nr;
     double ez, er;
     if (i == 0)
@@ -438,19 +440,19 @@ __global__ void k_efield(const double *phi, double *Ez, double *Er, typename V2<
 
 template <typename T>
 void launch_efield(const double *phi, double *Ez, double *Er, typename V2<T>::type *E2, int nz,
-                   int nr, double dz, double dr, cudaStream_t st) {
-    k_efield<T><<<nblk(nz * nr), 256, 0, st>>>(phi, Ez, Er, E2, nz, nr, dz, dr);
+                   int nr, double dz, double dr, const StepCtl *ctl, cudaStream_t st) {
+    k_efield<T><<<nblk(nz * nr), 256, 0, st>>>(phi, Ez, Er, E2, nz, nr, dz, dr, ctl);
 }
 template void launch_efield<float>(const double *, double *, double *, float2 *, int, int, double,
-                                   double, cudaStream_t);
+                                   double, const StepCtl *, cudaStream_t);
 template void launch_efield<double>(const double *, double *, double *, double2 *, int, int,
-                                    double, double, cudaStream_t);
+                                    double, double, const StepCtl *, cudaStream_t);
 
 __global__ void k_moments(const double *Ne, const double *Ni, const double *V, const double *phi,
                           const double *Ez, const double *Er, double *m_ne, double *m_ni,
-                          double *m_phi, double *m_ez, double *m_er, int ng) {
+                          double *m_phi, double *m_ez, double *m_er, int ng, const StepCtl *ctl) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ng) return;
+    if (k >= ng || (ctl && ctl->halt)) return;
     m_ne[k] += Ne[k] / V[k];
     m_ni[k] += Ni[k] / V[k];
     m_phi[k] += phi[k];
@@ -460,8 +462,8 @@ __global__ void k_moments(const double *Ne, const double *Ni, const double *V, c
 
 void launch_moments(const double *Ne, const double *Ni, const double *V, const double *phi,
                     const double *Ez, const double *Er, double *m_ne, double *m_ni, double *m_phi,
-                    double *m_ez, double *m_er, int ng, cudaStream_t st) {
-    k_moments<<<nblk(ng), 256, 0, st>>>(Ne, Ni, V, phi, Ez, Er, m_ne, m_ni, m_phi, m_ez, m_er, ng);
+                    double *m_ez, double *m_er, int ng, const StepCtl *ctl, cudaStream_t st) {
+    k_moments<<<nblk(ng), 256, 0, st>>>(Ne, Ni, V, phi, Ez, Er, m_ne, m_ni, m_phi, m_ez, m_er, ng, ctl);
 }
 
 }  // namespace pic

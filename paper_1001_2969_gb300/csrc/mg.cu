@@ -40,9 +40,10 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 
 // nodal chi of every coarse level: full weighting in z, injection on the
 // boundary rows; one warp per column, lanes over rows, levels in shared memory
-__global__ void k_chi_levels(const MGFast *__restrict__ mp, int nr) {
+__global__ void k_chi_levels(const MGFast *__restrict__ mp, int nr, const StepCtl *ctl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MGFast &m = *mp;
+    if (ctl && ctl->halt) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nz0 = m.nz[0];
     const int j = blockIdx.x * (blockDim.x >> 5) + warp;
     if (j >= nr) return;
@@ -67,10 +68,11 @@ __global__ void k_chi_levels(const MGFast *__restrict__ mp, int nr) {
 }
 
 // face coefficients of every level (flat index over all levels' nodes)
-__global__ void k_coefs_levels(const MGFast *__restrict__ mp, int nr, double dr, int face_mean, int total) {
+__global__ void k_coefs_levels(const MGFast *__restrict__ mp, int nr, double dr, int face_mean, int total,
+                               const StepCtl *ctl) {
     const MGFast &m = *mp;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= total) return;
+    if (g >= total || (ctl && ctl->halt)) return;
     int l = 0, k = g;
     while (k >= m.nz[l] * nr) {
         k -= m.nz[l] * nr;
@@ -141,8 +143,10 @@ inline int line_chunk(int n) {
 
 // One warp per line over all lines of levels [l0, l1).  Computed in Ts.
 template <typename Ts>
-__global__ void k_factor_lines(const MGFast *__restrict__ mp, int l0, int l1, int nr, int M, int nlines) {
+__global__ void k_factor_lines(const MGFast *__restrict__ mp, int l0, int l1, int nr, int M, int nlines,
+                               const StepCtl *ctl) {
     const MGFast &m = *mp;
+    if (ctl && ctl->halt) return;
     const int n = nr - 1;
     const int p = threadIdx.x & 31;
     int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -298,10 +302,11 @@ __device__ __forceinline__ void warp_line_solve(const Ts *__restrict__ F, Ts *Bs
 
 // right-hand side rho A_j dz / eps0 and the Dirichlet data of phi
 __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, double *phi, const double *phi_zL,
-                         double V, int nz, int nr, double dz, double dr, int cold) {
+                         double V_arg, int nz, int nr, double dz, double dr, int cold, const StepCtl *ctl) {
     const MGFast &m = *mp;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nz * nr) return;
+    if (k >= nz * nr || (ctl && ctl->halt)) return;
+    const double V = ctl ? ctl->V : V_arg;  // in a timestep the voltage comes with the step
     const int i = k / nr, j = k % nr;
     double v = 0.0, dg = 0.0;
     if (i > 0 && i < nz - 1 && j < nr - 1) {
@@ -343,46 +348,7 @@ __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, doubl
 // the first kBarGroup blocks, separated by a barrier among those blocks only;
 // the rest of the grid waits at the next full barrier.
 // ---------------------------------------------------------------------------
-constexpr long long kSpinLimit = 1LL << 26;
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void atom_add_release(unsigned *p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Barrier on a counter that only grows: thread 0 of each block adds 1 with
-// release semantics and polls with acquire loads until the counter reaches
-// the target of this barrier (its number of participants times the number
-// of barriers of this kind the block has passed).  The block's writes before
-// the barrier are visible to every participant after it.  The poll is
-// bounded: after kSpinLimit tries (or once another block gave up) the block
-// raises `timeout` and returns false.
 constexpr int kBarGroup = 8;  // blocks that sweep the coarse levels alone
-
-__device__ __forceinline__ bool count_barrier(unsigned *count, unsigned target, MGCtl *ctl) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        atom_add_release(count, 1u);
-        long long it = 0;
-        while ((int)(ld_acquire(count) - target) < 0) {
-            if ((++it & 255) == 0 && (it > kSpinLimit || *(volatile int *)&ctl->timeout)) {
-                atomicExch(&ctl->timeout, 1);
-                ok = 0;
-                break;
-            }
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 // ---- factor lines into shared memory ----
 // A line's factors move in one bulk copy that completes on the region's
@@ -451,10 +417,12 @@ constexpr int kUL = 4;  // unknowns per thread and batch of a level's right-hand
 
 template <typename Tv, int M>
 __global__ void __launch_bounds__(kSolveThreads, 1)
-    k_solve_persistent(const MGFast *__restrict__ mp, double *phi, int nr, int first_cycle, SolveLayout lay) {
+    k_solve_persistent(const MGFast *__restrict__ mp, double *phi, int nr, int first_cycle, SolveLayout lay,
+                       double tol, int max_cycles, const StepCtl *sctl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MGFast &m = *mp;
     MGCtl *ctl = m.ctl;
+    if (sctl && sctl->halt) return;  // an earlier failure of this step
     const int n = nr - 1, nz0 = m.nz[0], ng = nz0 * nr, L = m.nlev - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
     constexpr int NW = kLine * M;  // unknowns of a line with its padding
@@ -648,7 +616,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
                 }
             }
         }
-        if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
+        if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
             leave(false);
             return;
         }
@@ -659,10 +627,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
             int d = 0;  // 0 continue, 1 converged, 2 out of cycles, 3 zero right-hand side
             if (bn == 0.0)
                 d = 3;
-            else if (ctl->tol > 0.0 && rn <= ctl->tol * bn)
+            else if (tol > 0.0 && rn <= tol * bn)
                 d = 1;
-            else if (cyc >= ctl->max_cycles)
-                d = ctl->tol > 0.0 ? 2 : 1;
+            else if (cyc >= max_cycles)
+                d = tol > 0.0 ? 2 : 1;
             s_decide = d;
             if (blockIdx.x == 0) {
                 ctl->last_res = rn;
@@ -723,7 +691,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
                 __syncthreads();
                 for (int j = tid; j < n; j += nt) phi[(size_t)nr + j] = BC[at(j)];
             }
-            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
+            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
                 leave(false);
                 return;
             }
@@ -732,7 +700,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
         // level 0's sweeps rewrite delta: when they run in the group alone,
         // every block's update of phi has to be in first
         if (lb == 0)
-            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl)) {
+            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
                 leave(false);
                 return;
             }
@@ -869,9 +837,9 @@ __global__ void __launch_bounds__(kSolveThreads, 1)
             // every other level boundary is a grid barrier
             bool ok;
             if (l > 0 && grp && l - 1 >= lb)
-                ok = in_group ? count_barrier(&ctl->gbar_count.v, (++ngroup) * G, ctl) : true;
+                ok = in_group ? count_barrier(&ctl->gbar_count.v, (++ngroup) * G, &ctl->timeout) : true;
             else
-                ok = count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, ctl);
+                ok = count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout);
             if (!ok) {
                 leave(false);
                 return;
@@ -922,45 +890,70 @@ void raise_smem_limits() {
 
 }  // namespace
 
+namespace {
+
+// a timestep's solve reports to the step control instead of the host: V-cycle
+// count, residual, an unconverged flag, and a halt on a timed-out wait
+__global__ void k_solve_done(const MGCtl *c, StepCtl *s) {
+    if (s->halt) return;
+    if (c->timeout) {
+        s->halt = 1;
+        s->halt_status = ST_TIMEOUT;
+        s->halt_step = s->step;
+        return;
+    }
+    const int cyc = c->zero_rhs ? 0 : c->cycles;
+    s->mg_cycles += (unsigned long long)cyc;
+    s->mg_last_cycles = cyc;
+    s->mg_last_res = (c->zero_rhs || !(c->bnorm > 0.0)) ? 0.0 : c->last_res / c->bnorm;
+    if (!c->zero_rhs && !c->converged) s->mg_flags |= 1;
+}
+
+}  // namespace
+
+void mg_fast_upload(MGFast &m, cudaStream_t st) {
+    cudaMemcpyAsync(m.self, &m, sizeof(MGFast), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+}
+
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
-                  int max_cycles, double *rel_res, int *launches, cudaStream_t st) {
+                  int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st) {
     const int nz = fd.nz, nr = fd.nr, n = nr - 1, ng = nz * nr;
     const int M = line_chunk(n);
     const int nlev = m.nlev;
     int L = 0;
     raise_smem_limits();
-    MGFast *mp = m.self;
-    cudaMemcpyAsync(mp, &m, sizeof(MGFast), cudaMemcpyHostToDevice, st);
+    MGFast *mp = m.self;  // uploaded once (mg_fast_upload)
     // set-up: levels' chi, coefficients, line factors, right-hand side and boundary data
     cudaMemcpyAsync(m.chi[0], chi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st);
     if (nlev > 1) {
-        k_chi_levels<<<(nr + 7) / 8, 256, (size_t)8 * 2 * nz * sizeof(double), st>>>(mp, nr);
+        k_chi_levels<<<(nr + 7) / 8, 256, (size_t)8 * 2 * nz * sizeof(double), st>>>(mp, nr, sctl);
         ++L;
     }
     int total = 0;
     for (int l = 0; l < nlev; ++l) total += m.nz[l] * nr;
     k_coefs_levels<<<(total + 255) / 256, 256, 0, st>>>(mp, nr, fd.dr, fd.chi_face == PIC_CHI_MEAN,
-                                                         total);
+                                                         total, sctl);
     ++L;
     {
         // line factors in the V-cycle's type; one warp per line
         int lines_all = 0;
         for (int l = 0; l < nlev; ++l) lines_all += m.nz[l] - 2;
         if (!mixed) {
-            k_factor_lines<double><<<(lines_all + 7) / 8, 256, 0, st>>>(mp, 0, nlev, nr, M, lines_all);
+            k_factor_lines<double><<<(lines_all + 7) / 8, 256, 0, st>>>(mp, 0, nlev, nr, M, lines_all, sctl);
             ++L;
         } else if (nlev > 1) {
-            k_factor_lines<float><<<(lines_all + 7) / 8, 256, 0, st>>>(mp, 0, nlev, nr, M, lines_all);
+            k_factor_lines<float><<<(lines_all + 7) / 8, 256, 0, st>>>(mp, 0, nlev, nr, M, lines_all, sctl);
             ++L;
         } else {
             // nz = 3: the single row is phi's own, solved in FP64
-            k_factor_lines<double><<<1, 32, 0, st>>>(mp, 0, 1, nr, M, 1);
+            k_factor_lines<double><<<1, 32, 0, st>>>(mp, 0, 1, nr, M, 1, sctl);
             ++L;
         }
     }
     k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(mp, rho, phi, phi_zL, V, nz, nr, fd.dz, fd.dr,
-                                               warm ? 0 : 1);
+                                               warm ? 0 : 1, sctl);
     ++L;
     // the solve alternates between phi and a copy (both carry the boundary values)
     cudaMemcpyAsync(m.phi2, phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st);
@@ -969,11 +962,7 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
         cudaMemsetAsync(m.u32[0], 0, sizeof(float) * ng, st);
     else
         cudaMemsetAsync(m.u64[0], 0, sizeof(double) * ng, st);
-    MGCtl c0;
-    memset(&c0, 0, sizeof(c0));
-    c0.tol = tol;
-    c0.max_cycles = max_cycles;
-    cudaMemcpyAsync(m.ctl, &c0, sizeof(MGCtl), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(m.ctl, 0, sizeof(MGCtl), st);
     // all cycles in one cooperative launch
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -1005,12 +994,25 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
         return kSolveNoLaunch;
     }
     const int grid = std::max(1, std::min(nsm * per_sm, std::min(nsm, (nz - 1) / 2)));
-    int first_cycle = 1, nrv = nr;
-    void *args[] = {(void *)&mp, (void *)&phi, (void *)&nrv, (void *)&first_cycle, (void *)&lay};
+    int first_cycle = 1, nrv = nr, mc = max_cycles;
+    double tv = tol;
+    const StepCtl *sc = sctl;
+    void *args[] = {(void *)&mp, (void *)&phi, (void *)&nrv, (void *)&first_cycle, (void *)&lay,
+                    (void *)&tv, (void *)&mc, (void *)&sc};
     const cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kSolveThreads, args, sp, st);
     ++L;
+    if (e != cudaSuccess) {
+        if (launches) *launches += L;
+        return kSolveNoLaunch;
+    }
+    if (sctl) {
+        // inside a timestep: the result stays on the device
+        k_solve_done<<<1, 1, 0, st>>>(m.ctl, sctl);
+        ++L;
+        if (launches) *launches += L;
+        return 0;
+    }
     if (launches) *launches += L;
-    if (e != cudaSuccess) return kSolveNoLaunch;
     MGCtl ch;
     cudaMemcpyAsync(&ch, m.ctl, sizeof(MGCtl), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);

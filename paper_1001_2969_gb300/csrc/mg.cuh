@@ -5,15 +5,12 @@
 
 namespace pic {
 
-// device-side control of one solve: the residual kernel's last block fills
-// it and raises `done`; the other kernels of a cycle return early once done
+// device-side control of one solve (the one-launch V-cycles)
 struct MGCtl {
-    unsigned long long res_bits;  // max |r| of the current cycle (bits of a positive double)
-    unsigned long long b_bits;    // max |b| (first cycle)
-    unsigned long long rb[2];     // per-cycle max |r| of the one-launch solve (alternating)
-    unsigned int blocks_in;
-    int done, converged, zero_rhs, cycles, max_cycles, timeout;
-    double tol, last_res, bnorm;
+    unsigned long long b_bits;  // max |b| (first cycle), bits of a positive double
+    unsigned long long rb[2];   // per-cycle max |r| (alternating)
+    int converged, zero_rhs, cycles, timeout;
+    double last_res, bnorm;
     // barrier counters of the one-launch solve (whole grid; the coarse
     // levels' group of blocks), each on its own cache line
     struct alignas(128) Line {
@@ -58,9 +55,16 @@ struct MGFast {
 // (the same count in FP32 and FP64)
 size_t mg_line_factor_elems(int nr);
 
-// solve into phi; returns the cycles (>= 0, converged) or -cycles-1
+// copy the level table to the device (once: its pointers do not change)
+void mg_fast_upload(MGFast &m, cudaStream_t st);
+
+// Solve into phi.  Alone (sctl null): returns the cycles (>= 0, converged)
+// or -cycles-1, after a host synchronisation.  Inside a timestep (sctl set):
+// enqueues the work only, takes the voltage from sctl->V, skips everything
+// once sctl->halt is set, reports cycles, residual and failures to sctl, and
+// returns 0 (or kSolveNoLaunch).
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
-                  int max_cycles, double *rel_res, int *launches, cudaStream_t st);
+                  int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st);
 
 }  // namespace pic

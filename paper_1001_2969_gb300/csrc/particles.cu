@@ -362,15 +362,15 @@ __device__ void emit_birth(const StepArgs<T> &a, BlockTally *bt, int ts, int ps,
 
 // null-collision Monte Carlo (Sec. 2.6) on the post-final-push state
 template <typename T>
-__device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, uint64_t id,
+__device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, uint64_t id, uint32_t step,
                                         PS<T> &p) {
-    const uint4 x = draw(a.key0, a.key1, id, a.step, 0, a.s);
+    const uint4 x = draw(a.key0, a.key1, id, step, 0, a.s);
     if ((unsigned long long)x.x >= a.t_null) return;
     atomicAdd(&bt->cnt[PIC_C_CAND + a.s], 1ull);
     T gx = p.vr, gy = p.vt, gz = p.vz;
     T vnx = 0, vny = 0, vnz = 0;
     if (a.s == 1) {
-        const uint4 y = draw(a.key0, a.key1, id, a.step, 1, a.s);
+        const uint4 y = draw(a.key0, a.key1, id, step, 1, a.s);
         T n0, n1, n2, n3;
         normals(y.x, y.y, n0, n1);
         normals(y.z, y.w, n2, n3);
@@ -432,8 +432,8 @@ __device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, ui
         p.vt = gn * dy;
         p.vz = gn * dz;
     } else {  // ionisation
-        const uint4 y = draw(a.key0, a.key1, id, a.step, 1, a.s);
-        const uint4 zz = draw(a.key0, a.key1, id, a.step, 2, a.s);
+        const uint4 y = draw(a.key0, a.key1, id, step, 1, a.s);
+        const uint4 zz = draw(a.key0, a.key1, id, step, 2, a.s);
         const T Eej = a.xs.B * m_tan(unif<T>(y.x) * m_atan((E - thr) / ((T)2 * a.xs.B)));
         T Esc = E - thr - Eej;
         if (Esc < (T)0) Esc = (T)0;
@@ -515,6 +515,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     __shared__ BlockTally bt;
     __shared__ int s_w[4];
     const int tid = threadIdx.x, lane = tid & 31;
+    if (a.ctl->halt) return;  // an earlier failure of this step
+    const uint32_t step = (uint32_t)a.ctl->step;  // Philox counter word
+    const bool do_split = a.ctl->do_split != 0;
     for (int k = tid; k < PIC_NCOUNT; k += blockDim.x) bt.cnt[k] = 0;
     if (tid < 3) bt.q[tid] = 0.0;
     if (a.eedf)
@@ -660,14 +663,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                     alive = false;
                 }
                 if (alive) {
-                    collide(a, &bt, id, p);
+                    collide(a, &bt, id, step, p);
                     if (a.eedf) {
                         const T Ek = a.half_m_e * (p.vr * p.vr + p.vt * p.vt + p.vz * p.vz);
                         const T x = Ek * a.eedf_scale;
                         if (x >= (T)0 && x < (T)a.eedf_bins)
                             atomicAdd(&s_eedf[(int)x], p.w);
                     }
-                    if (a.do_split) {  // weight-conserving split (Sec. 2.2)
+                    if (do_split) {  // weight-conserving split (Sec. 2.2)
                         const T wr_ = a.w_ref[p.j];
                         if (p.w > wr_) {
                             T Nf = m_floor(p.w / wr_);

@@ -19,7 +19,6 @@ using namespace pic;
 namespace {
 
 constexpr int kNumTiming = 5;  // solve, particle pass e, particle pass i, sort+births, other
-constexpr int kSmallBirthsHost = 2048;
 
 struct RawBuf {
     void *q0 = nullptr, *q1 = nullptr;
@@ -47,13 +46,19 @@ struct SpecDev {
     void *sig4 = nullptr;   // T[n_e][4], channels interleaved
     void *w_ref = nullptr;  // T[ncr]
     int64_t cap = 0, bcap = 0;
-    uint64_t next_id = 0;
-    int64_t n_alive_host = 0;
+    uint64_t next_id = 0;  // host copy of the device's step control
 };
 
 struct EvRec {
     int phase;
     cudaEvent_t a, b;
+};
+
+// one timestep captured as a CUDA graph, per parity of the current buffer set
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;  // kernels in the graph
+    bool failed = false;   // capture or instantiation failed: launch directly
 };
 
 }  // namespace
@@ -68,6 +73,8 @@ struct pic_handle {
     cudaStream_t st = nullptr;
     std::vector<std::pair<void *, size_t>> allocs;
     DevScalars *ds = nullptr;
+    StepCtl *sctl = nullptr;  // step control (device)
+    double *rf_d = nullptr;   // rf table on the device: amplitudes, frequencies, phases
     int32_t *scal = nullptr;  // per-species device scalars (n_main, n_births, n_alive, n_total)
     SpecDev sp[2];
     int cur = 0;
@@ -81,11 +88,16 @@ struct pic_handle {
     double *tmp_grid[3] = {nullptr, nullptr, nullptr};
     MGFast mgf;
     RadixTmp rtmp;
-    int64_t step = 0;
+    int64_t step = 0;  // host copy of the device's step number (exact after each call)
     int64_t nsamples = 0;
-    int64_t mg_cycles_total = 0, steps_total = 0;
+    int64_t mg_cycles_total = 0, steps_total = 0;  // host copies (device step control)
     int last_cycles = 0;
     double last_res = 0.0;
+    int step_grid = 1;  // blocks of the particle pass (they walk the chunks)
+    cudaStream_t user_st = nullptr;  // the caller's stream
+    cudaStream_t gst = nullptr;      // private stream the step graphs are captured on and run on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    StepGraph graphs[2];
     double ngas = 0.0, nu_max[2] = {0, 0}, p_null[2] = {0, 0};
     unsigned long long t_null[2] = {0, 0};
     std::string err;
@@ -209,13 +221,6 @@ pic_status validate(const pic_config *c, std::string &why) {
     return PIC_OK;
 }
 
-double voltage(const pic_handle *h, double t) {
-    double v = 0.0;
-    for (int k = 0; k < h->cfg.rf.n; ++k)
-        v += h->own_rf[k] * sin(2.0 * kPi * h->own_rf[h->cfg.rf.n + k] * t + h->own_rf[2 * h->cfg.rf.n + k]);
-    return v;
-}
-
 // node volumes of Sec. 2.4 (z-r^2 or z-r), inner halves on the boundary rows
 // and on r = R
 void node_volumes(const pic_handle *h, std::vector<double> &V) {
@@ -253,6 +258,38 @@ __global__ void k_iota(int32_t *p, int n) {
 __global__ void k_scale(const double *src, double *dst, int n, double f) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) dst[k] = src[k] * f;
+}
+
+// step prologue: the field time's electrode voltage (Sec. 2.5 boundary data)
+// and the split flag, from the step number on the device
+__global__ void k_step_begin(StepCtl *c, const double *rf, int nrf, double dt, int split_every) {
+    if (c->halt) return;
+    const double t = (double)(c->step + 1) * dt;
+    double v = 0.0;
+    for (int k = 0; k < nrf; ++k) v += rf[k] * sin(2.0 * kPi * rf[nrf + k] * t + rf[2 * nrf + k]);
+    c->V = v;
+    c->do_split = split_every > 0 && (c->step % split_every) == split_every - 1;
+}
+
+// step epilogue: the new particle counts take effect and the step advances
+__global__ void k_step_end(StepCtl *c, int32_t *nalive0, const int32_t *ntotal0, int32_t *nalive1,
+                           const int32_t *ntotal1) {
+    if (c->halt) return;
+    *nalive0 = *ntotal0;
+    *nalive1 = *ntotal1;
+    c->step += 1;
+}
+
+// host values the device's step control starts from
+void push_ctl(pic_handle *h) {
+    StepCtl c;
+    cudaMemcpyAsync(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    c.step = h->step;
+    c.next_id[0] = h->sp[0].next_id;
+    c.next_id[1] = h->sp[1].next_id;
+    cudaMemcpyAsync(h->sctl, &c, sizeof(StepCtl), cudaMemcpyHostToDevice, h->st);
+    cudaStreamSynchronize(h->st);
 }
 
 cudaEvent_t ev_get(pic_handle *h) {
@@ -337,6 +374,17 @@ void setup_device(pic_handle *h) {
     const size_t ts = h->mixed ? sizeof(float) : sizeof(double);
     h->ds = (DevScalars *)dalloc(h, sizeof(DevScalars));
     cudaMemsetAsync(h->ds, 0, sizeof(DevScalars), h->st);
+    {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        h->step_grid = std::max(1, nsm * 8);
+    }
+    h->sctl = (StepCtl *)dalloc(h, sizeof(StepCtl));
+    cudaMemsetAsync(h->sctl, 0, sizeof(StepCtl), h->st);
+    h->rf_d = (double *)dalloc(h, std::max<size_t>(1, h->own_rf.size()) * sizeof(double));
+    if (!h->own_rf.empty())
+        cudaMemcpyAsync(h->rf_d, h->own_rf.data(), h->own_rf.size() * sizeof(double), cudaMemcpyHostToDevice, h->st);
     h->scal = (int32_t *)dalloc(h, 2 * 8 * sizeof(int32_t));
     cudaMemsetAsync(h->scal, 0, 2 * 8 * sizeof(int32_t), h->st);
     for (int s = 0; s < 2; ++s) {
@@ -427,6 +475,7 @@ void setup_device(pic_handle *h) {
     m.phi2 = (double *)dalloc(h, gb);
     m.ctl = (MGCtl *)dalloc(h, sizeof(MGCtl));
     m.self = (MGFast *)dalloc(h, sizeof(MGFast));
+    mg_fast_upload(m, h->st);
     // births radix scratch
     int64_t bmax = std::max(h->sp[0].bcap, h->sp[1].bcap);
     h->rtmp.max_n = (int)bmax;
@@ -435,6 +484,7 @@ void setup_device(pic_handle *h) {
     h->rtmp.v0 = (uint32_t *)dalloc(h, (size_t)bmax * 4);
     h->rtmp.v1 = (uint32_t *)dalloc(h, (size_t)bmax * 4);
     h->rtmp.hist = (uint32_t *)dalloc(h, (size_t)256 * (bmax / 2048 + 2) * 4);
+    h->rtmp.flag = (int *)dalloc(h, sizeof(int));
     if (h->mixed)
         alloc_tables<float>(h);
     else
@@ -467,12 +517,12 @@ pic_status load_all(pic_handle *h) {
         const int32_t vals[8] = {(int32_t)n, 0, 0, 0, (int32_t)n, (int32_t)n, 0, 0};
         cudaMemcpyAsync(h->scal + s * 8, vals, sizeof(vals), cudaMemcpyHostToDevice, h->st);
         d.next_id = (uint64_t)n;
-        d.n_alive_host = n;
         h->launches += 2;
     }
     h->cur = 0;
     deposit_current<T>(h);
     cudaStreamSynchronize(h->st);
+    push_ctl(h);
     return cuda_check(h, "load");
 }
 
@@ -521,9 +571,7 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     a.xs.B = (T)x.B_eV;
     a.key0 = (uint32_t)h->cfg.seed;
     a.key1 = (uint32_t)(h->cfg.seed >> 32);
-    a.step = (uint32_t)h->step;
-    a.do_split = h->cfg.split_every > 0 &&
-                 (h->step % h->cfg.split_every) == h->cfg.split_every - 1;
+    a.ctl = h->sctl;
     a.w_ref = (const T *)h->sp[s].w_ref;
     a.E = (const typename V2<T>::type *)h->E2;
     SpecDev &d = h->sp[s];
@@ -547,45 +595,27 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     a.eedf_scale = h->cfg.eedf_bins > 0 ? (T)(h->cfg.eedf_bins / h->cfg.eedf_emax_eV) : (T)0;
 }
 
-struct StepHost {
-    int32_t n_births[2];
-    int32_t n_total[2];
-    int32_t status;
-};
-
+// Enqueues one timestep (Sec. 2.1 merged cycle) without a host
+// synchronisation; failures halt the step on the device (StepCtl) and are
+// resolved by pic_step after the last step of the call.
 template <typename T>
-pic_status one_step(pic_handle *h) {
+void one_step(pic_handle *h) {
     cudaStream_t st = h->st;
-    pic_status result = PIC_OK;
     const int src = h->cur, dst = 1 - h->cur;
     {
         PhaseTimer t(h, 0);
+        k_step_begin<<<1, 1, 0, st>>>(h->sctl, h->rf_d, h->cfg.rf.n, h->cfg.dt, h->cfg.split_every);
         launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q,
                         h->cfg.sp[0].q * h->cfg.sp[0].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[0].m),
                         h->cfg.sp[1].q * h->cfg.sp[1].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[1].m),
-                        h->rho, h->chi, h->ng, st);
-        const double Vt = voltage(h, (double)(h->step + 1) * h->cfg.dt);
+                        h->rho, h->chi, h->ng, h->sctl, st);
         FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
         int L = 0;
-        double res = 0.0;
-        const int r = mg_fast_solve(fd, h->mgf, h->rho, h->chi, Vt,
-                                    h->has_phiL ? h->phiL_d : nullptr, h->phi, true, h->mixed,
-                                    h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, st);
-        if (r == kSolveTimeout) {
-            h->launches += L;
-            return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
-        }
-        if (r == kSolveNoLaunch) {
-            h->launches += L;
-            return fail(h, PIC_ERR_CUDA, "multigrid solve could not be launched");
-        }
-        h->last_cycles = r >= 0 ? r : -r - 1;
-        h->last_res = res;
-        h->mg_cycles_total += h->last_cycles;
-        if (r < 0) result = PIC_ERR_NOT_CONVERGED;
+        mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi, true,
+                      h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st);
         launch_efield<T>(h->phi, h->Ez, h->Er, (typename V2<T>::type *)h->E2, h->nz, h->nr, h->dz,
-                         h->dr, st);
-        h->launches += L + 2;
+                         h->dr, h->sctl, st);
+        h->launches += L + 3;
     }
     for (int s = 0; s < 2; ++s) {
         cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), st);
@@ -596,9 +626,8 @@ pic_status one_step(pic_handle *h) {
         PhaseTimer t(h, 1 + s);
         StepArgs<T> a;
         fill_step_args<T>(h, a, s, src, dst);
-        const int64_t nch = (h->sp[s].n_alive_host + kStepChunk - 1) / kStepChunk;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nch, 152 * 8));
-        launch_step<T>(a, grid, st);
+        // blocks walk the chunks of the count on the device
+        launch_step<T>(a, h->step_grid, st);
         h->launches += 1;
         h->particle_launches += 1;
     }
@@ -608,65 +637,74 @@ pic_status one_step(pic_handle *h) {
             SpecDev &d = h->sp[s];
             // entries the pass wrote into the destination main buffer
             cudaMemcpyAsync(d.d_nmain[dst], d.d_nalive, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-            launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, st);
-            launch_rank<T>(view<T>(d.main[dst]), d.d_nmain[dst], view<T>(d.births[dst]),
-                           d.d_nbirths[dst], d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, st);
-            h->launches += 4;
+            launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, h->sctl, st);
+            h->launches += 3;
         }
-        StepHost sh;
+        // capacity and births overflow: the step halts before any permutation changes
+        launch_step_check(h->ds, h->sctl, st);
         for (int s = 0; s < 2; ++s) {
-            cudaMemcpyAsync(&sh.n_births[s], h->sp[s].d_nbirths[dst], 4, cudaMemcpyDeviceToHost, st);
-            cudaMemcpyAsync(&sh.n_total[s], h->sp[s].d_ntotal, 4, cudaMemcpyDeviceToHost, st);
-        }
-        cudaMemcpyAsync(&sh.status, &h->ds->status, 4, cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
-        pic_status ce = cuda_check(h, "particle pass");
-        if (ce != PIC_OK) return ce;
-        if (sh.status & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
-            // leave the state at the last completed step
-            cudaMemsetAsync(&h->ds->status, 0, 4, st);
-            deposit_current<T>(h);
-            cudaStreamSynchronize(st);
-            return fail(h, PIC_ERR_CAPACITY, (sh.status & ST_CAPACITY)
-                                                 ? "particle capacity exceeded"
-                                                 : "births capacity exceeded");
+            SpecDev &d = h->sp[s];
+            launch_rank<T>(view<T>(d.main[dst]), d.d_nmain[dst], view<T>(d.births[dst]),
+                           d.d_nbirths[dst], d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->sctl, st);
         }
         for (int s = 0; s < 2; ++s) {
             SpecDev &d = h->sp[s];
-            const int nb = sh.n_births[s];
-            if (nb > 0) {
-                if (nb <= kSmallBirthsHost) {
-                    launch_birth_ids_small(d.bkey[dst], d.births[dst].id, nb, d.next_id, st);
-                    h->launches += 1;
-                } else {
-                    int L = 0;
-                    launch_birth_ids_radix(d.bkey[dst], d.births[dst].id, nb, d.next_id, h->rtmp, &L, st);
-                    h->launches += L;
-                }
-                d.next_id += (uint64_t)nb;
-            }
-            cudaMemcpyAsync(d.d_nalive, d.d_ntotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-            d.n_alive_host = sh.n_total[s];
+            launch_birth_ids(d.bkey[dst], d.births[dst].id, d.d_nbirths[dst], h->sctl, s, h->rtmp, st);
         }
-        if (sh.status & ST_NAN) {
-            cudaMemsetAsync(&h->ds->status, 0, 4, st);
-            result = PIC_ERR_NUMERIC;
-            h->err = "non-finite particle state (particles dropped)";
-        }
+        h->launches += 5;
     }
     {
         PhaseTimer t(h, 4);
         launch_moments(h->N[0], h->N[1], h->V, h->phi, h->Ez, h->Er, h->m_acc[0], h->m_acc[1],
-                       h->m_acc[2], h->m_acc[3], h->m_acc[4], h->ng, st);
-        h->launches += 1;
+                       h->m_acc[2], h->m_acc[3], h->m_acc[4], h->ng, h->sctl, st);
+        k_step_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nalive, h->sp[0].d_ntotal, h->sp[1].d_nalive,
+                                     h->sp[1].d_ntotal);
+        h->launches += 2;
     }
-    h->nsamples += 1;
-    h->steps_total += 1;
     h->cur = dst;
-    h->step += 1;
-    pic_status ce = cuda_check(h, "step");
-    if (ce != PIC_OK) return ce;
-    return result;
+}
+
+void drop_graphs(pic_handle *h) {
+    for (auto &g : h->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = StepGraph();
+    }
+}
+
+void destroy_streams(pic_handle *h) {
+    drop_graphs(h);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->gst) cudaStreamDestroy(h->gst);
+    h->ev_in = h->ev_out = nullptr;
+    h->gst = nullptr;
+}
+
+// capture one step (from the current parity) on the private stream
+template <typename T>
+void capture_step(pic_handle *h, StepGraph &g) {
+    const int cur = h->cur;
+    const int64_t L0 = h->launches, P0 = h->particle_launches;
+    cudaStream_t keep = h->st;
+    h->st = h->gst;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        one_step<T>(h);
+        e = cudaStreamEndCapture(h->gst, &graph);
+    }
+    h->st = keep;
+    h->cur = cur;
+    g.launches = h->launches - L0;
+    h->launches = L0;
+    h->particle_launches = P0;
+    if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || !g.exec) {
+        g.exec = nullptr;
+        g.failed = true;
+        cudaGetLastError();
+    }
 }
 
 void release(pic_handle *h, void *p) {
@@ -704,17 +742,17 @@ pic_status set_particles_t(pic_handle *h, int s, const pic_particles_view *v) {
     cudaMemcpyAsync(d.d_nbirths[c], &zero, 4, cudaMemcpyHostToDevice, h->st);
     cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), h->st);
     launch_hist<T>(view<T>(d.main[c]), d.d_nmain[c], d.counts, h->st);
-    launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, h->st);
+    launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, nullptr, h->st);
     launch_rank<T>(view<T>(d.main[c]), d.d_nmain[c], view<T>(d.births[c]), d.d_nbirths[c],
-                   d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->st);
+                   d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, nullptr, h->st);
     cudaMemcpyAsync(d.d_nalive, d.d_ntotal, 4, cudaMemcpyDeviceToDevice, h->st);
     h->launches += 6;
     d.next_id = mx;
-    d.n_alive_host = n;
     deposit_current<T>(h);
     cudaStreamSynchronize(h->st);
     if (stage) release(h, stage);
     if (sid) release(h, sid);
+    push_ctl(h);
     return cuda_check(h, "set_particles");
 }
 
@@ -783,6 +821,13 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out) {
     if (!h) return PIC_ERR_ARG;
     h->cfg = *cfg;
     h->st = (cudaStream_t)cfg->stream;
+    h->user_st = h->st;
+    if (cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking) != cudaSuccess) {
+        h->gst = nullptr;
+        cudaGetLastError();
+    }
+    cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
     for (int s = 0; s < 2; ++s) {
         const pic_xsec &x = cfg->xs[s];
         h->own_sigma[s].assign(x.sigma_m2, x.sigma_m2 + (size_t)x.n_ch * x.n_e);
@@ -825,12 +870,14 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out) {
         if (s != PIC_OK) {
             fprintf(stderr, "pic_init: %s\n", h->err.c_str());
             free_all(h);
+            destroy_streams(h);
             delete h;
             return s;
         }
     } catch (const std::bad_alloc &) {
         fprintf(stderr, "pic_init: device allocation failed\n");
         free_all(h);
+        destroy_streams(h);
         delete h;
         return PIC_ERR_CUDA;
     }
@@ -841,16 +888,96 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out) {
 pic_status pic_step(pic_handle *h, int32_t nsteps) {
     if (!h) return PIC_ERR_ARG;
     if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps < 0");
-    pic_status first = PIC_OK;
+    if (nsteps == 0) return PIC_OK;
+    const int64_t step0 = h->step;
+    const int cur0 = h->cur;
+    // steps run as graph replays on the private stream, ordered after the
+    // caller's stream and before it again; with profiling on they launch
+    // one by one on the caller's stream (phase timers)
+    bool on_gst = false;
     for (int k = 0; k < nsteps; ++k) {
-        pic_status s = h->mixed ? one_step<float>(h) : one_step<double>(h);
-        if (s == PIC_ERR_NOT_CONVERGED || s == PIC_ERR_NUMERIC) {
-            if (first == PIC_OK) first = s;
+        StepGraph &g = h->graphs[h->cur];
+        if (!h->prof && h->gst && !g.exec && !g.failed) {
+            if (h->mixed)
+                capture_step<float>(h, g);
+            else
+                capture_step<double>(h, g);
+        }
+        if (!h->prof && g.exec) {
+            if (!on_gst) {
+                cudaEventRecord(h->ev_in, h->st);
+                cudaStreamWaitEvent(h->gst, h->ev_in, 0);
+                on_gst = true;
+            }
+            cudaGraphLaunch(g.exec, h->gst);
+            h->launches += g.launches;
+            h->particle_launches += 2;
+            h->cur ^= 1;
             continue;
         }
-        if (s != PIC_OK) return s;
+        if (on_gst) {
+            cudaEventRecord(h->ev_out, h->gst);
+            cudaStreamWaitEvent(h->st, h->ev_out, 0);
+            on_gst = false;
+        }
+        if (h->mixed)
+            one_step<float>(h);
+        else
+            one_step<double>(h);
     }
-    return first;
+    if (on_gst) {
+        cudaEventRecord(h->ev_out, h->gst);
+        cudaStreamWaitEvent(h->st, h->ev_out, 0);
+    }
+    // the one synchronisation of the call: the step control and the status word
+    StepCtl c;
+    int32_t status = 0;
+    cudaMemcpyAsync(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(&status, &h->ds->status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    pic_status ce = cuda_check(h, "step");
+    if (ce != PIC_OK) return ce;
+    const int64_t done = c.halt ? c.halt_step - step0 : (int64_t)nsteps;
+    h->cur = (int)(cur0 ^ (int)(done & 1));
+    h->step = step0 + done;
+    h->nsamples += done;
+    h->steps_total += done;
+    h->sp[0].next_id = c.next_id[0];
+    h->sp[1].next_id = c.next_id[1];
+    h->mg_cycles_total = (int64_t)c.mg_cycles;
+    h->last_cycles = c.mg_last_cycles;
+    h->last_res = c.mg_last_res;
+    pic_status result = PIC_OK;
+    if (c.mg_flags & 1) {
+        result = PIC_ERR_NOT_CONVERGED;
+        h->err = "multigrid stopped before the tolerance";
+        const int32_t z = 0;
+        cudaMemcpyAsync(&h->sctl->mg_flags, &z, sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+    }
+    if (status & ST_NAN) {
+        result = PIC_ERR_NUMERIC;
+        h->err = "non-finite particle state (particles dropped)";
+        cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
+    }
+    if (c.halt) {
+        // the state stays at the last completed step
+        const int32_t z[3] = {0, 0, 0};
+        cudaMemcpyAsync(&h->sctl->halt, z, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+        cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
+        if (c.halt_status & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
+            if (h->mixed)
+                deposit_current<float>(h);
+            else
+                deposit_current<double>(h);
+            cudaStreamSynchronize(h->st);
+            return fail(h, PIC_ERR_CAPACITY, (c.halt_status & ST_CAPACITY) ? "particle capacity exceeded"
+                                                                           : "births capacity exceeded");
+        }
+        cudaStreamSynchronize(h->st);
+        return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
+    }
+    cudaStreamSynchronize(h->st);
+    return result;
 }
 
 pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, double V,
@@ -865,7 +992,7 @@ pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, 
     double res = 0.0;
     const int r = mg_fast_solve(fd, h->mgf, h->tmp_grid[0], h->tmp_grid[1], V,
                                 h->has_phiL ? h->phiL_d : nullptr, h->tmp_grid[2], false,
-                                h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, h->st);
+                                h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, &res, &L, nullptr, h->st);
     h->launches += L;
     if (r == kSolveTimeout) return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
     if (r == kSolveNoLaunch) return fail(h, PIC_ERR_CUDA, "multigrid solve could not be launched");
@@ -924,6 +1051,7 @@ pic_status pic_moments(pic_handle *h, pic_moments_out *out, int32_t reset) {
         cudaMemsetAsync(h->ds->qabs, 0, sizeof(ds.qabs), h->st);
         h->nsamples = 0;
         h->mg_cycles_total = 0;
+        cudaMemsetAsync(&h->sctl->mg_cycles, 0, sizeof(unsigned long long), h->st);
         h->steps_total = 0;
         cudaStreamSynchronize(h->st);
     }
@@ -955,15 +1083,18 @@ pic_status pic_set_particles(pic_handle *h, int32_t s, const pic_particles_view 
 pic_status pic_set_step(pic_handle *h, int64_t step) {
     if (!h || step < 0) return fail(h, PIC_ERR_ARG, "bad step");
     h->step = step;
-    return PIC_OK;
+    push_ctl(h);
+    return cuda_check(h, "set_step");
 }
 
 pic_status pic_set_boundary(pic_handle *h, const double *phi_zL, int32_t on_device) {
     if (!h) return PIC_ERR_ARG;
     if (!phi_zL) {
+        if (h->has_phiL) drop_graphs(h);
         h->has_phiL = false;
         return PIC_OK;
     }
+    if (!h->has_phiL) drop_graphs(h);
     cudaMemcpyAsync(h->phiL_d, phi_zL, (size_t)h->nr * sizeof(double),
                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st);
     h->has_phiL = true;
@@ -977,7 +1108,7 @@ pic_status pic_get_fields(pic_handle *h, double *rho, double *chi, double *phi, 
     launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q,
                     h->cfg.sp[0].q * h->cfg.sp[0].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[0].m),
                     h->cfg.sp[1].q * h->cfg.sp[1].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[1].m),
-                    h->rho, h->chi, h->ng, h->st);
+                    h->rho, h->chi, h->ng, nullptr, h->st);
     h->launches += 1;
     const size_t gb = (size_t)h->ng * sizeof(double);
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -1096,6 +1227,7 @@ pic_status pic_load(pic_handle *h, const char *path) {
     h->step = hdr[3];
     h->sp[0].next_id = ids[0];
     h->sp[1].next_id = ids[1];
+    push_ctl(h);
     cudaMemcpy(h->phi, g.data(), g.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(h->N[0], N0.data(), N0.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(h->N[1], N1.data(), N1.size() * 8, cudaMemcpyHostToDevice);
@@ -1127,8 +1259,10 @@ pic_status pic_timings(pic_handle *h, double *ms, int64_t *particle_launches, in
 void pic_destroy(pic_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);
+    if (h->gst) cudaStreamSynchronize(h->gst);
     resolve_events(h);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
+    destroy_streams(h);
     free_all(h);
     delete h;
 }

@@ -26,6 +26,67 @@ enum : int {
     ST_TIMEOUT = 8,
 };
 
+// Step control on the device.  A timestep runs with no host
+// synchronisation: the first failed check sets `halt`, every later kernel of
+// the pic_step call returns at once, and the host reads this block once per
+// call.  Step-dependent values (step number, electrode voltage, split flag)
+// live here too, so a step's launches are the same every time (graph replay).
+struct StepCtl {
+    int32_t halt;         // a step failed: later step kernels do nothing
+    int32_t halt_status;  // ST_* bits of the failure
+    int64_t halt_step;    // number of the step that failed
+    int64_t step;         // number of the step being taken
+    double V;             // electrode voltage at the step's field time
+    int32_t do_split;     // the step splits heavy particles
+    int32_t mg_flags;     // bit 0: a solve stopped before the tolerance
+    uint64_t next_id[2];  // next particle id per species
+    unsigned long long mg_cycles;  // V-cycles of all solves so far
+    int32_t mg_last_cycles;
+    int32_t pad;
+    double mg_last_res;   // relative residual of the last solve
+    unsigned int bar;     // barrier counter of the births numbering
+    int32_t bar_timeout;  // a bounded wait of the births numbering gave up
+};
+
+// ---- grid barrier of cooperative launches ----
+// Thread 0 of each block adds 1 with release semantics and polls with
+// acquire loads until the counter (which only grows) reaches `target`: the
+// participants times the barriers of this kind the block has passed.  The
+// block's writes before the barrier are visible to every participant after
+// it.  The poll is bounded: after kSpinLimit tries, or once another block
+// gave up, the block raises *timeout and the call returns false.
+constexpr long long kSpinLimit = 1LL << 26;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void atom_add_release(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool count_barrier(unsigned *count, unsigned target, int *timeout) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        atom_add_release(count, 1u);
+        long long it = 0;
+        while ((int)(ld_acquire(count) - target) < 0) {
+            if ((++it & 255) == 0 && (it > kSpinLimit || *(volatile int *)timeout)) {
+                atomicExch(timeout, 1);
+                ok = 0;
+                break;
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // four-wide vectors: float4 for the mixed path, two 16-byte halves for FP64
 struct alignas(16) dbl4 {
     double x, y, z, w;
@@ -112,9 +173,9 @@ struct StepArgs {
     T v_gas;                    // sqrt(k T_gas / M_gas)
     T ion_acc;                  // a_ion = a_e * ion_acc (newborn ion)
     Xs<T> xs;
-    uint32_t key0, key1, step;
+    uint32_t key0, key1;
+    const StepCtl *ctl;  // step number (Philox counter), split flag, halt
     // splitting
-    int do_split;
     const T *w_ref;  // [ncr]
     // fields at the nodes {E_z, E_r}
     const typename V2<T>::type *E;
@@ -165,22 +226,25 @@ template <typename T>
 void launch_hist(PBuf<T> buf, const int32_t *n_dev, int32_t *counts, cudaStream_t st);
 // exclusive scan of counts[ncell] into cursor, total into *n_alive, capacity check
 void launch_scan(const int32_t *counts, int32_t *cursor, int ncell, int32_t *block_sums,
-                 int32_t *n_alive, int64_t capacity, DevScalars *ds, cudaStream_t st);
+                 int32_t *n_alive, int64_t capacity, DevScalars *ds, const StepCtl *ctl,
+                 cudaStream_t st);
+// a failed check of the step so far (capacity, births overflow) halts it
+void launch_step_check(const DevScalars *ds, StepCtl *ctl, cudaStream_t st);
 template <typename T>
 void launch_rank(PBuf<T> main, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,
                  int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
-                 const int32_t *status, cudaStream_t st);
-// assigns births ids next_id + rank of (key) among the nb births
-void launch_birth_ids_small(const uint64_t *key, uint64_t *id, int nb, uint64_t next_id,
-                            cudaStream_t st);
+                 const int32_t *status, const StepCtl *ctl, cudaStream_t st);
+// births of species s get ids next_id[s] + rank of their key among the
+// *nb births (one cooperative launch; next_id[s] advances by *nb)
 struct RadixTmp {
     uint64_t *k0, *k1;
     uint32_t *v0, *v1;
     uint32_t *hist;
+    int *flag;
     int max_n;
 };
-void launch_birth_ids_radix(const uint64_t *key, uint64_t *id, int nb, uint64_t next_id,
-                            RadixTmp tmp, int *launches, cudaStream_t st);
+void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, StepCtl *ctl, int s,
+                      RadixTmp tmp, cudaStream_t st);
 
 // ---- multigrid (field.cu) ----
 struct MGLevel {
@@ -201,17 +265,20 @@ struct FieldDims {
     double dz, dr, L;
     int chi_face;
 };
+// ctl (may be null): skip when the step has halted
 void launch_finalize(const double *Ne, const double *Ni, const double *V, double q0, double q1,
-                     double chi0, double chi1, double *rho, double *chi, int ng, cudaStream_t st);
+                     double chi0, double chi1, double *rho, double *chi, int ng, const StepCtl *ctl,
+                     cudaStream_t st);
 // multigrid solve into phi (device); returns cycles, residual and the launch count
 int mg_solve(const FieldDims &fd, MGWork &mg, const double *rho, const double *chi, double V,
              const double *phi_zL, double *phi, bool warm, bool mixed, double tol, int max_cycles,
              double *rel_res, int *launches, cudaStream_t st);
 template <typename T>
 void launch_efield(const double *phi, double *Ez, double *Er, typename V2<T>::type *E2, int nz,
-                   int nr, double dz, double dr, cudaStream_t st);
+                   int nr, double dz, double dr, const StepCtl *ctl, cudaStream_t st);
 void launch_moments(const double *Ne, const double *Ni, const double *V, const double *phi,
                     const double *Ez, const double *Er, double *m_ne, double *m_ni,
-                    double *m_phi, double *m_ez, double *m_er, int ng, cudaStream_t st);
+                    double *m_phi, double *m_ez, double *m_er, int ng, const StepCtl *ctl,
+                    cudaStream_t st);
 
 }  // namespace pic

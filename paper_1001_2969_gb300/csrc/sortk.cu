@@ -8,7 +8,10 @@
 //
 // Newborns are numbered next_id + rank of their key (parent species, parent
 // id, birth slot): one block ranks small batches directly, larger batches
-// go through an LSD radix sort of (key, index) pairs.
+// go through an LSD radix sort of (key, index) pairs, both in one
+// cooperative launch that reads the count on the device.
+#include <algorithm>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -59,8 +62,9 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int *tot
     return warp_excl + x - v;
 }
 
-__global__ void k_scan_tiles(const int32_t *counts, int ncell, int32_t *block_sums) {
+__global__ void k_scan_tiles(const int32_t *counts, int ncell, int32_t *block_sums, const StepCtl *ctl) {
     __shared__ int s_warp[32];
+    if (ctl && ctl->halt) return;
     const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
     int v = 0;
     for (int q = 0; q < 4; ++q) v += (base + q < ncell) ? counts[base + q] : 0;
@@ -70,9 +74,10 @@ __global__ void k_scan_tiles(const int32_t *counts, int ncell, int32_t *block_su
 }
 
 __global__ void k_scan_top(int32_t *block_sums, int nblocks, int32_t *n_alive, int64_t capacity,
-                           DevScalars *ds) {
+                           DevScalars *ds, const StepCtl *ctl) {
     __shared__ int s_warp[32];
     __shared__ int s_carry;
+    if (ctl && ctl->halt) return;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nblocks; b0 += blockDim.x) {
@@ -93,8 +98,9 @@ __global__ void k_scan_top(int32_t *block_sums, int nblocks, int32_t *n_alive, i
 }
 
 __global__ void k_scan_apply(const int32_t *counts, int ncell, const int32_t *block_sums,
-                             int32_t *cursor) {
+                             int32_t *cursor, const StepCtl *ctl) {
     __shared__ int s_warp[32];
+    if (ctl && ctl->halt) return;
     const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
     int c[4];
     int v = 0;
@@ -110,20 +116,34 @@ __global__ void k_scan_apply(const int32_t *counts, int ncell, const int32_t *bl
 }
 
 void launch_scan(const int32_t *counts, int32_t *cursor, int ncell, int32_t *block_sums,
-                 int32_t *n_alive, int64_t capacity, DevScalars *ds, cudaStream_t st) {
+                 int32_t *n_alive, int64_t capacity, DevScalars *ds, const StepCtl *ctl,
+                 cudaStream_t st) {
     const int nb = (ncell + kScanTile - 1) / kScanTile;
-    k_scan_tiles<<<nb, kScanThreads, 0, st>>>(counts, ncell, block_sums);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb, n_alive, capacity, ds);
-    k_scan_apply<<<nb, kScanThreads, 0, st>>>(counts, ncell, block_sums, cursor);
+    k_scan_tiles<<<nb, kScanThreads, 0, st>>>(counts, ncell, block_sums, ctl);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb, n_alive, capacity, ds, ctl);
+    k_scan_apply<<<nb, kScanThreads, 0, st>>>(counts, ncell, block_sums, cursor, ctl);
+}
+
+__global__ void k_step_check(const DevScalars *ds, StepCtl *ctl) {
+    const int st = ds->status & (ST_CAPACITY | ST_BIRTH_OVERFLOW);
+    if (!ctl->halt && st) {
+        ctl->halt = 1;
+        ctl->halt_status = st;
+        ctl->halt_step = ctl->step;
+    }
+}
+
+void launch_step_check(const DevScalars *ds, StepCtl *ctl, cudaStream_t st) {
+    k_step_check<<<1, 1, 0, st>>>(ds, ctl);
 }
 
 // ---- rank: perm[cursor[cell]++] = element (main first, then births) ----
 template <typename T>
 __global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
                        const int32_t *n_births_dev, int32_t *cursor, int32_t *perm,
-                       const int32_t *n_alive, int64_t cap, const int32_t *status) {
+                       const int32_t *n_alive, int64_t cap, const int32_t *status, const StepCtl *ctl) {
     // a failed step keeps the previous permutation
-    if ((int64_t)*n_alive > cap || (*status & (ST_CAPACITY | ST_BIRTH_OVERFLOW))) return;
+    if ((ctl && ctl->halt) || (int64_t)*n_alive > cap || (*status & (ST_CAPACITY | ST_BIRTH_OVERFLOW))) return;
     const int nm = *n_main_dev, nb = *n_births_dev;
     const int total = nm + nb;
     const int lane = threadIdx.x & 31;
@@ -146,134 +166,154 @@ __global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
 template <typename T>
 void launch_rank(PBuf<T> mainb, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,
                  int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
-                 const int32_t *status, cudaStream_t st) {
+                 const int32_t *status, const StepCtl *ctl, cudaStream_t st) {
     k_rank<T><<<152 * 8, 256, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap,
-                                        status);
+                                        status, ctl);
 }
 
-// ---- newborn numbering, small batches: rank by counting smaller keys ----
+// ---- newborn numbering ----
+// Births get ids next_id + rank of their key (parent species, parent id,
+// birth index), as in the oracle.  One cooperative launch: up to
+// kSmallBirths keys block 0 ranks each key by counting smaller ones; above
+// that the grid runs an LSD radix sort over 8-bit digits (a digit shared by
+// every key is skipped), tiles of kRadixTile keys, grid barriers between the
+// histogram, scan and scatter phases.
 constexpr int kSmallBirths = 2048;
-
-__global__ void k_birth_ids_small(const uint64_t *key, uint64_t *id, int nb, uint64_t next_id) {
-    __shared__ uint64_t s_key[kSmallBirths];
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) s_key[k] = key[k];
-    __syncthreads();
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const uint64_t mine = s_key[k];
-        int rank = 0;
-        for (int q = 0; q < nb; ++q) rank += s_key[q] < mine;
-        id[k] = next_id + (uint64_t)rank;
-    }
-}
-
-void launch_birth_ids_small(const uint64_t *key, uint64_t *id, int nb, uint64_t next_id,
-                            cudaStream_t st) {
-    if (nb <= 0) return;
-    k_birth_ids_small<<<1, 1024, 0, st>>>(key, id, nb, next_id);
-}
-
-// ---- newborn numbering, large batches: LSD radix sort, 8-bit digits ----
-constexpr int kRadixThreads = 256;
-constexpr int kRadixPer = 8;
+constexpr int kRadixThreads = 1024;
+constexpr int kRadixPer = 2;
 constexpr int kRadixTile = kRadixThreads * kRadixPer;
 
-__global__ void k_radix_init(const uint64_t *key, uint64_t *k0, uint32_t *v0, int n) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) {
-        k0[e] = key[e];
-        v0[e] = (uint32_t)e;
-    }
-}
-
-__global__ void k_radix_hist(const uint64_t *keys, int n, int shift, uint32_t *hist, int ntiles) {
-    __shared__ uint32_t s_h[256];
-    s_h[threadIdx.x] = 0;
-    __syncthreads();
-    const int base = blockIdx.x * kRadixTile;
-    for (int q = 0; q < kRadixPer; ++q) {
-        const int e = base + q * kRadixThreads + threadIdx.x;
-        if (e < n) atomicAdd(&s_h[(keys[e] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[threadIdx.x * ntiles + blockIdx.x] = s_h[threadIdx.x];
-}
-
-__global__ void k_radix_scan(uint32_t *hist, int total) {
+__global__ void __launch_bounds__(kRadixThreads)
+    k_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb_dev, StepCtl *ctl, int s, RadixTmp t) {
+    // the small path's keys and the scatter's per-warp digit counts share space
+    constexpr int kBuf = kSmallBirths * 8 > (kRadixThreads / 32) * 256 * 4 ? kSmallBirths * 8
+                                                                            : (kRadixThreads / 32) * 256 * 4;
+    __shared__ __align__(16) unsigned char s_buf[kBuf];
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(s_buf);
+    uint32_t (*s_wc)[256] = reinterpret_cast<uint32_t (*)[256]>(s_buf);
+    __shared__ uint32_t s_run[256];
     __shared__ int s_warp[32];
     __shared__ int s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < total; b0 += blockDim.x) {
-        const int k = b0 + threadIdx.x;
-        const int v = k < total ? (int)hist[k] : 0;
-        int tot;
-        const int ex = block_exclusive_scan(v, s_warp, &tot);
-        const int carry = s_carry;
-        if (k < total) hist[k] = (uint32_t)(carry + ex);
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + tot;
-        __syncthreads();
-    }
-}
-
-// stable scatter of one tile: rounds of 256 keys in order; inside a round a
-// key's place is (keys of its digit in earlier warps) + (earlier lanes of
-// its warp with the same digit)
-__global__ void k_radix_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout,
-                                uint32_t *vout, int n, int shift, const uint32_t *hist,
-                                int ntiles) {
-    __shared__ uint32_t s_run[256];
-    __shared__ uint32_t s_wc[kRadixThreads / 32][256];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_run[tid] = hist[tid * ntiles + blockIdx.x];
-    for (int w = 0; w < kRadixThreads / 32; ++w) s_wc[w][tid] = 0;
-    __syncthreads();
-    const int base = blockIdx.x * kRadixTile;
-    for (int q = 0; q < kRadixPer; ++q) {
-        const int e = base + q * kRadixThreads + tid;
-        const bool valid = e < n;
-        uint64_t key = valid ? kin[e] : 0;
-        const int d = valid ? (int)((key >> shift) & 255u) : 256 + lane;  // unique dummies
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int rank_w = __popc(peers & ((1u << lane) - 1u));
-        if (valid && lane == __ffs(peers) - 1) s_wc[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            uint32_t off = s_run[d];
-            for (int w = 0; w < warp; ++w) off += s_wc[w][d];
-            const uint32_t pos = off + (uint32_t)rank_w;
-            kout[pos] = key;
-            vout[pos] = vin[e];
-        }
-        __syncthreads();
-        uint32_t add = 0;
-        for (int w = 0; w < kRadixThreads / 32; ++w) {
-            add += s_wc[w][tid];
-            s_wc[w][tid] = 0;
-        }
-        s_run[tid] += add;
-        __syncthreads();
-    }
-}
-
-__global__ void k_radix_ids(const uint32_t *v, uint64_t *id, int n, uint64_t next_id) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) id[v[r]] = next_id + (uint64_t)r;
-}
-
-void launch_birth_ids_radix(const uint64_t *key, uint64_t *id, int nb, uint64_t next_id,
-                            RadixTmp t, int *launches, cudaStream_t st) {
+    if (ctl->halt) return;
+    const int nb = *nb_dev;
     if (nb <= 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (nb <= kSmallBirths) {
+        if (blockIdx.x != 0) return;
+        const uint64_t base = ctl->next_id[s];
+        for (int k = tid; k < nb; k += blockDim.x) s_key[k] = key[k];
+        __syncthreads();
+        for (int k = tid; k < nb; k += blockDim.x) {
+            const uint64_t mine = s_key[k];
+            int rank = 0;
+            for (int q = 0; q < nb; ++q) rank += s_key[q] < mine;
+            id[k] = base + (uint64_t)rank;
+        }
+        __syncthreads();
+        if (tid == 0) ctl->next_id[s] = base + (uint64_t)nb;
+        return;
+    }
+    // every block reads the base before the first barrier; block 0 moves it on at the end
+    const uint64_t base = ctl->next_id[s];
     const int ntiles = (nb + kRadixTile - 1) / kRadixTile;
-    k_radix_init<<<(nb + 255) / 256, 256, 0, st>>>(key, t.k0, t.v0, nb);
-    int L = 1;
+    unsigned nbar = 0;
+    // a wait that gives up halts the step (its ids would be wrong)
+    auto bar = [&]() {
+        if (count_barrier(&ctl->bar, (++nbar) * gridDim.x, &ctl->bar_timeout)) return true;
+        if (tid == 0 && atomicExch(&ctl->halt, 1) == 0) {
+            ctl->halt_status = ST_TIMEOUT;
+            ctl->halt_step = ctl->step;
+        }
+        return false;
+    };
+    for (int e = blockIdx.x * blockDim.x + tid; e < nb; e += gridDim.x * blockDim.x) {
+        t.k0[e] = key[e];
+        t.v0[e] = (uint32_t)e;
+    }
+    if (!bar()) return;
     uint64_t *ka = t.k0, *kb = t.k1;
     uint32_t *va = t.v0, *vb = t.v1;
     for (int shift = 0; shift < 64; shift += 8) {
-        k_radix_hist<<<ntiles, kRadixThreads, 0, st>>>(ka, nb, shift, t.hist, ntiles);
-        k_radix_scan<<<1, 1024, 0, st>>>(t.hist, 256 * ntiles);
-        k_radix_scatter<<<ntiles, kRadixThreads, 0, st>>>(ka, va, kb, vb, nb, shift, t.hist, ntiles);
-        L += 3;
+        // digit histogram per tile: hist[d * ntiles + tile]
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            if (tid < 256) s_run[tid] = 0;
+            __syncthreads();
+            for (int q = 0; q < kRadixPer; ++q) {
+                const int e = tile * kRadixTile + q * kRadixThreads + tid;
+                if (e < nb) atomicAdd(&s_run[(ka[e] >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            if (tid < 256) t.hist[tid * ntiles + tile] = s_run[tid];
+            __syncthreads();
+        }
+        if (!bar()) return;
+        // block 0: exclusive scan in digit-major order; a digit held by all
+        // keys leaves the order as it is
+        if (blockIdx.x == 0) {
+            if (tid < 256) {
+                uint32_t c = 0;
+                for (int tl = 0; tl < ntiles; ++tl) c += t.hist[tid * ntiles + tl];
+                s_run[tid] = c;
+            }
+            __syncthreads();
+            int all = 0;
+            for (int d = 0; d < 256; ++d) all |= s_run[d] == (uint32_t)nb;
+            if (tid == 0) *t.flag = all;
+            if (!all) {
+                if (tid == 0) s_carry = 0;
+                __syncthreads();
+                const int total = 256 * ntiles;
+                for (int b0 = 0; b0 < total; b0 += blockDim.x) {
+                    const int k = b0 + tid;
+                    const int v = k < total ? (int)t.hist[k] : 0;
+                    int tot;
+                    const int ex = block_exclusive_scan(v, s_warp, &tot);
+                    const int carry = s_carry;
+                    if (k < total) t.hist[k] = (uint32_t)(carry + ex);
+                    __syncthreads();
+                    if (tid == 0) s_carry = carry + tot;
+                    __syncthreads();
+                }
+            }
+        }
+        if (!bar()) return;
+        if (*(volatile int *)t.flag) continue;
+        // stable scatter of each tile: rounds of kRadixThreads keys in order;
+        // inside a round a key's place is (keys of its digit in earlier
+        // warps) + (earlier lanes of its warp with the same digit)
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            if (tid < 256) s_run[tid] = t.hist[tid * ntiles + tile];
+            for (int k = tid; k < (kRadixThreads / 32) * 256; k += blockDim.x) (&s_wc[0][0])[k] = 0;
+            __syncthreads();
+            for (int q = 0; q < kRadixPer; ++q) {
+                const int e = tile * kRadixTile + q * kRadixThreads + tid;
+                const bool valid = e < nb;
+                const uint64_t kv = valid ? ka[e] : 0;
+                const int d = valid ? (int)((kv >> shift) & 255u) : 256 + lane;  // unique dummies
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int rank_w = __popc(peers & ((1u << lane) - 1u));
+                if (valid && lane == __ffs(peers) - 1) s_wc[warp][d] = __popc(peers);
+                __syncthreads();
+                if (valid) {
+                    uint32_t off = s_run[d];
+                    for (int w = 0; w < warp; ++w) off += s_wc[w][d];
+                    const uint32_t pos = off + (uint32_t)rank_w;
+                    kb[pos] = kv;
+                    vb[pos] = va[e];
+                }
+                __syncthreads();
+                if (tid < 256) {
+                    uint32_t add = 0;
+                    for (int w = 0; w < kRadixThreads / 32; ++w) {
+                        add += s_wc[w][tid];
+                        s_wc[w][tid] = 0;
+                    }
+                    s_run[tid] += add;
+                }
+                __syncthreads();
+            }
+        }
+        if (!bar()) return;
         uint64_t *tk = ka;
         ka = kb;
         kb = tk;
@@ -281,18 +321,35 @@ void launch_birth_ids_radix(const uint64_t *key, uint64_t *id, int nb, uint64_t 
         va = vb;
         vb = tv;
     }
-    k_radix_ids<<<(nb + 255) / 256, 256, 0, st>>>(va, id, nb, next_id);
-    L += 1;
-    if (launches) *launches += L;
+    for (int r = blockIdx.x * blockDim.x + tid; r < nb; r += gridDim.x * blockDim.x) id[va[r]] = base + (uint64_t)r;
+    if (blockIdx.x == 0 && tid == 0) ctl->next_id[s] = base + (uint64_t)nb;
+}
+
+void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, StepCtl *ctl, int s,
+                      RadixTmp tmp, cudaStream_t st) {
+    // one block per SM (the launch needs them co-resident), per device
+    static int grids[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &grid = grids[dev & 63];
+    if (grid == 0) {
+        int nsm = 0, per = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_birth_ids, kRadixThreads, 0);
+        grid = std::max(1, std::min(nsm, nsm * per));
+    }
+    cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned) + sizeof(int32_t), st);  // counter and timeout flag
+    void *args[] = {(void *)&key, (void *)&id, (void *)&nb, (void *)&ctl, (void *)&s, (void *)&tmp};
+    cudaLaunchCooperativeKernel((void *)k_birth_ids, grid, kRadixThreads, args, 0, st);
 }
 
 template void launch_hist<float>(PBuf<float>, const int32_t *, int32_t *, cudaStream_t);
 template void launch_hist<double>(PBuf<double>, const int32_t *, int32_t *, cudaStream_t);
 template void launch_rank<float>(PBuf<float>, const int32_t *, PBuf<float>, const int32_t *,
                                  int32_t *, int32_t *, const int32_t *, int64_t, const int32_t *,
-                                 cudaStream_t);
+                                 const StepCtl *, cudaStream_t);
 template void launch_rank<double>(PBuf<double>, const int32_t *, PBuf<double>, const int32_t *,
                                   int32_t *, int32_t *, const int32_t *, int64_t, const int32_t *,
-                                  cudaStream_t);
+                                  const StepCtl *, cudaStream_t);
 
 }  // namespace pic

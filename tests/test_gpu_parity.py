@@ -293,6 +293,40 @@ def test_multi_step_parity_fp64(pic):
     assert nerr(m["eedf"], om["eedf"]) < 1e-9
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_graph_replay_matches_direct_launches(pic, prec):
+    """Steps replayed as CUDA graphs (the default) give what the same steps
+    launched one by one (profiling on) give: the same ids, counts and
+    counters, fields and particles to rounding (deposit atomics add in any
+    order).  Five steps in two calls cover both buffer parities."""
+    cfg = W.scaled(W.config("c1", precision=prec), 20_000)
+    ha, hb = pic.pic_init(cfg), pic.pic_init(cfg)
+    pic.pic_profile(ha, True)
+    for k in (3, 2):
+        assert pic.pic_step(ha, k) == 0
+        assert pic.pic_step(hb, k) == 0
+    ca, cb = pic.pic_get_counts(ha), pic.pic_get_counts(hb)
+    assert ca["step"] == cb["step"] == 5
+    tol = 1e-11 if prec == "fp64" else 1e-5
+    fa, fb = pic.pic_get_fields(ha), pic.pic_get_fields(hb)
+    for name in ("phi", "rho", "Ez"):
+        assert nerr(fb[name], fa[name]) < tol, name
+    for s in (0, 1):
+        ga, gb = by_id(pic.pic_get_particles(ha, s)), by_id(pic.pic_get_particles(hb, s))
+        if prec == "fp64":
+            assert np.array_equal(ga["id"], gb["id"])
+            assert list(ca["next_id"]) == list(cb["next_id"])
+            for k in FIELDS:
+                assert nerr(gb[k], ga[k]) < 1e-10, k
+        else:
+            common = np.intersect1d(ga["id"], gb["id"])
+            assert len(common) >= len(ga["id"]) - 5
+    ma, mb = pic.pic_moments(ha), pic.pic_moments(hb)
+    if prec == "fp64":
+        assert list(ma["counters"][:22]) == list(mb["counters"][:22])
+    assert ma["counters"][pic.PIC_C_STEPS] == mb["counters"][pic.PIC_C_STEPS] == 5
+
+
 def test_births_capacity_error_keeps_the_state(pic):
     cfg = _state_cfg("fp64", births_capacity=16)
     e, i = _random_state(cfg, 30_000, 1000, seed=21, hot=4.0)
