@@ -35,6 +35,22 @@ WORKLOAD = ("c2 production reactor: R 20 cm, L 2.5 cm, 129x513 nodes, 1e7 e- + 1
 BYTES_PER_PARTICLE = {"mixed": 88, "fp64": 152}
 
 
+def whole_job(ms, psteps, e2e_seconds, e2e_psteps, world, device="cuda"):
+    """Whole-job figures over `world` ranks of independent replicas: the
+    particle-steps all ranks processed over the slowest rank's time, for the
+    device-timed region and for the end-to-end one.  Returns (ms_max,
+    psteps_sum, e2e_seconds_max, e2e_psteps_sum); one rank returns its own."""
+    if world <= 1:
+        return ms, psteps, e2e_seconds, e2e_psteps
+    import torch
+
+    t_max = torch.tensor([ms, e2e_seconds], dtype=torch.float64, device=device)
+    n_sum = torch.tensor([psteps, e2e_psteps], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(n_sum, op=torch.distributed.ReduceOp.SUM)
+    return float(t_max[0]), float(n_sum[0]), float(t_max[1]), float(n_sum[1])
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -303,14 +319,9 @@ def main():
     res = run_gpu(args, rank, world)
     main_r = res[args.precision]
     # whole job: units all ranks processed / the slowest rank's time
-    if world > 1:
-        t = torch.tensor([main_r["ms"], main_r["psteps"]], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[0:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(mx[1:2], op=torch.distributed.ReduceOp.SUM)
-        ms_max, psteps_sum = float(mx[0]), float(mx[1])
-    else:
-        ms_max, psteps_sum = main_r["ms"], main_r["psteps"]
+    e = main_r["e2e"]
+    ms_max, psteps_sum, e2e_s, e2e_n = whole_job(main_r["ms"], main_r["psteps"], e["seconds"],
+                                                 e["psteps"], world)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return 0
@@ -352,7 +363,7 @@ def main():
                         "solve_ms_per_step": t64["solve_ms"] / args.fp64_steps,
                         "mg_cycles_per_step": r["mg_cycles"]}
     e = main_r["e2e"]
-    line["e2e"] = {"value": e["psteps"] / e["seconds"], "unit": UNIT,
+    line["e2e"] = {"value": e2e_n / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"],
                    "steps": e["steps"]}
     if not args.no_cpu:
