@@ -154,12 +154,18 @@ __global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
             c = mainb.cell[e];
         else if (e < total)
             c = births.cell[e - nm];
-        const unsigned peers = __match_any_sync(0xffffffffu, c);
-        const int leader = __ffs(peers) - 1;
+        // the input is in (old) cell order, so equal cells sit in runs of
+        // lanes: the first lane of a run reserves places for the whole run
+        const int cprev = __shfl_up_sync(0xffffffffu, c, 1);
+        const bool head = lane == 0 || cprev != c;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const int first = 31 - __clz(heads & ((2u << lane) - 1u));  // head of this lane's run
+        const unsigned above = heads & ~((2u << lane) - 1u);
+        const int rend = above ? __ffs(above) - 1 : 32;               // one past the run's end
         int pos = 0;
-        if (c >= 0 && lane == leader) pos = atomicAdd(cursor + c, __popc(peers));
-        pos = __shfl_sync(peers, pos, leader);
-        if (c >= 0) perm[pos + __popc(peers & ((1u << lane) - 1u))] = e;
+        if (c >= 0 && head) pos = atomicAdd(cursor + c, rend - lane);
+        pos = __shfl_sync(0xffffffffu, pos, first);
+        if (c >= 0) perm[pos + (lane - first)] = e;
     }
 }
 
