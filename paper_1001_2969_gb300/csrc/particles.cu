@@ -167,6 +167,11 @@ __device__ __forceinline__ void shape_r(int weighting, int j, T o, T &s0, T &s1)
     if (weighting == PIC_WEIGHT_ZR) {
         s1 = o;
         s0 = (T)1 - o;
+    } else if (sizeof(T) == 4) {
+        const T t = (T)(2 * j + 1);
+        const T it = m_div((T)1, t);
+        s1 = o * ((T)(2 * j) + o) * it;
+        s0 = ((T)1 - o) * (t + o) * it;
     } else {
         const T t = (T)(2 * j + 1);
         s1 = m_div(o * ((T)(2 * j) + o), t);
@@ -483,6 +488,10 @@ __device__ __forceinline__ void cpa4(void *dst, const void *src) {
 
 constexpr int kThreads = 256;
 constexpr int kPPT = 4;
+// the block's EEDF is kept in this many interleaved copies (lane % copies):
+// electrons of a warp crowd into few low-energy bins, and same-address
+// shared-memory atomics of a warp are serialised
+constexpr int kEedfCopies = 8;
 constexpr int kChunk = kThreads * kPPT;
 static_assert(kChunk == kStepChunk, "chunk size");
 constexpr int kHalo = 3;
@@ -521,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     for (int k = tid; k < PIC_NCOUNT; k += blockDim.x) bt.cnt[k] = 0;
     if (tid < 3) bt.q[tid] = 0.0;
     if (a.eedf)
-        for (int k = tid; k < a.eedf_bins; k += blockDim.x) s_eedf[k] = (T)0;
+        for (int k = tid; k < a.eedf_bins * kEedfCopies; k += blockDim.x) s_eedf[k] = (T)0;
     const int WCAP = kWinBytes / (int)sizeof(T);
     const int n = *a.n_alive;
     const int nmain = *a.n_main_src;
@@ -651,8 +660,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                     p.ar = m_abs(p.ar);
                 }
                 bool alive = true;
-                if (!(m_finite(p.oz) && m_finite(p.orr) && m_finite(p.vr) && m_finite(p.vt) &&
-                      m_finite(p.vz) && m_finite(p.w))) {
+                // one test for all: a NaN or infinity anywhere makes the sum
+                // non-finite (the values are far below overflow)
+                if (!m_finite(p.oz + p.orr + p.vr + p.vt + p.vz + p.w)) {
                     atomicOr(&a.ds->status, ST_NAN);
                     alive = false;
                 }
@@ -668,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                         const T Ek = a.half_m_e * (p.vr * p.vr + p.vt * p.vt + p.vz * p.vz);
                         const T x = Ek * a.eedf_scale;
                         if (x >= (T)0 && x < (T)a.eedf_bins)
-                            atomicAdd(&s_eedf[(int)x], p.w);
+                            atomicAdd(&s_eedf[(int)x * kEedfCopies + (lane & (kEedfCopies - 1))], p.w);
                     }
                     if (do_split) {  // weight-conserving split (Sec. 2.2)
                         const T wr_ = a.w_ref[p.j];
@@ -766,8 +776,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
         if (bt.cnt[k]) atomicAdd(&a.ds->cnt[k], bt.cnt[k]);
     if (tid < 3 && bt.q[tid] != 0.0) atomicAdd(&a.ds->qabs[tid], bt.q[tid]);
     if (a.eedf)
-        for (int k = tid; k < a.eedf_bins; k += blockDim.x)
-            if (s_eedf[k] != (T)0) atomicAdd(a.eedf + k, (double)s_eedf[k]);
+        for (int k = tid; k < a.eedf_bins; k += blockDim.x) {
+            double v = 0.0;
+            for (int c = 0; c < kEedfCopies; ++c) v += (double)s_eedf[k * kEedfCopies + c];
+            if (v != 0.0) atomicAdd(a.eedf + k, v);
+        }
 }
 
 template <typename T>
@@ -775,7 +788,7 @@ void launch_step(const StepArgs<T> &a, int grid, cudaStream_t st) {
     // the ions' pass is latency-bound: it takes the prefetching variant
     const bool pf = a.s == 1;
     const size_t stage = (size_t)kChunk * (2 * sizeof(typename V4<T>::type) + sizeof(uint64_t) + sizeof(int32_t));
-    const size_t eedf = (size_t)(a.eedf ? a.eedf_bins : 0) * sizeof(T);
+    const size_t eedf = (size_t)(a.eedf ? a.eedf_bins : 0) * kEedfCopies * sizeof(T);
     if (pf) {
         const size_t smem = win_bytes<true>() + stage + eedf;
         cudaFuncSetAttribute(k_step<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
