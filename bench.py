@@ -259,6 +259,48 @@ def cpu_baseline(cfg_name, n_per_species, steps):
             "ms_per_step": 1e3 * dt / steps}
 
 
+def accuracy_vs_oracle(cfg_name, n_per_species, stream):
+    """Each output's error against the FP64 oracle after one step of the same
+    seeded sample of the workload (both GPU precisions): fields relative to
+    their largest magnitude, particle states likewise over the particles both
+    sides hold, and how many particles one side holds and the other not
+    (FP32 decisions at thresholds)."""
+    import numpy as np
+    import workloads as W
+    from oracle import Oracle
+    from paper_1001_2969_gb300 import pic
+
+    cfg = W.scaled(W.config(cfg_name), n_per_species)
+    o = Oracle(cfg)
+    o.load()
+    o.step(1)
+    o.finalize()
+    ref_f = {k: o.grid(k) for k in ("phi", "Ez", "Er", "rho", "chi")}
+    ref_p = [o.get_particles(s) for s in (0, 1)]
+    out = {"sample": f"{cfg_name} mesh and load with {n_per_species} particles per species, one step",
+           "norm": "max |gpu - oracle| / max |oracle| per output"}
+    for prec in ("mixed", "fp64"):
+        h = pic.pic_init(W.scaled(W.config(cfg_name, precision=prec), n_per_species),
+                         stream=stream.cuda_stream)
+        pic.pic_step(h, 1)
+        f = pic.pic_get_fields(h)
+        r = {k: float(np.abs(f[k] - ref_f[k]).max() / np.abs(ref_f[k]).max()) for k in ref_f}
+        worst, unmatched = {}, 0
+        for s in (0, 1):
+            g = pic.pic_get_particles(h, s)
+            common, gi, oi = np.intersect1d(g["id"], ref_p[s]["id"], return_indices=True)
+            unmatched += len(g["id"]) + len(ref_p[s]["id"]) - 2 * len(common)
+            for k in ("r", "z", "vr", "vt", "vz", "w"):
+                a, b = np.asarray(g[k])[gi], np.asarray(ref_p[s][k])[oi]
+                e = float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+                worst[k] = max(worst.get(k, 0.0), e)
+        r["particles"] = worst
+        r["particles_on_one_side_only"] = int(unmatched)
+        out[prec] = r
+        pic.pic_destroy(h)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,6 +410,8 @@ def main():
                    "steps": e["steps"]}
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_sample, args.cpu_steps)
+        line["accuracy_vs_fp64_oracle"] = accuracy_vs_oracle(args.config, args.cpu_sample,
+                                                             torch.cuda.current_stream())
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
