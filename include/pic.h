@@ -130,6 +130,7 @@ typedef struct pic_config {
 } pic_config;
 
 typedef struct pic_handle pic_handle;
+typedef struct pic_batch pic_batch;
 
 /* Host particle arrays, absolute coordinates, FP64.  cell (nullable) is
  * filled by pic_get_particles with the stored cell index j (nz-1) + i and
@@ -177,11 +178,49 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out);
  * null-collision Monte Carlo (Sec. 2.6), weight splitting on split steps
  * (Sec. 2.2), first push of the next step in the local X-Y frame with the
  * theta rotation (Sec. 2.3), deposit of rho and chi, and a re-sort of the
- * particles by cell.  Returns the first non-OK status of the steps;
+ * particles by cell (Sec. 2.1 merged cycle).  The steps run without host
+ * synchronisation, each as one CUDA graph replay (captured on first use per
+ * buffer parity, on a private stream ordered after and before the handle's
+ * stream; launched one by one while profiling is on); the call synchronises
+ * once at the end.  Returns the first non-OK status of the steps;
  * PIC_ERR_NOT_CONVERGED is non-fatal (the step completes).  On
- * PIC_ERR_CAPACITY the particle state is left at the last completed step.
+ * PIC_ERR_CAPACITY and PIC_ERR_TIMEOUT the particle state is left at the last
+ * completed step.
  */
 pic_status pic_step(pic_handle *h, int32_t nsteps);
+
+/*
+ * Batched reactors (no counterpart in the paper, which runs one reactor).
+ * pic_batch_init groups n distinct handles (each made by pic_init: any mesh,
+ * particle count and precision); the caller keeps ownership of the handles
+ * and must destroy the batch before them.  pic_batch_step advances every
+ * reactor by nsteps timesteps: each step of all reactors is one CUDA graph
+ * launch that forks into one branch per reactor (its whole timestep, as
+ * pic_step would run it) and joins, so the GPU runs the reactors side by
+ * side.  The work is ordered after `stream` (a cudaStream_t; NULL: the legacy
+ * default stream) and after each handle's own stream, and before them again;
+ * the call synchronises once.  statuses (NULL or n entries) receives what
+ * pic_step would have returned for each handle; the return value is the
+ * first non-OK one.  Handles must have profiling off.  Errors: PIC_ERR_ARG
+ * (null, repeated handle, n < 1), PIC_ERR_CUDA (streams, events).
+ */
+pic_status pic_batch_init(pic_handle *const *handles, int32_t n, void *stream, pic_batch **out);
+
+/*
+ * pic_tune -- choose the particle pass's shape per species (no counterpart
+ * in the paper).  Shapes: 0 direct loads, 1 the chunk's particles prefetched
+ * into shared memory (cp.async), 2 and 3 the same with 8 instead of 4
+ * particles per thread; -1 the default (electrons 0, ions 1).  With
+ * steps_per_variant > 0 every shape runs that many real steps of this
+ * reactor (the simulation advances) with CUDA events around each species'
+ * pass, the fastest per species is kept and, if variants is not NULL,
+ * written to variants[0..1] (electrons, ions).  With steps_per_variant = 0
+ * the shapes are set from variants[0..1].  Captured step graphs are dropped.
+ * Errors: PIC_ERR_ARG, and any error of the timed steps.
+ */
+pic_status pic_tune(pic_handle *h, int32_t steps_per_variant, int32_t *variants);
+pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses);
+void pic_batch_destroy(pic_batch *b);
 
 /*
  * pic_field_solve -- stand-alone solve of Eq. (2) (Sec. 2.1, 2.5) on the
@@ -275,11 +314,12 @@ pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64
 pic_status pic_save(pic_handle *h, const char *path);
 pic_status pic_load(pic_handle *h, const char *path);
 
-/* pic_profile -- when on, record CUDA events around each phase of every
- * step on the handle's stream.  pic_timings returns the accumulated
- * milliseconds per phase [0 solve, 1 particle kernels, 2 births+sort,
- * 3 other], the number of particle-kernel launches, and the number of all
- * kernel launches this handle has made. */
+/* pic_profile -- when on, steps launch one by one (no graph) and CUDA events
+ * bracket each phase of every step on the handle's stream.  pic_timings
+ * returns the accumulated milliseconds per phase [0 solve, 1 electron pass,
+ * 2 ion pass, 3 sort and births, 4 moments and step end], the number of
+ * particle-kernel launches, and the number of all kernel launches this
+ * handle has made (graph nodes included). */
 pic_status pic_profile(pic_handle *h, int32_t on);
 pic_status pic_timings(pic_handle *h, double *ms, int64_t *particle_launches,
                        int64_t *all_launches, int32_t reset);

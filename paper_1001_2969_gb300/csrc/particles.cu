@@ -487,13 +487,11 @@ __device__ __forceinline__ void cpa4(void *dst, const void *src) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kPPT = 4;
 // the block's EEDF is kept in this many interleaved copies (lane % copies):
 // electrons of a warp crowd into few low-energy bins, and same-address
 // shared-memory atomics of a warp are serialised
 constexpr int kEedfCopies = 8;
-constexpr int kChunk = kThreads * kPPT;
-static_assert(kChunk == kStepChunk, "chunk size");
+
 constexpr int kHalo = 3;
 // deposit window of a block: smaller with the prefetch staging beside it
 template <bool PF>
@@ -508,8 +506,10 @@ __host__ __device__ constexpr int win_bytes() {
 // PF: the chunk's particles come into shared memory by cp.async a chunk at
 // a time (latency-bound passes gain; passes bound by issue and shared-memory
 // traffic, like the electrons' with their collisions, lose)
-template <typename T, bool PF>
+// PPT: particles per thread in a chunk (kThreads * PPT particles)
+template <typename T, bool PF, int kPPT>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepArgs<T> a) {
+    constexpr int kChunk = kThreads * kPPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = typename V4<T>::type;
     constexpr int kWinBytes = win_bytes<PF>();
@@ -783,21 +783,29 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
         }
 }
 
-template <typename T>
-void launch_step(const StepArgs<T> &a, int grid, cudaStream_t st) {
-    // the ions' pass is latency-bound: it takes the prefetching variant
-    const bool pf = a.s == 1;
-    const size_t stage = (size_t)kChunk * (2 * sizeof(typename V4<T>::type) + sizeof(uint64_t) + sizeof(int32_t));
+template <typename T, bool PF, int PPT>
+void launch_variant(const StepArgs<T> &a, int grid, cudaStream_t st) {
+    const size_t stage =
+        PF ? (size_t)kThreads * PPT * (2 * sizeof(typename V4<T>::type) + sizeof(uint64_t) + sizeof(int32_t)) : 0;
     const size_t eedf = (size_t)(a.eedf ? a.eedf_bins : 0) * kEedfCopies * sizeof(T);
-    if (pf) {
-        const size_t smem = win_bytes<true>() + stage + eedf;
-        cudaFuncSetAttribute(k_step<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_step<T, true><<<grid, kThreads, smem, st>>>(a);
-    } else {
-        const size_t smem = win_bytes<false>() + eedf;
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_step<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_step<T, false><<<grid, kThreads, smem, st>>>(a);
+    const size_t smem = win_bytes<PF>() + stage + eedf;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_step<T, PF, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_step<T, PF, PPT><<<grid, kThreads, smem, st>>>(a);
+}
+
+// variant: bit 0 = prefetch the chunk into shared memory, bit 1 = 8
+// particles per thread (else 4); -1 = the default for the species (ions
+// prefetch: their pass is latency-bound; electrons do not: theirs is bound
+// by issue and shared-memory traffic)
+template <typename T>
+void launch_step(const StepArgs<T> &a, int grid, int variant, cudaStream_t st) {
+    const int v = variant >= 0 ? (variant & 3) : (a.s == 1 ? 1 : 0);
+    switch (v) {
+        case 0: launch_variant<T, false, 4>(a, grid, st); break;
+        case 1: launch_variant<T, true, 4>(a, grid, st); break;
+        case 2: launch_variant<T, false, 8>(a, grid, st); break;
+        default: launch_variant<T, true, 8>(a, grid, st); break;
     }
 }
 
@@ -942,7 +950,7 @@ void launch_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, const int3
 }
 
 #define PIC_INST(T)                                                                              \
-    template void launch_step<T>(const StepArgs<T> &, int, cudaStream_t);                        \
+    template void launch_step<T>(const StepArgs<T> &, int, int, cudaStream_t);                   \
     template void launch_load<T>(PBuf<T>, int64_t, int, int, int, double, double, double, double, \
                                  double, uint32_t, uint32_t, int64_t, cudaStream_t);              \
     template void launch_deposit<T>(PBuf<T>, const int32_t *, int, int, int, double *,           \

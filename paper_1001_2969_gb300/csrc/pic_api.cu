@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -94,6 +95,7 @@ struct pic_handle {
     int last_cycles = 0;
     double last_res = 0.0;
     int step_grid = 1;  // blocks of the particle pass (they walk the chunks)
+    int variant[2] = {-1, -1};  // particle-pass shape per species (-1: default)
     cudaStream_t user_st = nullptr;  // the caller's stream
     cudaStream_t gst = nullptr;      // private stream the step graphs are captured on and run on
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -106,6 +108,23 @@ struct pic_handle {
     std::vector<cudaEvent_t> ev_pool;
     double t_ms[kNumTiming] = {0, 0, 0, 0, 0};
     int64_t launches = 0, particle_launches = 0;
+};
+
+// Several reactors stepped together: each step of all of them is one graph
+// that forks into one branch per reactor (its whole timestep on the
+// reactor's private stream) and joins, keyed by the buffer parities.
+struct pic_batch {
+    std::vector<pic_handle *> hs;
+    cudaStream_t st = nullptr;      // the caller's stream
+    cudaStream_t origin = nullptr;  // where the batch graphs are captured and run
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        std::vector<int64_t> launches;  // kernels per reactor in the graph
+        bool failed = false;
+    };
+    std::map<std::vector<char>, Graph> graphs;
 };
 
 namespace {
@@ -627,7 +646,7 @@ void one_step(pic_handle *h) {
         StepArgs<T> a;
         fill_step_args<T>(h, a, s, src, dst);
         // blocks walk the chunks of the count on the device
-        launch_step<T>(a, h->step_grid, st);
+        launch_step<T>(a, h->step_grid, h->variant[s], st);
         h->launches += 1;
         h->particle_launches += 1;
     }
@@ -698,6 +717,44 @@ void capture_step(pic_handle *h, StepGraph &g) {
     g.launches = h->launches - L0;
     h->launches = L0;
     h->particle_launches = P0;
+    if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || !g.exec) {
+        g.exec = nullptr;
+        g.failed = true;
+        cudaGetLastError();
+    }
+}
+
+// capture one step of every reactor of the batch as one fork-join graph
+void capture_batch(pic_batch *b, pic_batch::Graph &g) {
+    const size_t nh = b->hs.size();
+    g.launches.assign(nh, 0);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(b->ev_fork, b->origin);
+        for (size_t k = 0; k < nh; ++k) {
+            pic_handle *h = b->hs[k];
+            const int cur = h->cur;
+            const int64_t L0 = h->launches, P0 = h->particle_launches;
+            cudaStreamWaitEvent(h->gst, b->ev_fork, 0);
+            cudaStream_t keep = h->st;
+            h->st = h->gst;
+            if (h->mixed)
+                one_step<float>(h);
+            else
+                one_step<double>(h);
+            h->st = keep;
+            h->cur = cur;  // the replays flip it
+            g.launches[k] = h->launches - L0;
+            h->launches = L0;
+            h->particle_launches = P0;
+            cudaEventRecord(b->ev_join[k], h->gst);
+            cudaStreamWaitEvent(b->origin, b->ev_join[k], 0);
+        }
+        e = cudaStreamEndCapture(b->origin, &graph);
+    }
     if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess || !g.exec) {
@@ -786,6 +843,61 @@ pic_status get_particles_t(pic_handle *h, int s, pic_particles_view *v, int64_t 
     release(h, sid);
     release(h, scell);
     return cuda_check(h, "get_particles");
+}
+
+// After the steps of a call are enqueued: the one synchronisation of the
+// call, then the step control and the status word decide the outcome; the
+// host copies of the step number, ids and solve statistics are refreshed,
+// and on a halt the state is left at the last completed step.
+pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int32_t nsteps) {
+    StepCtl c;
+    int32_t status = 0;
+    cudaMemcpyAsync(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(&status, &h->ds->status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    pic_status ce = cuda_check(h, "step");
+    if (ce != PIC_OK) return ce;
+    const int64_t done = c.halt ? c.halt_step - step0 : (int64_t)nsteps;
+    h->cur = (int)(cur0 ^ (int)(done & 1));
+    h->step = step0 + done;
+    h->nsamples += done;
+    h->steps_total += done;
+    h->sp[0].next_id = c.next_id[0];
+    h->sp[1].next_id = c.next_id[1];
+    h->mg_cycles_total = (int64_t)c.mg_cycles;
+    h->last_cycles = c.mg_last_cycles;
+    h->last_res = c.mg_last_res;
+    pic_status result = PIC_OK;
+    if (c.mg_flags & 1) {
+        result = PIC_ERR_NOT_CONVERGED;
+        h->err = "multigrid stopped before the tolerance";
+        const int32_t z = 0;
+        cudaMemcpyAsync(&h->sctl->mg_flags, &z, sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+    }
+    if (status & ST_NAN) {
+        result = PIC_ERR_NUMERIC;
+        h->err = "non-finite particle state (particles dropped)";
+        cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
+    }
+    if (c.halt) {
+        // the state stays at the last completed step
+        const int32_t z[3] = {0, 0, 0};
+        cudaMemcpyAsync(&h->sctl->halt, z, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+        cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
+        if (c.halt_status & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
+            if (h->mixed)
+                deposit_current<float>(h);
+            else
+                deposit_current<double>(h);
+            cudaStreamSynchronize(h->st);
+            return fail(h, PIC_ERR_CAPACITY, (c.halt_status & ST_CAPACITY) ? "particle capacity exceeded"
+                                                                           : "births capacity exceeded");
+        }
+        cudaStreamSynchronize(h->st);
+        return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
+    }
+    cudaStreamSynchronize(h->st);
+    return result;
 }
 
 }  // namespace
@@ -929,55 +1041,145 @@ pic_status pic_step(pic_handle *h, int32_t nsteps) {
         cudaEventRecord(h->ev_out, h->gst);
         cudaStreamWaitEvent(h->st, h->ev_out, 0);
     }
-    // the one synchronisation of the call: the step control and the status word
-    StepCtl c;
-    int32_t status = 0;
-    cudaMemcpyAsync(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
-    cudaMemcpyAsync(&status, &h->ds->status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-    cudaStreamSynchronize(h->st);
-    pic_status ce = cuda_check(h, "step");
-    if (ce != PIC_OK) return ce;
-    const int64_t done = c.halt ? c.halt_step - step0 : (int64_t)nsteps;
-    h->cur = (int)(cur0 ^ (int)(done & 1));
-    h->step = step0 + done;
-    h->nsamples += done;
-    h->steps_total += done;
-    h->sp[0].next_id = c.next_id[0];
-    h->sp[1].next_id = c.next_id[1];
-    h->mg_cycles_total = (int64_t)c.mg_cycles;
-    h->last_cycles = c.mg_last_cycles;
-    h->last_res = c.mg_last_res;
-    pic_status result = PIC_OK;
-    if (c.mg_flags & 1) {
-        result = PIC_ERR_NOT_CONVERGED;
-        h->err = "multigrid stopped before the tolerance";
-        const int32_t z = 0;
-        cudaMemcpyAsync(&h->sctl->mg_flags, &z, sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+    return finish_call(h, step0, cur0, nsteps);
+}
+
+pic_status pic_tune(pic_handle *h, int32_t steps_per_variant, int32_t *variants) {
+    if (!h || steps_per_variant < 0) return PIC_ERR_ARG;
+    if (steps_per_variant == 0) {
+        if (!variants) return fail(h, PIC_ERR_ARG, "no variants given");
+        for (int s = 0; s < 2; ++s)
+            if (variants[s] < -1 || variants[s] >= kStepVariants) return fail(h, PIC_ERR_ARG, "bad variant");
+        h->variant[0] = variants[0];
+        h->variant[1] = variants[1];
+        drop_graphs(h);  // the shape is part of the captured step
+        return PIC_OK;
     }
-    if (status & ST_NAN) {
-        result = PIC_ERR_NUMERIC;
-        h->err = "non-finite particle state (particles dropped)";
-        cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
+    // time every shape on real steps of this reactor (the simulation advances)
+    const bool prof = h->prof;
+    double best[2] = {1e300, 1e300};
+    int pick[2] = {-1, -1};
+    double t[kNumTiming];
+    int64_t pl = 0, al = 0;
+    pic_timings(h, nullptr, nullptr, nullptr, 1);
+    for (int v = 0; v < kStepVariants; ++v) {
+        h->variant[0] = h->variant[1] = v;
+        h->prof = true;
+        pic_status st = pic_step(h, steps_per_variant);
+        h->prof = prof;
+        if (st != PIC_OK && st != PIC_ERR_NOT_CONVERGED) return st;
+        pic_timings(h, t, &pl, &al, 1);
+        for (int s = 0; s < 2; ++s)
+            if (t[1 + s] < best[s]) {
+                best[s] = t[1 + s];
+                pick[s] = v;
+            }
     }
-    if (c.halt) {
-        // the state stays at the last completed step
-        const int32_t z[3] = {0, 0, 0};
-        cudaMemcpyAsync(&h->sctl->halt, z, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
-        cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
-        if (c.halt_status & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
-            if (h->mixed)
-                deposit_current<float>(h);
-            else
-                deposit_current<double>(h);
-            cudaStreamSynchronize(h->st);
-            return fail(h, PIC_ERR_CAPACITY, (c.halt_status & ST_CAPACITY) ? "particle capacity exceeded"
-                                                                           : "births capacity exceeded");
+    h->variant[0] = pick[0];
+    h->variant[1] = pick[1];
+    drop_graphs(h);
+    if (variants) {
+        variants[0] = pick[0];
+        variants[1] = pick[1];
+    }
+    return PIC_OK;
+}
+
+pic_status pic_batch_init(pic_handle *const *handles, int32_t n, void *stream, pic_batch **out) {
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!handles || n < 1) return PIC_ERR_ARG;
+    for (int k = 0; k < n; ++k) {
+        if (!handles[k] || !handles[k]->gst) return PIC_ERR_ARG;
+        for (int q = 0; q < k; ++q)
+            if (handles[q] == handles[k]) return PIC_ERR_ARG;
+    }
+    pic_batch *b = new (std::nothrow) pic_batch();
+    if (!b) return PIC_ERR_ARG;
+    b->hs.assign(handles, handles + n);
+    b->st = (cudaStream_t)stream;
+    bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    b->ev_join.assign(n, nullptr);
+    for (int k = 0; k < n && ok; ++k)
+        ok = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        pic_batch_destroy(b);
+        return PIC_ERR_CUDA;
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
+    if (!b || nsteps < 0) return PIC_ERR_ARG;
+    const size_t nh = b->hs.size();
+    for (pic_handle *h : b->hs)
+        if (h->prof) return fail(h, PIC_ERR_ARG, "batched steps need profiling off");
+    std::vector<int64_t> step0(nh);
+    std::vector<int> cur0(nh);
+    for (size_t k = 0; k < nh; ++k) {
+        step0[k] = b->hs[k]->step;
+        cur0[k] = b->hs[k]->cur;
+        // the reactor's own work so far comes first
+        cudaEventRecord(b->hs[k]->ev_in, b->hs[k]->st);
+        cudaStreamWaitEvent(b->origin, b->hs[k]->ev_in, 0);
+    }
+    cudaEventRecord(b->ev_in, b->st);
+    cudaStreamWaitEvent(b->origin, b->ev_in, 0);
+    for (int s = 0; s < nsteps; ++s) {
+        std::vector<char> key(nh);
+        for (size_t k = 0; k < nh; ++k) key[k] = (char)b->hs[k]->cur;
+        pic_batch::Graph &g = b->graphs[key];
+        if (!g.exec && !g.failed) capture_batch(b, g);
+        if (g.exec) {
+            cudaGraphLaunch(g.exec, b->origin);
+            for (size_t k = 0; k < nh; ++k) {
+                b->hs[k]->cur ^= 1;
+                b->hs[k]->particle_launches += 2;
+                b->hs[k]->launches += g.launches[k];
+            }
+            continue;
         }
-        cudaStreamSynchronize(h->st);
-        return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
+        // no graph: the reactors' steps one after another
+        for (pic_handle *h : b->hs) {
+            cudaStream_t keep = h->st;
+            h->st = b->origin;
+            if (h->mixed)
+                one_step<float>(h);
+            else
+                one_step<double>(h);
+            h->st = keep;
+        }
     }
-    cudaStreamSynchronize(h->st);
-    return result;
+    cudaEventRecord(b->ev_out, b->origin);
+    cudaStreamWaitEvent(b->st, b->ev_out, 0);
+    for (pic_handle *h : b->hs) cudaStreamWaitEvent(h->st, b->ev_out, 0);
+    cudaStreamSynchronize(b->st);
+    pic_status first = PIC_OK;
+    for (size_t k = 0; k < nh; ++k) {
+        const pic_status r = nsteps > 0 ? finish_call(b->hs[k], step0[k], cur0[k], nsteps) : PIC_OK;
+        if (statuses) statuses[k] = r;
+        if (first == PIC_OK && r != PIC_OK) first = r;
+    }
+    return first;
+}
+
+void pic_batch_destroy(pic_batch *b) {
+    if (!b) return;
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    for (auto &kv : b->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (cudaEvent_t e : b->ev_join)
+        if (e) cudaEventDestroy(e);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    delete b;
 }
 
 pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, double V,

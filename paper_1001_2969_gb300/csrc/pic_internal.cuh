@@ -198,11 +198,13 @@ struct StepArgs {
     T eedf_scale;  // bins per eV
 };
 
-constexpr int kStepChunk = 1024;  // particles per chunk of the particle kernel
 
 // ---- launchers (particles.cu) ----
+// variant: particle-pass shape (bit 0 shared-memory prefetch, bit 1 eight
+// particles per thread), -1 the species' default
+constexpr int kStepVariants = 4;
 template <typename T>
-void launch_step(const StepArgs<T> &a, int grid, cudaStream_t st);
+void launch_step(const StepArgs<T> &a, int grid, int variant, cudaStream_t st);
 template <typename T>
 void launch_load(PBuf<T> dst, int64_t n, int s, int nz, int nr, double dz, double dr,
                  double n0, double T_eV, double m, uint32_t key0, uint32_t key1,

@@ -86,7 +86,8 @@ class pic_moments_out(C.Structure):
 SYMBOLS = ("pic_init", "pic_step", "pic_field_solve", "pic_moments", "pic_get_particles",
            "pic_set_particles", "pic_set_step", "pic_set_boundary", "pic_get_fields",
            "pic_get_counts", "pic_save", "pic_load", "pic_profile", "pic_timings", "pic_destroy",
-           "pic_last_error", "pic_status_string", "pic_field_solve_noalloc")
+           "pic_last_error", "pic_status_string", "pic_field_solve_noalloc", "pic_batch_init",
+           "pic_batch_step", "pic_batch_destroy", "pic_tune")
 
 
 class PicError(RuntimeError):
@@ -108,6 +109,11 @@ def lib():
         vp = C.c_void_p
         L.pic_init.argtypes = [C.POINTER(pic_config), C.POINTER(vp)]
         L.pic_step.argtypes = [vp, C.c_int32]
+        L.pic_batch_init.argtypes = [C.POINTER(vp), C.c_int32, vp, C.POINTER(vp)]
+        L.pic_batch_step.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.pic_batch_destroy.argtypes = [vp]
+        L.pic_batch_destroy.restype = None
+        L.pic_tune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
         L.pic_field_solve.argtypes = [vp, vp, vp, C.c_double, vp, C.c_int32,
                                       C.POINTER(pic_solve_info)]
         L.pic_moments.argtypes = [vp, C.POINTER(pic_moments_out), C.c_int32]
@@ -247,6 +253,56 @@ def pic_init(cfg: dict, load: bool = True, stream=None, torch_memory: bool = Tru
 
 def pic_step(h: Handle, nsteps: int = 1) -> int:
     return _check(h, lib().pic_step(h.ptr, int(nsteps)))
+
+
+class Batch:
+    """Reactors stepped together (pic_batch_*); keeps its handles alive."""
+
+    def __init__(self, handles, stream=None):
+        self.handles = list(handles)
+        arr = (C.c_void_p * len(self.handles))(*[h.ptr for h in self.handles])
+        ptr = C.c_void_p()
+        st = lib().pic_batch_init(arr, len(self.handles), stream, C.byref(ptr))
+        if st != PIC_OK:
+            raise PicError(st, f"pic_batch_init failed: {lib().pic_status_string(st).decode()}")
+        self.ptr = ptr
+
+    def step(self, nsteps: int = 1):
+        """Advance every reactor; returns the per-reactor statuses (as pic_step's)."""
+        sts = (C.c_int32 * len(self.handles))()
+        lib().pic_batch_step(self.ptr, int(nsteps), sts)
+        out = list(sts)
+        for h, st in zip(self.handles, out):
+            _check(h, st)
+        return out
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().pic_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        self.close()
+
+
+def pic_tune(h: Handle, steps_per_variant: int = 2, variants=None):
+    """Time the particle-pass shapes (or set them when steps_per_variant is 0);
+    returns the shapes in use [electrons, ions]."""
+    v = (C.c_int32 * 2)(*(variants if variants is not None else (-1, -1)))
+    _check(h, lib().pic_tune(h.ptr, int(steps_per_variant), v))
+    return list(v)
+
+
+def pic_batch_init(handles, stream=None) -> Batch:
+    return Batch(handles, stream)
+
+
+def pic_batch_step(b: Batch, nsteps: int = 1):
+    return b.step(nsteps)
+
+
+def pic_batch_destroy(b: Batch) -> None:
+    b.close()
 
 
 def pic_field_solve(h: Handle, rho, chi, V: float):

@@ -115,6 +115,39 @@ def config(name: str, **over) -> dict:
     return cfg
 
 
+def batch_configs(n: int = 64, seed: int = 4, n_lo: int = 50_000, n_hi: int = 5_000_000,
+                  precision: str = "mixed") -> list:
+    """The batched sweep (c4): n independent argon reactors drawn from `seed`.
+
+    Mesh nz in {33, 65, 129} and nr in {65, ..., 513} (at least 2 nz - 1)
+    with c2's cell size (R and L follow the mesh), particles per species
+    log-uniform in [n_lo, n_hi], pressure log-uniform in [1, 100] Pa, voltage
+    uniform in [50, 500] V at 13.56 MHz, n0 5e15 m^-3, dt = T_rf/200; reactor k
+    takes Philox seed 1000 + k.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        nz = int(rng.choice([33, 65, 129]))
+        nr_opts = [r for r in (65, 129, 257, 513) if r >= 2 * nz - 1]
+        nr = int(rng.choice(nr_opts))
+        npart = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        p = float(np.exp(rng.uniform(np.log(1.0), np.log(100.0))))
+        v = float(rng.uniform(50.0, 500.0))
+        cfg = dict(R=0.20 * (nr - 1) / 512, L=0.025 * (nz - 1) / 128, nz=nz, nr=nr,
+                   species=_species(5e15, npart),
+                   rf=dict(amp=[v], freq=[F_RF], phase=[0.0]),
+                   gas=dict(p_Pa=p, T_K=300.0, m_gas=M_AR),
+                   dt=1.0 / F_RF / 200, steps=500, split_every=200)
+        cfg["xsec"] = argon_tables(4.0 * v)
+        cfg.update(dict(seed=1000 + k, weighting="zr2", chi_face="max", scatter="vs",
+                        mg_max_cycles=50, mg_tol=1e-10, phi_zL=None, eedf_bins=200,
+                        eedf_emax=100.0, precision=precision))
+        cfg["name"] = f"c4-{k}"
+        out.append(cfg)
+    return out
+
+
 def scaled(cfg: dict, n_per_species: int) -> dict:
     """Same workload with a different particle count (capacity follows)."""
     out = dict(cfg)
