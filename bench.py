@@ -301,6 +301,63 @@ def accuracy_vs_oracle(cfg_name, n_per_species, stream):
     return out
 
 
+def batch_run(args):
+    """The batched sweep: args.batch independent reactors (workloads.batch_configs),
+    each tuned, then stepped together (one graph launch per step) and, for
+    comparison, one after another; particle-steps/s over all reactors."""
+    import torch
+    import workloads as W
+    from paper_1001_2969_gb300 import pic
+
+    stream = torch.cuda.current_stream()
+    cfgs = W.batch_configs(n=args.batch, precision=args.precision)
+    t0 = time.perf_counter()
+    hs = [pic.pic_init(c, stream=stream.cuda_stream) for c in cfgs]
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    shapes = [pic.pic_tune(h, 1) for h in hs]
+    t_tune = time.perf_counter() - t0
+    b = pic.pic_batch_init(hs, stream.cuda_stream)
+    b.step(args.warmup)
+
+    def count():
+        return sum(int(pic.pic_get_counts(h)["n_alive"].sum()) for h in hs)
+
+    def timed(fn):
+        n0 = count()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return 0.5 * (n0 + count()) * args.steps / (ms * 1e-3), ms / args.steps
+
+    v_batch, ms_batch = timed(lambda: b.step(args.steps))
+
+    def one_by_one():
+        for _ in range(args.steps):
+            for h in hs:
+                pic.pic_step(h, 1)
+
+    v_seq, ms_seq = timed(one_by_one)
+    b.close()
+    line = {"metric": "particle-steps/s of a batch of independent reactors", "unit": UNIT,
+            "value": v_batch, "ms_per_step": ms_batch, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.batch} reactors drawn by workloads.batch_configs (seed 4): "
+                                   "33x65 to 129x513 nodes, 5e4-5e6 particles per species, "
+                                   "1-100 Pa, 50-500 V at 13.56 MHz",
+                       "particles": count(), "precision": args.precision},
+            "one_reactor_after_another": {"value": v_seq, "ms_per_step": ms_seq},
+            "tuned_shapes": {"electrons": [s[0] for s in shapes], "ions": [s[1] for s in shapes]},
+            "init_s": t_init, "tune_s": t_tune}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,12 +375,16 @@ def main():
                     help="time only the stand-alone field solve on the workload's mesh")
     ap.add_argument("--particles", type=int, default=0,
                     help="particles per species (default: the workload's; smaller for profiling)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time a batch of this many independent reactors instead (batched sweep)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.solve_only:
         return solve_only(args) if rank == 0 else 0
+    if args.batch > 0:
+        return batch_run(args) if rank == 0 else 0
 
     if args.impl == "reference":
         if rank != 0:
