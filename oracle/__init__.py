@@ -70,6 +70,7 @@ class OrcConfig(C.Structure):
         ("weighting", C.c_int32), ("chi_face", C.c_int32), ("scatter", C.c_int32),
         ("split_every", C.c_int32), ("mg_max_cycles", C.c_int32), ("mg_tol", C.c_double),
         ("phi_zL", _dp), ("eedf_bins", C.c_int32), ("eedf_emax", C.c_double),
+        ("circuit_C", C.c_double),
     ]
 
 
@@ -120,6 +121,7 @@ def _declare(L):
     L.orc_scatter_dir.argtypes = [C.c_double] * 5 + [_dp]
     L.orc_ejected_energy.restype = C.c_double
     L.orc_ejected_energy.argtypes = [C.c_double] * 4
+    L.orc_get_circuit.argtypes = [vp, _dp]
     L.orc_w_ref.restype = C.c_double
     L.orc_w_ref.argtypes = [vp, C.c_int, C.c_int]
 
@@ -189,6 +191,7 @@ class Oracle:
             c.phi_zL = _ptr(pz)
         c.eedf_bins = cfg.get("eedf_bins", 0)
         c.eedf_emax = cfg.get("eedf_emax", 100.0)
+        c.circuit_C = float(cfg.get("circuit_C", 0.0))
         if capacity is None:
             capacity = max(int(1.5 * max(sp["capacity"] for sp in cfg["species"])), 64)
         self.capacity = capacity
@@ -336,6 +339,12 @@ class Oracle:
 
     def cos_chi(self, eps, R):
         return lib().orc_cos_chi(self.h, eps, R)
+
+    def circuit(self):
+        """(electrode voltage V, electrode charge Q, capacitor charge Q_c) after the last step."""
+        out = np.zeros(3)
+        lib().orc_get_circuit(self.h, _ptr(out))
+        return tuple(out)
 
     def w_ref(self, s, j):
         return lib().orc_w_ref(self.h, s, j)

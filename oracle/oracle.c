@@ -52,6 +52,10 @@ struct orc_state {
     double ng, nu_max[2], p_null[2];
     int64_t cnt[ORC_C_NCOUNT];
     double qabs[ORC_Q_NCOUNT];
+    double qpass[ORC_Q_NCOUNT]; /* absorbed charge of the last particle pass */
+    /* external circuit: superposition parts of phi and the circuit state */
+    double *phiP, *phiL, *zero;
+    double circ_V, circ_Q, circ_Qc;
     /* births of the current pass */
     orc_birth *b;
     int64_t nb, bcap;
@@ -385,6 +389,9 @@ orc_state *orc_create(const orc_config *cfg, int64_t capacity) {
     st->phi = xmalloc(ng * sizeof(double));
     st->Ez = xmalloc(ng * sizeof(double));
     st->Er = xmalloc(ng * sizeof(double));
+    st->phiP = xmalloc(ng * sizeof(double));
+    st->phiL = xmalloc(ng * sizeof(double));
+    st->zero = xmalloc(ng * sizeof(double));
     st->m_ne = xmalloc(ng * sizeof(double));
     st->m_ni = xmalloc(ng * sizeof(double));
     st->m_phi = xmalloc(ng * sizeof(double));
@@ -421,6 +428,9 @@ void orc_destroy(orc_state *st) {
     free(st->phi);
     free(st->Ez);
     free(st->Er);
+    free(st->phiP);
+    free(st->phiL);
+    free(st->zero);
     free(st->m_ne);
     free(st->m_ni);
     free(st->m_phi);
@@ -1013,6 +1023,7 @@ static void first_push(const orc_state *st, orc_p *q) {
 static void absorb(orc_state *st, int s, int wall, double w) {
     st->cnt[ORC_C_ABS + s * 3 + wall] += 1;
     st->qabs[wall] += st->c.q[s] * w;
+    st->qpass[wall] += st->c.q[s] * w;
 }
 
 /* newborn: first push, wall test, record */
@@ -1213,6 +1224,7 @@ void orc_particle_pass(orc_state *st) {
     uint32_t step = (uint32_t)st->step;
     int do_split = st->c.split_every > 0 && (st->step % st->c.split_every) == st->c.split_every - 1;
     st->nb = 0;
+    memset(st->qpass, 0, sizeof(st->qpass));
     if (st->c.eedf_bins > 0) memset(st->eedf_pass, 0, st->c.eedf_bins * sizeof(double));
     for (int s = 0; s < 2; ++s) {
         orc_store *P = &st->p[s];
@@ -1296,6 +1308,71 @@ void orc_particle_pass(orc_state *st) {
 }
 
 /*
+ * Charge on the z = 0 electrode (nodes j < nr-1; the corner belongs to the
+ * grounded wall).  READING (the paper gives the circuit, not the discrete
+ * charge): Gauss's law on the electrode row of the finite-volume mesh, i.e.
+ * the displacement flux eps0 c_{0j} (phi_0j - phi_1j) through the z-face
+ * into row 1, less the charge rho_0j V_0j of the half cell in front of the
+ * electrode.
+ */
+static double electrode_charge(const orc_state *st, const double *phi, const double *rho,
+                               const double *V) {
+    int nr = st->c.nr;
+    double q = 0.0;
+    for (int j = 0; j < nr - 1; ++j) {
+        double c0 = (1.0 + face_chi(st, st->chi[IDX(0, j)], st->chi[IDX(1, j)])) * area_z(st, j) / st->dz;
+        q += ORC_EPS0 * c0 * (phi[IDX(0, j)] - phi[IDX(1, j)]) - rho[IDX(0, j)] * V[IDX(0, j)];
+    }
+    return q;
+}
+
+/*
+ * External circuit (Sec. 2.5, end), Vahedi's superposition: with a blocking
+ * capacitor C between the rf source and the z = 0 electrode, phi_P solves
+ * the plasma's charge with the electrode at 0 (other boundaries as usual),
+ * phi_L the charge-free problem with the electrode at 1 and every other
+ * boundary at 0, both with the same coefficient 1 + chi (each warm-started
+ * from its last solution).  The electrode charge is linear in its voltage,
+ * Q = Q_P + V Q_L, and the circuit equation
+ *   Q^t = Q^{t-1} + C (V_rf^t - V^t) - Q_c^{t-1} + Q_conv^t,
+ * with Q_c^t = C (V_rf^t - V^t) and Q_conv the charge the electrode
+ * collected in the last particle pass, fixes V^t; then
+ * phi = phi_P + V^t phi_L.  READING: Q and Q_c start at 0.
+ */
+static void circuit_solve(orc_state *st, double Vrf, const double *V, int *cycles, double *rel_res) {
+    int64_t ng = (int64_t)st->c.nz * st->c.nr;
+    double *keep_phi = st->phi, *keep_rho = st->rho;
+    const double *keep_zL = st->c.phi_zL;
+    int c1 = 0, c2 = 0;
+    double r1 = 0.0, r2 = 0.0;
+    st->phi = st->phiP;
+    orc_solve(st, 0.0, st->c.mg_tol, st->c.mg_max_cycles, &c1, &r1);
+    st->phi = st->phiL;
+    st->rho = st->zero;
+    st->c.phi_zL = NULL;
+    orc_solve(st, 1.0, st->c.mg_tol, st->c.mg_max_cycles, &c2, &r2);
+    st->phi = keep_phi;
+    st->rho = keep_rho;
+    st->c.phi_zL = keep_zL;
+    double QP = electrode_charge(st, st->phiP, st->rho, V);
+    double QL = electrode_charge(st, st->phiL, st->zero, V);
+    double C = st->c.circuit_C;
+    double Vt = (st->circ_Q - st->circ_Qc + C * Vrf + st->qpass[0] - QP) / (QL + C);
+    st->circ_V = Vt;
+    st->circ_Q = QP + Vt * QL;
+    st->circ_Qc = C * (Vrf - Vt);
+    for (int64_t k = 0; k < ng; ++k) st->phi[k] = st->phiP[k] + Vt * st->phiL[k];
+    if (cycles) *cycles = c1 + c2;
+    if (rel_res) *rel_res = r1 > r2 ? r1 : r2;
+}
+
+void orc_get_circuit(const orc_state *st, double out[3]) {
+    out[0] = st->circ_V;
+    out[1] = st->circ_Q;
+    out[2] = st->circ_Qc;
+}
+
+/*
  * One timestep (Sec. 2.1 cycle, merged form): rho, chi from the deposit at
  * x~ -> solve at t_{n+1} -> E -> particle pass -> deposit at the new x~ ->
  * time averages (Sec. 3: moments averaged over time).
@@ -1309,7 +1386,10 @@ void orc_step(orc_state *st, int nsteps, int *last_cycles, double *last_res) {
         double t = (double)(st->step + 1) * st->c.dt;
         int cyc = 0;
         double res = 0.0;
-        orc_solve(st, orc_voltage(st, t), st->c.mg_tol, st->c.mg_max_cycles, &cyc, &res);
+        if (st->c.circuit_C > 0.0)
+            circuit_solve(st, orc_voltage(st, t), V, &cyc, &res);
+        else
+            orc_solve(st, orc_voltage(st, t), st->c.mg_tol, st->c.mg_max_cycles, &cyc, &res);
         if (last_cycles) *last_cycles = cyc;
         if (last_res) *last_res = res;
         orc_efield(st);

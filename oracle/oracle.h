@@ -85,6 +85,9 @@ typedef struct {
     const double *phi_zL; /* nullable: nr potentials on z = L */
     int32_t eedf_bins;
     double eedf_emax;
+    /* external circuit (Sec. 2.5, end): blocking capacitor (F) between the
+     * rf source and the z = 0 electrode; 0 drives the electrode directly */
+    double circuit_C;
 } orc_config;
 
 typedef struct orc_state orc_state;
@@ -107,6 +110,10 @@ void orc_set_next_id(orc_state *st, int s, uint64_t next_id);
 uint64_t orc_get_next_id(const orc_state *st, int s);
 void orc_set_step(orc_state *st, int64_t step);
 int64_t orc_get_step(const orc_state *st);
+
+/* external circuit state: out[0] electrode voltage V, out[1] electrode
+ * charge Q, out[2] capacitor charge Q_c (C, after the last step) */
+void orc_get_circuit(const orc_state *st, double out[3]);
 
 /* loading: the whole load, or particles [p0, p1) of species s only */
 void orc_load(orc_state *st);
