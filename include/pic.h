@@ -127,6 +127,10 @@ typedef struct pic_config {
     pic_free_fn free;
     void *alloc_ctx;
     void *stream;         /* cudaStream_t */
+    /* external circuit (Sec. 2.5, end): a blocking capacitor circuit_C (F)
+     * between the rf source and the z = 0 electrode, solved by Vahedi's
+     * superposition each step; 0 drives the electrode directly */
+    double circuit_C;
 } pic_config;
 
 typedef struct pic_handle pic_handle;
@@ -311,6 +315,14 @@ pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64
 
 /* pic_save / pic_load -- checkpoint: particles, phi, step, ids, counters.
  * Resuming is bit-exact because every draw is keyed by (id, step). */
+/*
+ * pic_get_circuit -- state of the external circuit after the last step:
+ * out[0] electrode voltage V (V), out[1] electrode charge Q (C), out[2]
+ * capacitor charge Q_c = circuit_C (V_rf - V) (C).  All zero without a
+ * circuit.  out: 3 doubles, host memory.
+ */
+pic_status pic_get_circuit(pic_handle *h, double *out);
+
 pic_status pic_save(pic_handle *h, const char *path);
 pic_status pic_load(pic_handle *h, const char *path);
 

@@ -302,11 +302,12 @@ __device__ __forceinline__ void warp_line_solve(const Ts *__restrict__ F, Ts *Bs
 
 // right-hand side rho A_j dz / eps0 and the Dirichlet data of phi
 __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, double *phi, const double *phi_zL,
-                         double V_arg, int nz, int nr, double dz, double dr, int cold, const StepCtl *ctl) {
+                         double V_arg, int nz, int nr, double dz, double dr, int cold, const StepCtl *ctl,
+                         int v_from_ctl) {
     const MGFast &m = *mp;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nz * nr || (ctl && ctl->halt)) return;
-    const double V = ctl ? ctl->V : V_arg;  // in a timestep the voltage comes with the step
+    const double V = (ctl && v_from_ctl) ? ctl->V : V_arg;  // in a timestep the source voltage comes with the step
     const int i = k / nr, j = k % nr;
     double v = 0.0, dg = 0.0;
     if (i > 0 && i < nz - 1 && j < nr - 1) {
@@ -894,7 +895,10 @@ namespace {
 
 // a timestep's solve reports to the step control instead of the host: V-cycle
 // count, residual, an unconverged flag, and a halt on a timed-out wait
-__global__ void k_solve_done(const MGCtl *c, StepCtl *s) {
+// `cont`: a second solve with the previous one's operator (the external
+// circuit's charge-free part) adds its cycles to the step's last report and
+// keeps the larger residual
+__global__ void k_solve_done(const MGCtl *c, StepCtl *s, int cont) {
     if (s->halt) return;
     if (c->timeout) {
         s->halt = 1;
@@ -904,8 +908,14 @@ __global__ void k_solve_done(const MGCtl *c, StepCtl *s) {
     }
     const int cyc = c->zero_rhs ? 0 : c->cycles;
     s->mg_cycles += (unsigned long long)cyc;
-    s->mg_last_cycles = cyc;
-    s->mg_last_res = (c->zero_rhs || !(c->bnorm > 0.0)) ? 0.0 : c->last_res / c->bnorm;
+    const double res = (c->zero_rhs || !(c->bnorm > 0.0)) ? 0.0 : c->last_res / c->bnorm;
+    if (cont) {
+        s->mg_last_cycles += cyc;
+        s->mg_last_res = fmax(s->mg_last_res, res);
+    } else {
+        s->mg_last_cycles = cyc;
+        s->mg_last_res = res;
+    }
     if (!c->zero_rhs && !c->converged) s->mg_flags |= 1;
 }
 
@@ -918,14 +928,18 @@ void mg_fast_upload(MGFast &m, cudaStream_t st) {
 
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
-                  int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st) {
+                  int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
+                  bool v_from_ctl, bool setup) {
     const int nz = fd.nz, nr = fd.nr, n = nr - 1, ng = nz * nr;
     const int M = line_chunk(n);
     const int nlev = m.nlev;
     int L = 0;
     raise_smem_limits();
     MGFast *mp = m.self;  // uploaded once (mg_fast_upload)
-    // set-up: levels' chi, coefficients, line factors, right-hand side and boundary data
+    // set-up: levels' chi, coefficients, line factors (skipped when the
+    // operator is the one of the previous solve), right-hand side and
+    // boundary data
+    if (setup) {
     cudaMemcpyAsync(m.chi[0], chi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st);
     if (nlev > 1) {
         k_chi_levels<<<(nr + 7) / 8, 256, (size_t)8 * 2 * nz * sizeof(double), st>>>(mp, nr, sctl);
@@ -952,8 +966,9 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
             ++L;
         }
     }
+    }
     k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(mp, rho, phi, phi_zL, V, nz, nr, fd.dz, fd.dr,
-                                               warm ? 0 : 1, sctl);
+                                               warm ? 0 : 1, sctl, v_from_ctl ? 1 : 0);
     ++L;
     // the solve alternates between phi and a copy (both carry the boundary values)
     cudaMemcpyAsync(m.phi2, phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st);
@@ -1007,7 +1022,7 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     }
     if (sctl) {
         // inside a timestep: the result stays on the device
-        k_solve_done<<<1, 1, 0, st>>>(m.ctl, sctl);
+        k_solve_done<<<1, 1, 0, st>>>(m.ctl, sctl, setup ? 0 : 1);
         ++L;
         if (launches) *launches += L;
         return 0;

@@ -774,7 +774,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     __syncthreads();
     for (int k = tid; k < PIC_NCOUNT; k += blockDim.x)
         if (bt.cnt[k]) atomicAdd(&a.ds->cnt[k], bt.cnt[k]);
-    if (tid < 3 && bt.q[tid] != 0.0) atomicAdd(&a.ds->qabs[tid], bt.q[tid]);
+    if (tid < 3 && bt.q[tid] != 0.0) {
+        atomicAdd(&a.ds->qabs[tid], bt.q[tid]);
+        atomicAdd(&a.ds->qstep[tid], bt.q[tid]);
+    }
     if (a.eedf)
         for (int k = tid; k < a.eedf_bins; k += blockDim.x) {
             double v = 0.0;

@@ -84,6 +84,8 @@ struct pic_handle {
     void *E2 = nullptr;
     double *phiL_d = nullptr;
     bool has_phiL = false;
+    // external circuit: the two superposition parts of phi and an empty charge grid
+    double *phi_P = nullptr, *phi_L = nullptr, *zero_grid = nullptr;
     double *m_acc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     double *eedf = nullptr;
     double *tmp_grid[3] = {nullptr, nullptr, nullptr};
@@ -214,6 +216,8 @@ pic_status validate(const pic_config *c, std::string &why) {
     if (c->scatter != PIC_SCATTER_VS && c->scatter != PIC_SCATTER_ISOTROPIC) return bad("scatter");
     if (c->split_every < 0) return bad("split_every must be >= 0");
     if (c->mg_max_cycles < 1) return bad("mg_max_cycles must be >= 1");
+    if (!(c->circuit_C >= 0.0) || !std::isfinite(c->circuit_C))
+        return bad("circuit_C must be finite and >= 0 (0: the electrode follows the source)");
     if (c->eedf_bins < 0 || c->eedf_bins > 4096) return bad("eedf_bins must be in [0, 4096]");
     if (c->eedf_bins > 0 && !(c->eedf_emax_eV > 0)) return bad("eedf_emax_eV must be positive");
     if (!(c->gas.T_K > 0) || !(c->gas.m_gas > 0) || c->gas.p_Pa < 0) return bad("gas");
@@ -297,6 +301,53 @@ __global__ void k_step_end(StepCtl *c, int32_t *nalive0, const int32_t *ntotal0,
     *nalive0 = *ntotal0;
     *nalive1 = *ntotal1;
     c->step += 1;
+}
+
+// External circuit (Sec. 2.5, end), Vahedi's superposition: the charge on
+// the z = 0 electrode (Gauss's law on the electrode row: displacement flux
+// eps0 c_0j (phi_0j - phi_1j) into row 1 less the half-cell charge
+// rho_0j V_0j, nodes j < nr - 1) is Q_P + V Q_L; the circuit equation
+// Q^t = Q^{t-1} + C (V_rf^t - V^t) - Q_c^{t-1} + Q_conv^t then fixes V^t.
+// One block.
+__global__ void k_circuit(StepCtl *c, DevScalars *ds, const double *cz0, const double *phiP,
+                          const double *phiL, const double *rho, const double *Vn, int nr, double C) {
+    __shared__ double sP[32], sL[32];
+    if (c->halt) return;
+    double qp = 0.0, ql = 0.0;
+    for (int j = threadIdx.x; j < nr - 1; j += blockDim.x) {
+        qp += kEps0 * cz0[j] * (phiP[j] - phiP[nr + j]) - rho[j] * Vn[j];
+        ql += kEps0 * cz0[j] * (phiL[j] - phiL[nr + j]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        qp += __shfl_xor_sync(0xffffffffu, qp, o);
+        ql += __shfl_xor_sync(0xffffffffu, ql, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sP[threadIdx.x >> 5] = qp;
+        sL[threadIdx.x >> 5] = ql;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double QP = 0.0, QL = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            QP += sP[w];
+            QL += sL[w];
+        }
+        const double Vrf = c->V;
+        const double Vt = (c->circ_Q - c->circ_Qc + C * Vrf + ds->qstep[0] - QP) / (QL + C);
+        c->circ_V = Vt;
+        c->circ_Q = QP + Vt * QL;
+        c->circ_Qc = C * (Vrf - Vt);
+        // the collected charge is taken; the coming particle pass adds anew
+        ds->qstep[0] = ds->qstep[1] = ds->qstep[2] = 0.0;
+    }
+}
+
+// phi = phi_P + V phi_L
+__global__ void k_superpose(const StepCtl *c, const double *phiP, const double *phiL, double *phi, int ng) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng || c->halt) return;
+    phi[k] = phiP[k] + c->circ_V * phiL[k];
 }
 
 // host values the device's step control starts from
@@ -439,6 +490,14 @@ void setup_device(pic_handle *h) {
     for (int k = 0; k < 5; ++k) h->m_acc[k] = (double *)dalloc(h, gb);
     h->E2 = dalloc(h, (size_t)h->ng * 2 * ts);
     h->phiL_d = (double *)dalloc(h, (size_t)h->nr * sizeof(double));
+    if (h->cfg.circuit_C > 0.0) {
+        h->phi_P = (double *)dalloc(h, gb);
+        h->phi_L = (double *)dalloc(h, gb);
+        h->zero_grid = (double *)dalloc(h, gb);
+        cudaMemsetAsync(h->phi_P, 0, gb, h->st);
+        cudaMemsetAsync(h->phi_L, 0, gb, h->st);
+        cudaMemsetAsync(h->zero_grid, 0, gb, h->st);
+    }
     h->eedf = (double *)dalloc(h, (size_t)std::max(1, h->cfg.eedf_bins) * sizeof(double));
     for (int s = 0; s < 2; ++s) cudaMemsetAsync(h->N[s], 0, gb, h->st);
     cudaMemsetAsync(h->phi, 0, gb, h->st);
@@ -630,8 +689,22 @@ void one_step(pic_handle *h) {
                         h->rho, h->chi, h->ng, h->sctl, st);
         FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
         int L = 0;
-        mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi, true,
-                      h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st);
+        if (h->cfg.circuit_C > 0.0) {
+            // phi_P: the plasma's charge, electrode at 0; phi_L: no charge,
+            // electrode at 1, every other boundary at 0; same operator
+            mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi_P,
+                          true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st,
+                          false, true);
+            mg_fast_solve(fd, h->mgf, h->zero_grid, h->chi, 1.0, nullptr, h->phi_L, true, h->mixed,
+                          h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, false, false);
+            k_circuit<<<1, 256, 0, st>>>(h->sctl, h->ds, h->mgf.cz[0], h->phi_P, h->phi_L, h->rho, h->V,
+                                         h->nr, h->cfg.circuit_C);
+            k_superpose<<<(h->ng + 255) / 256, 256, 0, st>>>(h->sctl, h->phi_P, h->phi_L, h->phi, h->ng);
+            L += 2;
+        } else {
+            mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi,
+                          true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st);
+        }
         launch_efield<T>(h->phi, h->Ez, h->Er, (typename V2<T>::type *)h->E2, h->nz, h->nr, h->dz,
                          h->dr, h->sctl, st);
         h->launches += L + 3;
@@ -1339,13 +1412,25 @@ pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64
     return cuda_check(h, "get_counts");
 }
 
+pic_status pic_get_circuit(pic_handle *h, double *out) {
+    if (!h || !out) return PIC_ERR_ARG;
+    StepCtl c;
+    cudaMemcpyAsync(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    out[0] = c.circ_V;
+    out[1] = c.circ_Q;
+    out[2] = c.circ_Qc;
+    return cuda_check(h, "get_circuit");
+}
+
 static const uint64_t kCkptMagic = 0x50494352475a3031ull;  // "PICRGZ01"
 
 pic_status pic_save(pic_handle *h, const char *path) {
     if (!h || !path) return PIC_ERR_ARG;
     FILE *f = fopen(path, "wb");
     if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint for writing");
-    int64_t hdr[8] = {(int64_t)kCkptMagic, h->nz, h->nr, h->step, h->mixed ? 1 : 0, 0, 0, 0};
+    const int circuit = h->cfg.circuit_C > 0.0 ? 1 : 0;
+    int64_t hdr[8] = {(int64_t)kCkptMagic, h->nz, h->nr, h->step, h->mixed ? 1 : 0, circuit, 0, 0};
     uint64_t ids[2] = {h->sp[0].next_id, h->sp[1].next_id};
     fwrite(hdr, sizeof(hdr), 1, f);
     fwrite(ids, sizeof(ids), 1, f);
@@ -1379,6 +1464,18 @@ pic_status pic_save(pic_handle *h, const char *path) {
         fwrite(a.data(), 8, (size_t)n * 8, f);
         fwrite(id.data(), 8, (size_t)n, f);
     }
+    if (circuit && st == PIC_OK) {
+        // circuit state, the charge collected since the last circuit solve,
+        // and the two superposition parts (the next solves start from them)
+        double cs[6];
+        pic_get_circuit(h, cs);
+        cudaMemcpy(cs + 3, h->ds->qstep, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+        fwrite(cs, 8, 6, f);
+        for (double *src : {h->phi_P, h->phi_L}) {
+            cudaMemcpy(g.data(), src, g.size() * 8, cudaMemcpyDeviceToHost);
+            fwrite(g.data(), 8, g.size(), f);
+        }
+    }
     fclose(f);
     return st;
 }
@@ -1389,8 +1486,9 @@ pic_status pic_load(pic_handle *h, const char *path) {
     if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint");
     int64_t hdr[8];
     uint64_t ids[2];
+    const int circuit = h->cfg.circuit_C > 0.0 ? 1 : 0;
     if (fread(hdr, sizeof(hdr), 1, f) != 1 || (uint64_t)hdr[0] != kCkptMagic || hdr[1] != h->nz ||
-        hdr[2] != h->nr || fread(ids, sizeof(ids), 1, f) != 1) {
+        hdr[2] != h->nr || hdr[5] != circuit || fread(ids, sizeof(ids), 1, f) != 1) {
         fclose(f);
         return fail(h, PIC_ERR_ARG, "checkpoint does not match this handle");
     }
@@ -1424,8 +1522,28 @@ pic_status pic_load(pic_handle *h, const char *path) {
         v.cell = nullptr;
         st = pic_set_particles(h, s, &v);
     }
+    double cs[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<double> gP, gL;
+    if (circuit && st == PIC_OK) {
+        gP.resize((size_t)h->ng);
+        gL.resize((size_t)h->ng);
+        if (fread(cs, 8, 6, f) != 6 || fread(gP.data(), 8, gP.size(), f) != gP.size() ||
+            fread(gL.data(), 8, gL.size(), f) != gL.size())
+            st = fail(h, PIC_ERR_ARG, "truncated checkpoint");
+    }
     fclose(f);
     if (st != PIC_OK) return st;
+    if (circuit) {
+        StepCtl c;
+        cudaMemcpy(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost);
+        c.circ_V = cs[0];
+        c.circ_Q = cs[1];
+        c.circ_Qc = cs[2];
+        cudaMemcpy(h->sctl, &c, sizeof(StepCtl), cudaMemcpyHostToDevice);
+        cudaMemcpy(h->ds->qstep, cs + 3, 3 * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(h->phi_P, gP.data(), gP.size() * 8, cudaMemcpyHostToDevice);
+        cudaMemcpy(h->phi_L, gL.data(), gL.size() * 8, cudaMemcpyHostToDevice);
+    }
     h->step = hdr[3];
     h->sp[0].next_id = ids[0];
     h->sp[1].next_id = ids[1];

@@ -46,6 +46,7 @@ struct StepCtl {
     double mg_last_res;   // relative residual of the last solve
     unsigned int bar;     // barrier counter of the births numbering
     int32_t bar_timeout;  // a bounded wait of the births numbering gave up
+    double circ_V, circ_Q, circ_Qc;  // external circuit: electrode voltage and charge, capacitor charge
 };
 
 // ---- grid barrier of cooperative launches ----
@@ -134,6 +135,7 @@ struct DevScalars {
     int32_t pad;
     unsigned long long cnt[PIC_NCOUNT];
     double qabs[3];
+    double qstep[3];  // absorbed charge per wall since the circuit last took it
     unsigned long long mg_res_bits;  // max |residual| of the last residual kernel
     unsigned long long mg_aux_bits;
 };

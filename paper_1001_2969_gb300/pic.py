@@ -65,7 +65,7 @@ class pic_config(C.Structure):
                 ("mg_tol", C.c_double), ("phi_zL", _dp), ("births_capacity", C.c_int64),
                 ("eedf_bins", C.c_int32), ("eedf_emax_eV", C.c_double), ("load", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("circuit_C", C.c_double)]
 
 
 class pic_particles_view(C.Structure):
@@ -87,7 +87,7 @@ SYMBOLS = ("pic_init", "pic_step", "pic_field_solve", "pic_moments", "pic_get_pa
            "pic_set_particles", "pic_set_step", "pic_set_boundary", "pic_get_fields",
            "pic_get_counts", "pic_save", "pic_load", "pic_profile", "pic_timings", "pic_destroy",
            "pic_last_error", "pic_status_string", "pic_field_solve_noalloc", "pic_batch_init",
-           "pic_batch_step", "pic_batch_destroy", "pic_tune")
+           "pic_batch_step", "pic_batch_destroy", "pic_tune", "pic_get_circuit")
 
 
 class PicError(RuntimeError):
@@ -114,6 +114,7 @@ def lib():
         L.pic_batch_destroy.argtypes = [vp]
         L.pic_batch_destroy.restype = None
         L.pic_tune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.pic_get_circuit.argtypes = [vp, _dp]
         L.pic_field_solve.argtypes = [vp, vp, vp, C.c_double, vp, C.c_int32,
                                       C.POINTER(pic_solve_info)]
         L.pic_moments.argtypes = [vp, C.POINTER(pic_moments_out), C.c_int32]
@@ -243,6 +244,7 @@ def pic_init(cfg: dict, load: bool = True, stream=None, torch_memory: bool = Tru
             keep += [a, f]
             c.alloc, c.free = a, f
     c.stream = stream
+    c.circuit_C = float(cfg.get("circuit_C", 0.0))
     ptr = C.c_void_p()
     st = L.pic_init(C.byref(c), C.byref(ptr))
     if st != PIC_OK:
@@ -283,6 +285,13 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def pic_get_circuit(h: Handle):
+    """(electrode voltage, electrode charge, capacitor charge) after the last step."""
+    out = np.zeros(3)
+    _check(h, lib().pic_get_circuit(h.ptr, _p(out)))
+    return tuple(out)
 
 
 def pic_tune(h: Handle, steps_per_variant: int = 2, variants=None):
