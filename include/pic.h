@@ -214,7 +214,7 @@ pic_status pic_batch_init(pic_handle *const *handles, int32_t n, void *stream, p
  * pic_tune -- choose the particle pass's shape per species (no counterpart
  * in the paper).  Shapes: 0 direct loads, 1 the chunk's particles prefetched
  * into shared memory (cp.async), 2 and 3 the same with 8 instead of 4
- * particles per thread; -1 the default (electrons 0, ions 1).  With
+ * particles per thread; -1 the default (electrons 2, ions 1).  With
  * steps_per_variant > 0 every shape runs that many real steps of this
  * reactor (the simulation advances) with CUDA events around each species'
  * pass, the fastest per species is kept and, if variants is not NULL,

@@ -365,33 +365,50 @@ __device__ void emit_birth(const StepArgs<T> &a, BlockTally *bt, int ts, int ps,
     a.bkey[ts][slot] = ((uint64_t)ps << 63) | (pid << 16) | (uint64_t)k;
 }
 
-// null-collision Monte Carlo (Sec. 2.6) on the post-final-push state
+// Null-collision Monte Carlo (Sec. 2.6) on the post-final-push state, in
+// three parts: the relative velocity against the target, the channel of a
+// candidate, and the collision itself.
 template <typename T>
-__device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, uint64_t id, uint32_t step,
-                                        PS<T> &p) {
-    const uint4 x = draw(a.key0, a.key1, id, step, 0, a.s);
-    if ((unsigned long long)x.x >= a.t_null) return;
-    atomicAdd(&bt->cnt[PIC_C_CAND + a.s], 1ull);
-    T gx = p.vr, gy = p.vt, gz = p.vz;
-    T vnx = 0, vny = 0, vnz = 0;
+struct Rel {
+    T gx, gy, gz;     // velocity relative to the target
+    T vnx, vny, vnz;  // the target atom's velocity (ions)
+    T g, E;           // relative speed, collision energy
+};
+
+// electrons: the gas at rest; ions: an atom drawn from the gas Maxwellian
+template <typename T>
+__device__ __forceinline__ Rel<T> relative(const StepArgs<T> &a, uint64_t id, uint32_t step, const PS<T> &p) {
+    Rel<T> r;
+    r.gx = p.vr;
+    r.gy = p.vt;
+    r.gz = p.vz;
+    r.vnx = r.vny = r.vnz = 0;
     if (a.s == 1) {
         const uint4 y = draw(a.key0, a.key1, id, step, 1, a.s);
         T n0, n1, n2, n3;
         normals(y.x, y.y, n0, n1);
         normals(y.z, y.w, n2, n3);
-        vnx = a.v_gas * n0;
-        vny = a.v_gas * n1;
-        vnz = a.v_gas * n2;
-        gx = p.vr - vnx;
-        gy = p.vt - vny;
-        gz = p.vz - vnz;
+        r.vnx = a.v_gas * n0;
+        r.vny = a.v_gas * n1;
+        r.vnz = a.v_gas * n2;
+        r.gx = p.vr - r.vnx;
+        r.gy = p.vt - r.vny;
+        r.gz = p.vz - r.vnz;
     }
-    const T g = m_sqrt(gx * gx + gy * gy + gz * gz);
-    const T E = a.half_m_e * g * g;
+    r.g = m_sqrt(r.gx * r.gx + r.gy * r.gy + r.gz * r.gz);
+    r.E = a.half_m_e * r.g * r.g;
+    return r;
+}
+
+// channel of a candidate whose stream-0 draw is x: -1 for a null collision
+// (also an inelastic channel picked below its threshold); counts nu_max
+// overruns and real collisions
+template <typename T>
+__device__ __forceinline__ int choose(const StepArgs<T> &a, BlockTally *bt, const uint4 x, const Rel<T> &r) {
     T nu[kMaxCh];
-    sigma_all(a.xs, E, nu);
+    sigma_all(a.xs, r.E, nu);
     T tot = 0;
-    const T ngg = a.ng * g;
+    const T ngg = a.ng * r.g;
 #pragma unroll
     for (int ch = 0; ch < kMaxCh; ++ch) {
         nu[ch] = ch < a.xs.n_ch ? ngg * nu[ch] : (T)0;
@@ -408,18 +425,28 @@ __device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, ui
             if (sel < cum) ch = k;
         }
     }
-    if (ch < 0) return;
+    if (ch < 0) return -1;
+    const int kind = a.xs.kind[ch];
+    if ((kind == PIC_XS_EXCITE || kind == PIC_XS_IONIZE) && r.E <= a.xs.thr[ch]) return -1;
+    atomicAdd(&bt->cnt[PIC_C_COLL + a.s * 4 + ch], 1ull);
+    return ch;
+}
+
+// the collision on channel ch (Vahedi-Surendra scattering, ionisation
+// births, charge exchange)
+template <typename T>
+__device__ __forceinline__ void scatter(const StepArgs<T> &a, BlockTally *bt, uint64_t id, uint32_t step,
+                                        const uint4 x, int ch, const Rel<T> &r, PS<T> &p) {
     const int kind = a.xs.kind[ch];
     const T thr = a.xs.thr[ch];
-    if ((kind == PIC_XS_EXCITE || kind == PIC_XS_IONIZE) && E <= thr) return;
-    atomicAdd(&bt->cnt[PIC_C_COLL + a.s * 4 + ch], 1ull);
+    const T g = r.g, E = r.E;
     if (kind == PIC_XS_CX) {
-        p.vr = vnx;
-        p.vt = vny;
-        p.vz = vnz;
+        p.vr = r.vnx;
+        p.vt = r.vny;
+        p.vz = r.vnz;
         return;
     }
-    const T ux = gx / g, uy = gy / g, uz = gz / g;
+    const T ux = r.gx / g, uy = r.gy / g, uz = r.gz / g;
     T dx, dy, dz;
     if (kind == PIC_XS_ELASTIC) {
         const T cc = cos_chi(a.scatter, E, unif<T>(x.z));
@@ -469,6 +496,18 @@ __device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, ui
     }
 }
 
+// the whole Monte Carlo step of one particle
+template <typename T>
+__device__ __forceinline__ void collide(const StepArgs<T> &a, BlockTally *bt, uint64_t id, uint32_t step,
+                                        PS<T> &p) {
+    const uint4 x = draw(a.key0, a.key1, id, step, 0, a.s);
+    if ((unsigned long long)x.x >= a.t_null) return;
+    atomicAdd(&bt->cnt[PIC_C_CAND + a.s], 1ull);
+    const Rel<T> r = relative(a, id, step, p);
+    const int ch = choose(a, bt, x, r);
+    if (ch >= 0) scatter(a, bt, id, step, x, ch, r, p);
+}
+
 // cp.async of 4, 8 or 16 bytes (global -> shared; both ends aligned to the size)
 __device__ __forceinline__ void cpa16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
@@ -492,37 +531,29 @@ constexpr int kThreads = 256;
 // shared-memory atomics of a warp are serialised
 constexpr int kEedfCopies = 8;
 
-constexpr int kHalo = 3;
-// deposit window of a block: smaller with the prefetch staging beside it
-template <bool PF>
-__host__ __device__ constexpr int win_bytes() {
-    return PF ? 8192 : 16384;
-}
-
 // The fused particle pass (Sec. 2.1 merged cycle).  Each block walks chunks
-// of kChunk particles of the cell-sorted input; chunk positions are close
-// in space, so the deposit goes to a shared-memory window around the
-// chunk's cells and is flushed with one global atomic per touched node.
+// of kChunk particles of the cell-sorted input.  Lanes of a warp hold
+// consecutive particles, so their output cells come in runs; each run's
+// deposit is summed across its lanes and its first lane adds it to the four
+// nodes with global reductions (fire-and-forget, resolved in L2).  A
+// shared-memory window of the chunk's nodes needs atomics that conflict
+// between runs and warps and costs more instructions than it saves.
 // PF: the chunk's particles come into shared memory by cp.async a chunk at
-// a time (latency-bound passes gain; passes bound by issue and shared-memory
-// traffic, like the electrons' with their collisions, lose)
+// a time, ahead of their use (for latency-bound passes)
 // PPT: particles per thread in a chunk (kThreads * PPT particles)
 template <typename T, bool PF, int kPPT>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepArgs<T> a) {
     constexpr int kChunk = kThreads * kPPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = typename V4<T>::type;
-    constexpr int kWinBytes = win_bytes<PF>();
-    T *win = reinterpret_cast<T *>(smem_raw);
     // the chunk's particles, fetched into shared memory ahead of their use
     // (PF): [kPPT][kThreads] of q0, q1, id, cell
-    V *st_q0 = reinterpret_cast<V *>(smem_raw + kWinBytes);
+    V *st_q0 = reinterpret_cast<V *>(smem_raw);
     V *st_q1 = st_q0 + kChunk;
     uint64_t *st_id = reinterpret_cast<uint64_t *>(st_q1 + kChunk);
     int32_t *st_cell = reinterpret_cast<int32_t *>(st_id + kChunk);
-    T *s_eedf = PF ? reinterpret_cast<T *>(st_cell + kChunk) : reinterpret_cast<T *>(smem_raw + kWinBytes);
+    T *s_eedf = PF ? reinterpret_cast<T *>(st_cell + kChunk) : reinterpret_cast<T *>(smem_raw);
     __shared__ BlockTally bt;
-    __shared__ int s_w[4];
     const int tid = threadIdx.x, lane = tid & 31;
     if (a.ctl->halt) return;  // an earlier failure of this step
     const uint32_t step = (uint32_t)a.ctl->step;  // Philox counter word
@@ -531,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     if (tid < 3) bt.q[tid] = 0.0;
     if (a.eedf)
         for (int k = tid; k < a.eedf_bins * kEedfCopies; k += blockDim.x) s_eedf[k] = (T)0;
-    const int WCAP = kWinBytes / (int)sizeof(T);
+    __syncthreads();  // tallies and EEDF cleared before any thread adds to them
     const int n = *a.n_alive;
     const int nmain = *a.n_main_src;
     const int nchunks = (n + kChunk - 1) / kChunk;
@@ -547,28 +578,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     for (int ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
         const int base = ck * kChunk;
         const int end = min(base + kChunk, n);
-        __syncthreads();
-        // request the chunk's particles, then read the next chunk's perm entries
+        // request the chunk's particles, then read the next chunk's perm
+        // entries; a thread fills and reads only its own slots, so chunks
+        // need no barrier
         if (PF) {
 #pragma unroll
-        for (int m = 0; m < kPPT; ++m) {
-            const int k = base + m * kThreads + tid;
-            if (k < end) {
-                const int pidx = pn[m];
-                const bool from_main = pidx < nmain;
-                const PBuf<T> &src = from_main ? a.src_main : a.src_births;
-                const int si = from_main ? pidx : pidx - nmain;
-                const int slot = m * kThreads + tid;
-                for (int h = 0; h < (int)(sizeof(V) / 16); ++h) {
-                    cpa16(reinterpret_cast<char *>(st_q0 + slot) + 16 * h, reinterpret_cast<const char *>(src.q0 + si) + 16 * h);
-                    cpa16(reinterpret_cast<char *>(st_q1 + slot) + 16 * h, reinterpret_cast<const char *>(src.q1 + si) + 16 * h);
+            for (int m = 0; m < kPPT; ++m) {
+                const int k = base + m * kThreads + tid;
+                if (k < end) {
+                    const int pidx = pn[m];
+                    const bool from_main = pidx < nmain;
+                    const PBuf<T> &src = from_main ? a.src_main : a.src_births;
+                    const int si = from_main ? pidx : pidx - nmain;
+                    const int slot = m * kThreads + tid;
+                    for (int h = 0; h < (int)(sizeof(V) / 16); ++h) {
+                        cpa16(reinterpret_cast<char *>(st_q0 + slot) + 16 * h,
+                              reinterpret_cast<const char *>(src.q0 + si) + 16 * h);
+                        cpa16(reinterpret_cast<char *>(st_q1 + slot) + 16 * h,
+                              reinterpret_cast<const char *>(src.q1 + si) + 16 * h);
+                    }
+                    cpa8(st_id + slot, src.id + si);
+                    cpa4(st_cell + slot, src.cell + si);
                 }
-                cpa8(st_id + slot, src.id + si);
-                cpa4(st_cell + slot, src.cell + si);
             }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        {
+            asm volatile("cp.async.commit_group;" ::: "memory");
             const int nb = (ck + gridDim.x) * kChunk;
 #pragma unroll
             for (int m = 0; m < kPPT; ++m) {
@@ -576,34 +609,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                 pn[m] = k < n ? a.perm[k] : 0;
             }
         }
-        }
-        if (tid == 0) {
-            const int pa = a.perm[base], pb = a.perm[end - 1];
-            const int ca = pa < nmain ? a.src_main.cell[pa] : a.src_births.cell[pa - nmain];
-            const int cb = pb < nmain ? a.src_main.cell[pb] : a.src_births.cell[pb - nmain];
-            int ia, ja, ib, jb;
-            decode_cell(ca, a.ncz, a.inv_ncz, ia, ja);
-            decode_cell(cb, a.ncz, a.inv_ncz, ib, jb);
-            int ilo = 0, ihi = a.ncz - 1;
-            if (ja == jb) {
-                ilo = ia;
-                ihi = ib;
-            }
-            const int wi0 = max(ilo - kHalo, 0), wi1 = min(ihi + 1 + kHalo, a.nz - 1);
-            const int wj0 = max(ja - kHalo, 0), wj1 = min(jb + 1 + kHalo, a.nr - 1);
-            int wz = wi1 - wi0 + 1, wr = wj1 - wj0 + 1;
-            if (wz * wr > WCAP) wz = 0;
-            s_w[0] = wi0;
-            s_w[1] = wj0;
-            s_w[2] = wz;
-            s_w[3] = wr;
-        }
-        __syncthreads();
-        const int wi0 = s_w[0], wj0 = s_w[1], wz = s_w[2], wr = s_w[3];
-        for (int k = tid; k < wz * wr; k += blockDim.x) win[k] = (T)0;
         // each thread reads back only the slots it requested itself
         if (PF) asm volatile("cp.async.wait_group 0;" ::: "memory");
-        __syncthreads();
 #pragma unroll 1
         for (int m = 0; m < kPPT; ++m) {
             const int k = base + m * kThreads + tid;
@@ -721,9 +728,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                 }
                 store_p(a.dst_main, k, p, out_cell, id);
             }
-            // Lanes hold consecutive particles of the cell-sorted input, so runs
-            // of lanes share an output cell: sum each run into its first lane,
-            // which then makes the four deposit atomics and the histogram count.
+            // runs of lanes with one output cell: sum each run into its first
+            // lane, which makes the four deposit reductions and the histogram count
             const int cprev = __shfl_up_sync(0xffffffffu, out_cell, 1);
             const bool head = lane == 0 || cprev != out_cell;
             const unsigned heads = __ballot_sync(0xffffffffu, head);
@@ -746,28 +752,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                 atomicAdd(a.counts[a.s] + out_cell, rend - lane);
                 int ci, cj;
                 decode_cell(out_cell, a.ncz, a.inv_ncz, ci, cj);
-                const int li = ci - wi0, lj = cj - wj0;
-                if (li >= 0 && li + 1 < wz && lj >= 0 && lj + 1 < wr) {
-                    T *wp = win + li * wr + lj;
-                    atomicAdd(wp, c00);
-                    atomicAdd(wp + 1, c01);
-                    atomicAdd(wp + wr, c10);
-                    atomicAdd(wp + wr + 1, c11);
-                } else {
-                    double *g = a.N[a.s] + (size_t)ci * a.nr + cj;
-                    atomicAdd(g, (double)c00);
-                    atomicAdd(g + 1, (double)c01);
-                    atomicAdd(g + a.nr, (double)c10);
-                    atomicAdd(g + a.nr + 1, (double)c11);
-                }
-            }
-        }
-        __syncthreads();
-        for (int k = tid; k < wz * wr; k += blockDim.x) {
-            const T v = win[k];
-            if (v != (T)0) {
-                const int gi = wi0 + k / wr, gj = wj0 + k % wr;
-                atomicAdd(a.N[a.s] + (size_t)gi * a.nr + gj, (double)v);
+                double *g = a.N[a.s] + (size_t)ci * a.nr + cj;
+                atomicAdd(g, (double)c00);
+                atomicAdd(g + 1, (double)c01);
+                atomicAdd(g + a.nr, (double)c10);
+                atomicAdd(g + a.nr + 1, (double)c11);
             }
         }
     }
@@ -791,19 +780,20 @@ void launch_variant(const StepArgs<T> &a, int grid, cudaStream_t st) {
     const size_t stage =
         PF ? (size_t)kThreads * PPT * (2 * sizeof(typename V4<T>::type) + sizeof(uint64_t) + sizeof(int32_t)) : 0;
     const size_t eedf = (size_t)(a.eedf ? a.eedf_bins : 0) * kEedfCopies * sizeof(T);
-    const size_t smem = win_bytes<PF>() + stage + eedf;
+    const size_t smem = stage + eedf;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_step<T, PF, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_step<T, PF, PPT><<<grid, kThreads, smem, st>>>(a);
 }
 
 // variant: bit 0 = prefetch the chunk into shared memory, bit 1 = 8
-// particles per thread (else 4); -1 = the default for the species (ions
-// prefetch: their pass is latency-bound; electrons do not: theirs is bound
-// by issue and shared-memory traffic)
+// particles per thread (else 4); -1 = the default for the species, the
+// faster shape on GB300 at 1e7 particles per species: ions prefetch 4 per
+// thread (their pass is latency-bound), electrons load directly, 8 per
+// thread (theirs is bound by issue)
 template <typename T>
 void launch_step(const StepArgs<T> &a, int grid, int variant, cudaStream_t st) {
-    const int v = variant >= 0 ? (variant & 3) : (a.s == 1 ? 1 : 0);
+    const int v = variant >= 0 ? (variant & 3) : (a.s == 1 ? 1 : 2);
     switch (v) {
         case 0: launch_variant<T, false, 4>(a, grid, st); break;
         case 1: launch_variant<T, true, 4>(a, grid, st); break;
