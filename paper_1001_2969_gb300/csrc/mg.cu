@@ -929,7 +929,7 @@ void mg_fast_upload(MGFast &m, cudaStream_t st) {
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
-                  bool v_from_ctl, bool setup) {
+                  bool v_from_ctl, bool setup, cudaEvent_t at_solve) {
     const int nz = fd.nz, nr = fd.nr, n = nr - 1, ng = nz * nr;
     const int M = line_chunk(n);
     const int nlev = m.nlev;
@@ -1005,6 +1005,7 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     int per_sm = 0;
     if (sp <= kSolveSmemLimit) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSolveThreads, sp);
     if (per_sm < 1) {
+        if (at_solve) cudaEventRecord(at_solve, st);
         if (launches) *launches += L;
         return kSolveNoLaunch;
     }
@@ -1014,7 +1015,28 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     const StepCtl *sc = sctl;
     void *args[] = {(void *)&mp, (void *)&phi, (void *)&nrv, (void *)&first_cycle, (void *)&lay,
                     (void *)&tv, (void *)&mc, (void *)&sc};
-    const cudaError_t e = cudaLaunchCooperativeKernel(fn, grid, kSolveThreads, args, sp, st);
+    // the highest stream priority: when a step sorts beside the solve, the
+    // solve's blocks take SMs as soon as the sort's short blocks retire
+    static int prio = 1;
+    if (prio > 0) {
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        prio = greatest;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kSolveThreads);
+    lc.dynamicSmemBytes = sp;
+    lc.stream = st;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributePriority;
+    at[1].val.priority = prio;
+    lc.attrs = at;
+    lc.numAttrs = 2;
+    if (at_solve) cudaEventRecord(at_solve, st);
+    const cudaError_t e = cudaLaunchKernelExC(&lc, fn, args);
     ++L;
     if (e != cudaSuccess) {
         if (launches) *launches += L;

@@ -100,8 +100,11 @@ struct pic_handle {
     int variant[2] = {-1, -1};  // particle-pass shape per species (-1: default)
     cudaStream_t user_st = nullptr;  // the caller's stream
     cudaStream_t gst = nullptr;      // private stream the step graphs are captured on and run on
+    cudaStream_t gst2 = nullptr;     // the step graph's second branch (the previous pass's cell sort)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     StepGraph graphs[2];
+    StepGraph sort_graphs[2];  // the last pass's cell sort at the end of a call
     double ngas = 0.0, nu_max[2] = {0, 0}, p_null[2] = {0, 0};
     unsigned long long t_null[2] = {0, 0};
     std::string err;
@@ -294,13 +297,24 @@ __global__ void k_step_begin(StepCtl *c, const double *rf, int nrf, double dt, i
     c->do_split = split_every > 0 && (c->step % split_every) == split_every - 1;
 }
 
-// step epilogue: the new particle counts take effect and the step advances
-__global__ void k_step_end(StepCtl *c, int32_t *nalive0, const int32_t *ntotal0, int32_t *nalive1,
-                           const int32_t *ntotal1) {
+// step epilogue: the pass wrote *nalive entries into the destination main
+// buffers; their cell sort is pending, and the step advances
+__global__ void k_step_end(StepCtl *c, int32_t *nmain0, const int32_t *nalive0, int32_t *nmain1,
+                           const int32_t *nalive1) {
     if (c->halt) return;
+    *nmain0 = *nalive0;
+    *nmain1 = *nalive1;
+    c->sort_pending = 1;
+    c->step += 1;
+}
+
+// sort epilogue: the sorted counts take effect for the next pass
+__global__ void k_sort_end(StepCtl *c, int32_t *nalive0, const int32_t *ntotal0, int32_t *nalive1,
+                           const int32_t *ntotal1) {
+    if (sort_skip(c)) return;
     *nalive0 = *ntotal0;
     *nalive1 = *ntotal1;
-    c->step += 1;
+    c->sort_pending = 0;
 }
 
 // External circuit (Sec. 2.5, end), Vahedi's superposition: the charge on
@@ -676,13 +690,60 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
 // Enqueues one timestep (Sec. 2.1 merged cycle) without a host
 // synchronisation; failures halt the step on the device (StepCtl) and are
 // resolved by pic_step after the last step of the call.
+// The cell sort of the last pass, whose output is the buffer set `par`
+// (Sec. 2.7; a GPU necessity here): per species an exclusive scan of the
+// pass's cell counts, the capacity check, the rank into the permutation the
+// next pass reads through.  Regular kernels only, so it can run beside the
+// cooperative field solve.
 template <typename T>
-void one_step(pic_handle *h) {
+void sort_branch(pic_handle *h, int par, cudaStream_t st) {
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, h->sctl, st);
+    }
+    // capacity and births overflow: the sort fails before any permutation changes
+    launch_step_check(h->ds, h->sctl, st);
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        launch_rank<T>(view<T>(d.main[par]), d.d_nmain[par], view<T>(d.births[par]), d.d_nbirths[par],
+                       d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->sctl, st);
+    }
+    h->launches += 9;
+}
+
+// the rest of the sort: newborn numbering (a cooperative launch, after the
+// field solve's), then the sorted counts take effect
+void sort_finish(pic_handle *h, int par, cudaStream_t st) {
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        launch_birth_ids(d.bkey[par], d.births[par].id, d.d_nbirths[par], h->sctl, s, h->rtmp, st);
+    }
+    k_sort_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nalive, h->sp[0].d_ntotal, h->sp[1].d_nalive,
+                                 h->sp[1].d_ntotal);
+    h->launches += 3;
+}
+
+// Enqueue one timestep (Sec. 2.1, merged cycle) on h->st: the field at the
+// new time (finalize, solve, E) beside the previous pass's cell sort (on
+// sb, forked and joined; in order on h->st when sb is null), then the
+// particle passes, the time averages and the step's end.  The pass's own
+// sort is left pending for the next step or the end of the call.
+template <typename T>
+void one_step(pic_handle *h, cudaStream_t sb) {
     cudaStream_t st = h->st;
     const int src = h->cur, dst = 1 - h->cur;
+    k_step_begin<<<1, 1, 0, st>>>(h->sctl, h->rf_d, h->cfg.rf.n, h->cfg.dt, h->cfg.split_every);
+    h->launches += 1;
+    if (!sb) {
+        PhaseTimer t(h, 3);
+        sort_branch<T>(h, src, st);
+    }
+    // with a second branch, the sort forks off right before the one-launch
+    // solve (after its set-up): the solve, at the highest priority, takes
+    // its SMs first and the sort's blocks fill the rest of the machine
+    cudaEvent_t fork = sb ? h->ev_fork : nullptr;
     {
         PhaseTimer t(h, 0);
-        k_step_begin<<<1, 1, 0, st>>>(h->sctl, h->rf_d, h->cfg.rf.n, h->cfg.dt, h->cfg.split_every);
         launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q,
                         h->cfg.sp[0].q * h->cfg.sp[0].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[0].m),
                         h->cfg.sp[1].q * h->cfg.sp[1].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[1].m),
@@ -694,7 +755,7 @@ void one_step(pic_handle *h) {
             // electrode at 1, every other boundary at 0; same operator
             mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi_P,
                           true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st,
-                          false, true);
+                          false, true, fork);
             mg_fast_solve(fd, h->mgf, h->zero_grid, h->chi, 1.0, nullptr, h->phi_L, true, h->mixed,
                           h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, false, false);
             k_circuit<<<1, 256, 0, st>>>(h->sctl, h->ds, h->mgf.cz[0], h->phi_P, h->phi_L, h->rho, h->V,
@@ -703,11 +764,22 @@ void one_step(pic_handle *h) {
             L += 2;
         } else {
             mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi,
-                          true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st);
+                          true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, true,
+                          true, fork);
+        }
+        if (sb) {
+            cudaStreamWaitEvent(sb, h->ev_fork, 0);
+            sort_branch<T>(h, src, sb);
+            cudaEventRecord(h->ev_join, sb);
         }
         launch_efield<T>(h->phi, h->Ez, h->Er, (typename V2<T>::type *)h->E2, h->nz, h->nr, h->dz,
                          h->dr, h->sctl, st);
-        h->launches += L + 3;
+        h->launches += L + 2;
+    }
+    if (sb) cudaStreamWaitEvent(st, h->ev_join, 0);
+    {
+        PhaseTimer t(h, 3);
+        sort_finish(h, src, st);
     }
     for (int s = 0; s < 2; ++s) {
         cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), st);
@@ -724,52 +796,40 @@ void one_step(pic_handle *h) {
         h->particle_launches += 1;
     }
     {
-        PhaseTimer t(h, 3);
-        for (int s = 0; s < 2; ++s) {
-            SpecDev &d = h->sp[s];
-            // entries the pass wrote into the destination main buffer
-            cudaMemcpyAsync(d.d_nmain[dst], d.d_nalive, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-            launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, h->sctl, st);
-            h->launches += 3;
-        }
-        // capacity and births overflow: the step halts before any permutation changes
-        launch_step_check(h->ds, h->sctl, st);
-        for (int s = 0; s < 2; ++s) {
-            SpecDev &d = h->sp[s];
-            launch_rank<T>(view<T>(d.main[dst]), d.d_nmain[dst], view<T>(d.births[dst]),
-                           d.d_nbirths[dst], d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->sctl, st);
-        }
-        for (int s = 0; s < 2; ++s) {
-            SpecDev &d = h->sp[s];
-            launch_birth_ids(d.bkey[dst], d.births[dst].id, d.d_nbirths[dst], h->sctl, s, h->rtmp, st);
-        }
-        h->launches += 5;
-    }
-    {
         PhaseTimer t(h, 4);
         launch_moments(h->N[0], h->N[1], h->V, h->phi, h->Ez, h->Er, h->m_acc[0], h->m_acc[1],
                        h->m_acc[2], h->m_acc[3], h->m_acc[4], h->ng, h->sctl, st);
-        k_step_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nalive, h->sp[0].d_ntotal, h->sp[1].d_nalive,
-                                     h->sp[1].d_ntotal);
+        k_step_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nmain[dst], h->sp[0].d_nalive, h->sp[1].d_nmain[dst],
+                                     h->sp[1].d_nalive);
         h->launches += 2;
     }
     h->cur = dst;
 }
 
+// the pending sort of the last pass (end of a call), on h->st
+template <typename T>
+void sort_tail(pic_handle *h) {
+    PhaseTimer t(h, 3);
+    sort_branch<T>(h, h->cur, h->st);
+    sort_finish(h, h->cur, h->st);
+}
+
 void drop_graphs(pic_handle *h) {
-    for (auto &g : h->graphs) {
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        g = StepGraph();
-    }
+    for (StepGraph *gs : {h->graphs, h->sort_graphs})
+        for (int k = 0; k < 2; ++k) {
+            if (gs[k].exec) cudaGraphExecDestroy(gs[k].exec);
+            gs[k] = StepGraph();
+        }
 }
 
 void destroy_streams(pic_handle *h) {
     drop_graphs(h);
-    if (h->ev_in) cudaEventDestroy(h->ev_in);
-    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    for (cudaEvent_t e : {h->ev_in, h->ev_out, h->ev_fork, h->ev_join})
+        if (e) cudaEventDestroy(e);
     if (h->gst) cudaStreamDestroy(h->gst);
-    h->ev_in = h->ev_out = nullptr;
-    h->gst = nullptr;
+    if (h->gst2) cudaStreamDestroy(h->gst2);
+    h->ev_in = h->ev_out = h->ev_fork = h->ev_join = nullptr;
+    h->gst = h->gst2 = nullptr;
 }
 
 // capture one step (from the current parity) on the private stream
@@ -782,7 +842,7 @@ void capture_step(pic_handle *h, StepGraph &g) {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        one_step<T>(h);
+        one_step<T>(h, h->gst2);
         e = cudaStreamEndCapture(h->gst, &graph);
     }
     h->st = keep;
@@ -797,6 +857,53 @@ void capture_step(pic_handle *h, StepGraph &g) {
         g.failed = true;
         cudaGetLastError();
     }
+}
+
+// capture the pending sort of the current parity (the end of a call)
+template <typename T>
+void capture_sort(pic_handle *h, StepGraph &g) {
+    const int64_t L0 = h->launches;
+    cudaStream_t keep = h->st;
+    h->st = h->gst;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        sort_tail<T>(h);
+        e = cudaStreamEndCapture(h->gst, &graph);
+    }
+    h->st = keep;
+    g.launches = h->launches - L0;
+    h->launches = L0;
+    if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || !g.exec) {
+        g.exec = nullptr;
+        g.failed = true;
+        cudaGetLastError();
+    }
+}
+
+// enqueue the pending sort on stream `on` (private stream: as a graph)
+void enqueue_sort_tail(pic_handle *h, cudaStream_t on) {
+    StepGraph &g = h->sort_graphs[h->cur];
+    if (on == h->gst && !g.exec && !g.failed) {
+        if (h->mixed)
+            capture_sort<float>(h, g);
+        else
+            capture_sort<double>(h, g);
+    }
+    if (on == h->gst && g.exec) {
+        cudaGraphLaunch(g.exec, h->gst);
+        h->launches += g.launches;
+        return;
+    }
+    cudaStream_t keep = h->st;
+    h->st = on;
+    if (h->mixed)
+        sort_tail<float>(h);
+    else
+        sort_tail<double>(h);
+    h->st = keep;
 }
 
 // capture one step of every reactor of the batch as one fork-join graph
@@ -815,9 +922,9 @@ void capture_batch(pic_batch *b, pic_batch::Graph &g) {
             cudaStream_t keep = h->st;
             h->st = h->gst;
             if (h->mixed)
-                one_step<float>(h);
+                one_step<float>(h, h->gst2);
             else
-                one_step<double>(h);
+                one_step<double>(h, h->gst2);
             h->st = keep;
             h->cur = cur;  // the replays flip it
             g.launches[k] = h->launches - L0;
@@ -930,7 +1037,8 @@ pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int32_t nsteps) {
     cudaStreamSynchronize(h->st);
     pic_status ce = cuda_check(h, "step");
     if (ce != PIC_OK) return ce;
-    const int64_t done = c.halt ? c.halt_step - step0 : (int64_t)nsteps;
+    // a failed sort ends the call at the pass it sorts, before any later failure
+    const int64_t done = c.sort_fail ? c.sort_fail_step - step0 : c.halt ? c.halt_step - step0 : (int64_t)nsteps;
     h->cur = (int)(cur0 ^ (int)(done & 1));
     h->step = step0 + done;
     h->nsamples += done;
@@ -952,22 +1060,26 @@ pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int32_t nsteps) {
         h->err = "non-finite particle state (particles dropped)";
         cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
     }
-    if (c.halt) {
-        // the state stays at the last completed step
+    if (c.halt || c.sort_fail) {
+        // the state stays at the last completed step (sorted: its sort is
+        // done, the failed pass's is dropped)
         const int32_t z[3] = {0, 0, 0};
         cudaMemcpyAsync(&h->sctl->halt, z, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(&h->sctl->sort_pending, z, 3 * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
         cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
-        if (c.halt_status & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
+        const int why = c.sort_fail ? c.sort_fail_status : c.halt_status;
+        if (why & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
             if (h->mixed)
                 deposit_current<float>(h);
             else
                 deposit_current<double>(h);
             cudaStreamSynchronize(h->st);
-            return fail(h, PIC_ERR_CAPACITY, (c.halt_status & ST_CAPACITY) ? "particle capacity exceeded"
-                                                                           : "births capacity exceeded");
+            return fail(h, PIC_ERR_CAPACITY, (why & ST_CAPACITY) ? "particle capacity exceeded"
+                                                                 : "births capacity exceeded");
         }
         cudaStreamSynchronize(h->st);
-        return fail(h, PIC_ERR_TIMEOUT, "multigrid grid barrier timed out");
+        return fail(h, PIC_ERR_TIMEOUT, c.sort_fail ? "births numbering: grid barrier timed out"
+                                                    : "multigrid grid barrier timed out");
     }
     cudaStreamSynchronize(h->st);
     return result;
@@ -1007,12 +1119,17 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out) {
     h->cfg = *cfg;
     h->st = (cudaStream_t)cfg->stream;
     h->user_st = h->st;
-    if (cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking) != cudaSuccess) {
-        h->gst = nullptr;
+    // the step's main branch at the highest priority, the sort branch at the lowest
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (cudaStreamCreateWithPriority(&h->gst, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->gst2, cudaStreamNonBlocking, least) != cudaSuccess) {
+        if (h->gst) cudaStreamDestroy(h->gst);
+        h->gst = h->gst2 = nullptr;
         cudaGetLastError();
     }
-    cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+    for (cudaEvent_t *e : {&h->ev_in, &h->ev_out, &h->ev_fork, &h->ev_join})
+        cudaEventCreateWithFlags(e, cudaEventDisableTiming);
     for (int s = 0; s < 2; ++s) {
         const pic_xsec &x = cfg->xs[s];
         h->own_sigma[s].assign(x.sigma_m2, x.sigma_m2 + (size_t)x.n_ch * x.n_e);
@@ -1106,10 +1223,12 @@ pic_status pic_step(pic_handle *h, int32_t nsteps) {
             on_gst = false;
         }
         if (h->mixed)
-            one_step<float>(h);
+            one_step<float>(h, nullptr);
         else
-            one_step<double>(h);
+            one_step<double>(h, nullptr);
     }
+    // the last pass's sort: the state between calls is sorted
+    enqueue_sort_tail(h, on_gst ? h->gst : h->st);
     if (on_gst) {
         cudaEventRecord(h->ev_out, h->gst);
         cudaStreamWaitEvent(h->st, h->ev_out, 0);
@@ -1222,10 +1341,30 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
             cudaStream_t keep = h->st;
             h->st = b->origin;
             if (h->mixed)
-                one_step<float>(h);
+                one_step<float>(h, nullptr);
             else
-                one_step<double>(h);
+                one_step<double>(h, nullptr);
             h->st = keep;
+        }
+    }
+    if (nsteps > 0) {
+        // every reactor's last sort, side by side on the reactors' streams
+        for (pic_handle *h : b->hs) {
+            StepGraph &g = h->sort_graphs[h->cur];
+            if (!g.exec && !g.failed) {
+                if (h->mixed)
+                    capture_sort<float>(h, g);
+                else
+                    capture_sort<double>(h, g);
+            }
+        }
+        cudaEventRecord(b->ev_fork, b->origin);
+        for (size_t k = 0; k < nh; ++k) {
+            pic_handle *h = b->hs[k];
+            cudaStreamWaitEvent(h->gst, b->ev_fork, 0);
+            enqueue_sort_tail(h, h->gst);
+            cudaEventRecord(b->ev_join[k], h->gst);
+            cudaStreamWaitEvent(b->origin, b->ev_join[k], 0);
         }
     }
     cudaEventRecord(b->ev_out, b->origin);

@@ -47,7 +47,32 @@ struct StepCtl {
     unsigned int bar;     // barrier counter of the births numbering
     int32_t bar_timeout;  // a bounded wait of the births numbering gave up
     double circ_V, circ_Q, circ_Qc;  // external circuit: electrode voltage and charge, capacitor charge
+    // The cell sort of a pass (scan, capacity check, rank, births numbering)
+    // runs in the next step beside its field solve, or at the end of the
+    // call: pending from the end of the pass until it is done.  A failed sort
+    // (capacity, births overflow, a wait that gave up) also halts the step.
+    int32_t sort_pending;
+    int32_t sort_fail;         // the sort failed: later sort kernels do nothing
+    int32_t sort_fail_status;  // ST_* bits of the failure
+    int32_t pad2;
+    int64_t sort_fail_step;    // number of the step whose sort failed
 };
+
+// a sort kernel has nothing to do: no pass waits for it, or the sort failed
+// (ctl null: a sort outside the timestep, always done)
+__device__ __forceinline__ bool sort_skip(const StepCtl *ctl) {
+    return ctl && (!ctl->sort_pending || ctl->sort_fail);
+}
+
+// a failure of the pending sort: the pass it sorts (the step before the one
+// being taken) did not complete, and nothing after it runs
+__device__ __forceinline__ void sort_failed(StepCtl *ctl, int status) {
+    if (atomicExch(&ctl->sort_fail, 1) == 0) {
+        ctl->sort_fail_status = status;
+        ctl->sort_fail_step = ctl->step - 1;
+    }
+    ctl->halt = 1;
+}
 
 // ---- grid barrier of cooperative launches ----
 // Thread 0 of each block adds 1 with release semantics and polls with
@@ -232,7 +257,7 @@ void launch_hist(PBuf<T> buf, const int32_t *n_dev, int32_t *counts, cudaStream_
 void launch_scan(const int32_t *counts, int32_t *cursor, int ncell, int32_t *block_sums,
                  int32_t *n_alive, int64_t capacity, DevScalars *ds, const StepCtl *ctl,
                  cudaStream_t st);
-// a failed check of the step so far (capacity, births overflow) halts it
+// a failed check of the pending sort's pass (capacity, births overflow)
 void launch_step_check(const DevScalars *ds, StepCtl *ctl, cudaStream_t st);
 template <typename T>
 void launch_rank(PBuf<T> main, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,

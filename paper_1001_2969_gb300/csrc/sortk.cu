@@ -64,7 +64,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int *tot
 
 __global__ void k_scan_tiles(const int32_t *counts, int ncell, int32_t *block_sums, const StepCtl *ctl) {
     __shared__ int s_warp[32];
-    if (ctl && ctl->halt) return;
+    if (sort_skip(ctl)) return;
     const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
     int v = 0;
     for (int q = 0; q < 4; ++q) v += (base + q < ncell) ? counts[base + q] : 0;
@@ -77,7 +77,7 @@ __global__ void k_scan_top(int32_t *block_sums, int nblocks, int32_t *n_alive, i
                            DevScalars *ds, const StepCtl *ctl) {
     __shared__ int s_warp[32];
     __shared__ int s_carry;
-    if (ctl && ctl->halt) return;
+    if (sort_skip(ctl)) return;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nblocks; b0 += blockDim.x) {
@@ -100,7 +100,7 @@ __global__ void k_scan_top(int32_t *block_sums, int nblocks, int32_t *n_alive, i
 __global__ void k_scan_apply(const int32_t *counts, int ncell, const int32_t *block_sums,
                              int32_t *cursor, const StepCtl *ctl) {
     __shared__ int s_warp[32];
-    if (ctl && ctl->halt) return;
+    if (sort_skip(ctl)) return;
     const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
     int c[4];
     int v = 0;
@@ -125,12 +125,9 @@ void launch_scan(const int32_t *counts, int32_t *cursor, int ncell, int32_t *blo
 }
 
 __global__ void k_step_check(const DevScalars *ds, StepCtl *ctl) {
+    if (sort_skip(ctl)) return;
     const int st = ds->status & (ST_CAPACITY | ST_BIRTH_OVERFLOW);
-    if (!ctl->halt && st) {
-        ctl->halt = 1;
-        ctl->halt_status = st;
-        ctl->halt_step = ctl->step;
-    }
+    if (st) sort_failed(ctl, st);
 }
 
 void launch_step_check(const DevScalars *ds, StepCtl *ctl, cudaStream_t st) {
@@ -143,7 +140,7 @@ __global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
                        const int32_t *n_births_dev, int32_t *cursor, int32_t *perm,
                        const int32_t *n_alive, int64_t cap, const int32_t *status, const StepCtl *ctl) {
     // a failed step keeps the previous permutation
-    if ((ctl && ctl->halt) || (int64_t)*n_alive > cap || (*status & (ST_CAPACITY | ST_BIRTH_OVERFLOW))) return;
+    if (sort_skip(ctl) || (int64_t)*n_alive > cap || (*status & (ST_CAPACITY | ST_BIRTH_OVERFLOW))) return;
     const int nm = *n_main_dev, nb = *n_births_dev;
     const int total = nm + nb;
     const int lane = threadIdx.x & 31;
@@ -173,8 +170,10 @@ template <typename T>
 void launch_rank(PBuf<T> mainb, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,
                  int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
                  const int32_t *status, const StepCtl *ctl, cudaStream_t st) {
-    k_rank<T><<<152 * 8, 256, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap,
-                                        status, ctl);
+    // short-lived blocks (a few tiles each): beside the field solve they
+    // retire often, so the solve's blocks find SMs early
+    k_rank<T><<<152 * 32, 256, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap,
+                                         status, ctl);
 }
 
 // ---- newborn numbering ----
@@ -200,7 +199,7 @@ __global__ void __launch_bounds__(kRadixThreads)
     __shared__ uint32_t s_run[256];
     __shared__ int s_warp[32];
     __shared__ int s_carry;
-    if (ctl->halt) return;
+    if (sort_skip(ctl)) return;
     const int nb = *nb_dev;
     if (nb <= 0) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -223,13 +222,10 @@ __global__ void __launch_bounds__(kRadixThreads)
     const uint64_t base = ctl->next_id[s];
     const int ntiles = (nb + kRadixTile - 1) / kRadixTile;
     unsigned nbar = 0;
-    // a wait that gives up halts the step (its ids would be wrong)
+    // a wait that gives up fails the sort (its ids would be wrong)
     auto bar = [&]() {
         if (count_barrier(&ctl->bar, (++nbar) * gridDim.x, &ctl->bar_timeout)) return true;
-        if (tid == 0 && atomicExch(&ctl->halt, 1) == 0) {
-            ctl->halt_status = ST_TIMEOUT;
-            ctl->halt_step = ctl->step;
-        }
+        if (tid == 0) sort_failed(ctl, ST_TIMEOUT);
         return false;
     };
     for (int e = blockIdx.x * blockDim.x + tid; e < nb; e += gridDim.x * blockDim.x) {
