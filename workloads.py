@@ -96,6 +96,15 @@ def config(name: str, **over) -> dict:
                    rf=dict(amp=amp, freq=[60e6, 2e6], phase=[0.0, 0.0]),
                    gas=dict(p_Pa=8.0, T_K=300.0, m_gas=M_AR),
                    dt=1.0 / 60e6 / 100, steps=1000, split_every=100)
+    elif name == "c5":
+        # the adjoint window: collisionless (the cross sections are zero,
+        # see collisionless()), 256 steps, checkpoints every 16
+        amp = [100.0]
+        cfg = dict(R=0.10, L=0.02, nz=65, nr=257, species=_species(1e15, 1_000_000),
+                   rf=dict(amp=amp, freq=[F_RF], phase=[0.0]),
+                   gas=dict(p_Pa=4.0, T_K=300.0, m_gas=M_AR),
+                   dt=1.0 / F_RF / 200, steps=256, split_every=0, ckpt=16,
+                   w_centre=(0.03, 0.01), w_sigma=0.005)
     elif name == "tiny":
         amp = [50.0]
         cfg = dict(R=0.004, L=0.004, nz=5, nr=5, species=_species(1e15, 8, cap_factor=64),
@@ -106,6 +115,8 @@ def config(name: str, **over) -> dict:
         raise KeyError(name)
     # table range: four times the summed electrode amplitude, in eV
     cfg["xsec"] = argon_tables(4.0 * sum(abs(a) for a in amp))
+    if name == "c5":
+        cfg["xsec"] = collisionless(cfg)["xsec"]
     cfg.update(dict(seed=1, weighting="zr2", chi_face="max", scatter="vs", mg_max_cycles=50,
                     mg_tol=1e-10, phi_zL=None, eedf_bins=200, eedf_emax=100.0,
                     precision="fp64"))
@@ -146,6 +157,30 @@ def batch_configs(n: int = 64, seed: int = 4, n_lo: int = 50_000, n_hi: int = 5_
         cfg["name"] = f"c4-{k}"
         out.append(cfg)
     return out
+
+
+def collisionless(cfg: dict) -> dict:
+    """Same workload with every cross section zero: no null-collision
+    candidates, hence no collisions and no births (the adjoint window)."""
+    out = dict(cfg)
+    xs = []
+    for t in cfg["xsec"]:
+        t = dict(t)
+        t["sigma"] = np.zeros_like(np.asarray(t["sigma"], dtype=np.float64))
+        xs.append(t)
+    out["xsec"] = xs
+    out["split_every"] = 0
+    return out
+
+
+def gaussian_weight(cfg: dict, centre=None, sigma=None) -> np.ndarray:
+    """Nodal weight w(r, z) of the adjoint window's functional: a Gaussian of
+    width sigma (m) centred at (r, z) = centre (m), on the (nz, nr) nodes."""
+    centre = cfg.get("w_centre", (0.03, 0.01)) if centre is None else centre
+    sigma = cfg.get("w_sigma", 0.005) if sigma is None else sigma
+    z = np.linspace(0.0, cfg["L"], cfg["nz"])[:, None]
+    r = np.linspace(0.0, cfg["R"], cfg["nr"])[None, :]
+    return np.exp(-((r - centre[0]) ** 2 + (z - centre[1]) ** 2) / (2.0 * sigma ** 2))
 
 
 def scaled(cfg: dict, n_per_species: int) -> dict:
