@@ -323,6 +323,34 @@ pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64
  */
 pic_status pic_get_circuit(pic_handle *h, double *out);
 
+/*
+ * pic_window -- a collisionless window of the timestep and the gradient of a
+ * time-averaged ion-density functional by a hand-written adjoint (the
+ * paper's timestep, Sec. 2.1 merged cycle, with the Monte Carlo step of
+ * Sec. 2.6 off: no collisions, births or splitting whatever the cross
+ * sections; the adjoint has no counterpart in the paper).
+ *
+ * From the handle's current particles and step index, takes nsteps steps
+ * with the first rf component's amplitude set to amp0 (V) and the z = L row
+ * of the potential set to phi_zL (nr values, V, host; NULL: zeros), and
+ * returns in *J the functional
+ *     J = (1/nsteps) sum_{n=1..nsteps} sum_k w[k] N_i^n(k),
+ * N_i^n the ion deposit after step n (the time average of the volume
+ * integral of w n_i), w: nz*nr doubles, host, row-major [i][j].  With grad
+ * != 0 also *dJ_damp = dJ/d amp0 and dJ_dphi_zL[0..nr-1] = dJ/d phi_zL
+ * (host).  The forward runs in the handle's precision; the adjoint is
+ * FP64.  The forward keeps the particle state every ckpt steps and the
+ * backward recomputes one such segment at a time (memory: about
+ * (nsteps/ckpt + ckpt) particle states).  Particles keep their slots (no
+ * sort) and one that reaches a wall leaves the sums.  The handle's own
+ * state (particles, fields, step, counters) is unchanged.
+ * Errors: PIC_ERR_ARG (nsteps < 1, ckpt < 1, null w, no rf component),
+ * PIC_ERR_NOT_CONVERGED / PIC_ERR_TIMEOUT (a solve of the window),
+ * PIC_ERR_CUDA (device memory).
+ */
+pic_status pic_window(pic_handle *h, int32_t nsteps, int32_t ckpt, const double *w, double amp0,
+                      const double *phi_zL, int32_t grad, double *J, double *dJ_damp, double *dJ_dphi_zL);
+
 pic_status pic_save(pic_handle *h, const char *path);
 pic_status pic_load(pic_handle *h, const char *path);
 

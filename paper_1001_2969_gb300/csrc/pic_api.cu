@@ -14,6 +14,7 @@
 
 #include "mg.cuh"
 #include "pic_internal.cuh"
+#include "window.cuh"
 
 using namespace pic;
 
@@ -1029,6 +1030,61 @@ pic_status get_particles_t(pic_handle *h, int s, pic_particles_view *v, int64_t 
 // call, then the step control and the status word decide the outcome; the
 // host copies of the step number, ids and solve statistics are refreshed,
 // and on a halt the state is left at the last completed step.
+void *win_alloc(void *ctx, size_t bytes) { return dalloc((pic_handle *)ctx, bytes); }
+void win_release(void *ctx, void *p) { release((pic_handle *)ctx, p); }
+
+// the collisionless window from the handle's current (sorted) particles
+template <typename T>
+pic_status window_t(pic_handle *h, int32_t nsteps, int32_t ckpt, const double *w, double amp0,
+                    const double *phi_zL, bool grad, double *J, double *dA, double *dphi) {
+    WindowIn<T> in{};
+    in.nz = h->nz;
+    in.nr = h->nr;
+    in.dz = h->dz;
+    in.dr = h->dr;
+    in.L = h->cfg.mesh.L;
+    in.dt = h->cfg.dt;
+    in.chi_face = h->cfg.chi_face;
+    in.mixed = h->mixed;
+    const int cur = h->cur;
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        in.q[s] = h->cfg.sp[s].q;
+        in.m[s] = h->cfg.sp[s].m;
+        int32_t na = 0, nm = 0;
+        cudaMemcpyAsync(&na, d.d_nalive, 4, cudaMemcpyDeviceToHost, h->st);
+        cudaMemcpyAsync(&nm, d.d_nmain[cur], 4, cudaMemcpyDeviceToHost, h->st);
+        cudaStreamSynchronize(h->st);
+        in.n[s] = na;
+        in.nmain[s] = nm;
+        in.main[s] = view<T>(d.main[cur]);
+        in.births[s] = view<T>(d.births[cur]);
+        in.perm[s] = d.perm;
+        fill_step_args<T>(h, in.args[s], s, cur, 1 - cur);
+    }
+    in.V = h->V;
+    in.phi0 = h->phi;
+    in.mgf = &h->mgf;
+    in.tol = h->cfg.mg_tol;
+    in.max_cycles = h->cfg.mg_max_cycles;
+    in.nrf = h->cfg.rf.n;
+    in.rf_amp = h->own_rf.data();
+    in.rf_freq = h->own_rf.data() + h->cfg.rf.n;
+    in.rf_phase = h->own_rf.data() + 2 * h->cfg.rf.n;
+    in.step0 = h->step;
+    in.st = h->st;
+    in.alloc = win_alloc;
+    in.release = win_release;
+    in.actx = h;
+    std::vector<double> pz((size_t)h->nr, 0.0);
+    if (phi_zL)
+        for (int j = 0; j < h->nr; ++j) pz[j] = phi_zL[j];
+    std::string err;
+    const int r = window_run<T>(in, nsteps, ckpt, w, amp0, pz.data(), grad, J, dA, dphi, err);
+    if (r != PIC_OK) return fail(h, (pic_status)r, err.c_str());
+    return cuda_check(h, "window");
+}
+
 pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int32_t nsteps) {
     StepCtl c;
     int32_t status = 0;
@@ -1560,6 +1616,14 @@ pic_status pic_get_circuit(pic_handle *h, double *out) {
     out[1] = c.circ_Q;
     out[2] = c.circ_Qc;
     return cuda_check(h, "get_circuit");
+}
+
+pic_status pic_window(pic_handle *h, int32_t nsteps, int32_t ckpt, const double *w, double amp0,
+                      const double *phi_zL, int32_t grad, double *J, double *dJ_damp, double *dJ_dphi_zL) {
+    if (!h || !w || nsteps < 1 || ckpt < 1) return fail(h, PIC_ERR_ARG, "bad window arguments");
+    if (h->cfg.rf.n < 1) return fail(h, PIC_ERR_ARG, "the window needs an rf component");
+    return h->mixed ? window_t<float>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL)
+                    : window_t<double>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL);
 }
 
 static const uint64_t kCkptMagic = 0x50494352475a3031ull;  // "PICRGZ01"

@@ -87,7 +87,7 @@ SYMBOLS = ("pic_init", "pic_step", "pic_field_solve", "pic_moments", "pic_get_pa
            "pic_set_particles", "pic_set_step", "pic_set_boundary", "pic_get_fields",
            "pic_get_counts", "pic_save", "pic_load", "pic_profile", "pic_timings", "pic_destroy",
            "pic_last_error", "pic_status_string", "pic_field_solve_noalloc", "pic_batch_init",
-           "pic_batch_step", "pic_batch_destroy", "pic_tune", "pic_get_circuit")
+           "pic_batch_step", "pic_batch_destroy", "pic_tune", "pic_get_circuit", "pic_window")
 
 
 class PicError(RuntimeError):
@@ -115,6 +115,7 @@ def lib():
         L.pic_batch_destroy.restype = None
         L.pic_tune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
         L.pic_get_circuit.argtypes = [vp, _dp]
+        L.pic_window.argtypes = [vp, C.c_int32, C.c_int32, _dp, C.c_double, _dp, C.c_int32, _dp, _dp, _dp]
         L.pic_field_solve.argtypes = [vp, vp, vp, C.c_double, vp, C.c_int32,
                                       C.POINTER(pic_solve_info)]
         L.pic_moments.argtypes = [vp, C.POINTER(pic_moments_out), C.c_int32]
@@ -292,6 +293,44 @@ def pic_get_circuit(h: Handle):
     out = np.zeros(3)
     _check(h, lib().pic_get_circuit(h.ptr, _p(out)))
     return tuple(out)
+
+
+def pic_window(h: Handle, nsteps: int, ckpt: int, w, amp0: float, phi_zL=None, grad: bool = True):
+    """The collisionless window from the handle's particles: (J, dJ/d amp0,
+    dJ/d phi_zL) with grad, else (J, None, None).  w: (nz, nr) weights."""
+    wv = _d(w).reshape(-1)
+    pz = None if phi_zL is None else _d(phi_zL)
+    J = np.zeros(1)
+    dA = np.zeros(1)
+    dP = np.zeros(h.nr)
+    _check(h, lib().pic_window(h.ptr, int(nsteps), int(ckpt), _p(wv), float(amp0),
+                               _p(pz) if pz is not None else None, 1 if grad else 0, _p(J),
+                               _p(dA), _p(dP)))
+    return (float(J[0]), float(dA[0]), dP) if grad else (float(J[0]), None, None)
+
+
+def window_function():
+    """torch.autograd.Function for J(amp0, phi_zL) of the collisionless window:
+    the forward calls pic_window with the gradient, the backward returns it
+    scaled by the incoming gradient.  Use as
+    ``window_function().apply(amp0, phi_zL, h, w, nsteps, ckpt)`` with amp0 a
+    0-d FP64 tensor and phi_zL an (nr,) FP64 tensor."""
+    import torch
+
+    class WindowJ(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, amp0, phi_zL, h, w, nsteps, ckpt):
+            J, dA, dP = pic_window(h, nsteps, ckpt, w, float(amp0), phi_zL.detach().cpu().numpy(), True)
+            ctx.save_for_backward(torch.tensor(dA, dtype=torch.float64),
+                                  torch.as_tensor(dP, dtype=torch.float64))
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dA, dP = ctx.saved_tensors
+            return gJ * dA, gJ * dP.to(gJ.device), None, None, None, None
+
+    return WindowJ
 
 
 def pic_tune(h: Handle, steps_per_variant: int = 2, variants=None):
