@@ -23,6 +23,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -358,6 +360,58 @@ def batch_run(args):
     return 0
 
 
+def adjoint_run(args):
+    """The adjoint window (workload c5): J alone and J with its gradient
+    (rf amplitude, z = L row) from the loaded state, ms per call, and the
+    forward's particle-steps/s."""
+    import torch
+    import workloads as W
+    from paper_1001_2969_gb300 import pic
+
+    stream = torch.cuda.current_stream()
+    cfg = W.config("c5", precision=args.precision)
+    if args.particles:
+        cfg = W.scaled(cfg, args.particles)
+    K, ck = cfg["steps"], cfg["ckpt"]
+    w = W.gaussian_weight(cfg)
+    amp = cfg["rf"]["amp"][0]
+    h = pic.pic_init(cfg, stream=stream.cuda_stream)
+    n = int(pic.pic_get_counts(h)["n_alive"].sum())
+    pic.pic_window(h, 4, 2, w, amp)  # warm-up (builds, first launches)
+
+    def timed(grad):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = pic.pic_window(h, K, ck, w, amp, grad=grad)
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    (J, _, _), t_fwd = timed(False)
+    (J2, dA, dP), t_grad = timed(True)
+    # central difference in the amplitude (1 V): differs from the adjoint
+    # where particles reach the walls (the loss events' share of the
+    # derivative is not in a pathwise adjoint)
+    fd = (pic.pic_window(h, K, ck, w, amp + 1.0, grad=False)[0] -
+          pic.pic_window(h, K, ck, w, amp - 1.0, grad=False)[0]) / 2.0
+    line = {"metric": "adjoint window: ms per J and per J with gradient", "unit": "ms",
+            "value": 1e3 * t_grad, "higher_is_better": False,
+            "dtype": "f32 forward + f64 adjoint" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "c5 adjoint window: R 10 cm, L 2 cm, 65x257 nodes, "
+                                   f"{n // 2} e- + {n // 2} Ar+ loaded at n0 1e15 m^-3, collisionless, "
+                                   f"{K} steps, checkpoints every {ck}, 100 V at 13.56 MHz; J = time average "
+                                   "of the integral of w n_i, w Gaussian at r 3 cm z 1 cm sigma 5 mm",
+                       "precision": args.precision},
+            "forward_ms": 1e3 * t_fwd, "gradient_ms": 1e3 * t_grad,
+            "forward_particle_steps_per_s": n * K / t_fwd,
+            "gradient_over_forward": t_grad / t_fwd,
+            "J": J, "dJ_damp": dA, "dJ_dphi_zL_max": float(np.abs(dP).max()),
+            "dJ_damp_central_difference_1V": fd,
+            "particles_lost_in_window": "yes (loaded plasma: electrons reach the walls)"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -375,6 +429,8 @@ def main():
                     help="time only the stand-alone field solve on the workload's mesh")
     ap.add_argument("--particles", type=int, default=0,
                     help="particles per species (default: the workload's; smaller for profiling)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the adjoint window (workload c5) instead")
     ap.add_argument("--batch", type=int, default=0,
                     help="time a batch of this many independent reactors instead (batched sweep)")
     args = ap.parse_args()
@@ -383,6 +439,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.solve_only:
         return solve_only(args) if rank == 0 else 0
+    if args.adjoint:
+        return adjoint_run(args)
     if args.batch > 0:
         return batch_run(args) if rank == 0 else 0
 

@@ -167,3 +167,31 @@ def test_window_gradient_by_central_differences_c1(pic):
         fd = (pic.pic_window(h, K, 4, w, amp, phi_zL=pz, grad=False)[0] -
               pic.pic_window(h, K, 4, w, amp, phi_zL=-pz, grad=False)[0]) / 0.2
         assert abs(fd - dP[j]) <= 1e-3 * scale, (j, fd, dP[j])
+
+
+def test_window_gradient_by_central_differences_c5_mesh(pic):
+    """The adjoint window's mesh (65 x 257) with 1M + 1M particles, FP64,
+    8 steps, no particle lost: dJ/d amp0 against central differences of the
+    GPU forward.  J moves by ~1e-11 of itself per volt here, so the solves
+    run to a relative residual of 1e-13 for the differences to resolve it."""
+    cfg = W.collisionless(W.config("c5", precision="fp64", mg_tol=1e-13))
+    n = 1_000_000
+    for sp in cfg["species"]:
+        sp["n_init"] = 0
+        sp["capacity"] = n + 4096
+        sp["n0"] = 1e13  # weak space charge of the random (not neutral) placement
+    vol = np.pi * cfg["R"] ** 2 * cfg["L"]
+    ws = cfg["species"][0]["n0"] * vol / n
+    parts = [W.random_particles(cfg, 0, n, seed=31, hot=0.2, accel=1e13, wscale=ws, margin=5e-3),
+             W.random_particles(cfg, 1, n, seed=32, hot=3.0, accel=1e9, wscale=ws, margin=5e-3)]
+    K, amp = 8, cfg["rf"]["amp"][0]
+    probe = handle(pic, cfg, parts, 0)
+    pic.pic_step(probe, K)
+    assert list(pic.pic_get_counts(probe)["n_alive"]) == [n, n]
+    h = handle(pic, cfg, parts, 0)
+    w = W.gaussian_weight(cfg)
+    J, dA, dP = pic.pic_window(h, K, 4, w, amp)
+    hA = 0.01 * amp
+    fd = (pic.pic_window(h, K, 4, w, amp + hA, grad=False)[0] -
+          pic.pic_window(h, K, 4, w, amp - hA, grad=False)[0]) / (2 * hA)
+    assert abs(fd - dA) <= 3e-3 * abs(dA), (fd, dA)
