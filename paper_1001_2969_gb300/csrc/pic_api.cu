@@ -103,7 +103,7 @@ struct pic_handle {
     cudaStream_t gst = nullptr;      // private stream the step graphs are captured on and run on
     cudaStream_t gst2 = nullptr;     // the step graph's second branch (the previous pass's cell sort)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
     StepGraph graphs[2];
     StepGraph sort_graphs[2];  // the last pass's cell sort at the end of a call
     double ngas = 0.0, nu_max[2] = {0, 0}, p_null[2] = {0, 0};
@@ -787,14 +787,25 @@ void one_step(pic_handle *h, cudaStream_t sb) {
         cudaMemsetAsync(h->sp[s].counts, 0, (size_t)h->ncell * sizeof(int32_t), st);
         cudaMemsetAsync(h->sp[s].d_nbirths[dst], 0, sizeof(int32_t), st);
     }
+    // the two species' passes are independent (what they share -- the other
+    // species' births, deposit and counts -- takes atomics or reserved
+    // slots): with a second branch the ion pass runs beside the electrons'
+    if (sb) {
+        cudaEventRecord(h->ev_fork2, st);
+        cudaStreamWaitEvent(sb, h->ev_fork2, 0);
+    }
     for (int s = 0; s < 2; ++s) {
         PhaseTimer t(h, 1 + s);
         StepArgs<T> a;
         fill_step_args<T>(h, a, s, src, dst);
         // blocks walk the chunks of the count on the device
-        launch_step<T>(a, h->step_grid, h->variant[s], st);
+        launch_step<T>(a, h->step_grid, h->variant[s], (sb && s == 1) ? sb : st);
         h->launches += 1;
         h->particle_launches += 1;
+    }
+    if (sb) {
+        cudaEventRecord(h->ev_join2, sb);
+        cudaStreamWaitEvent(st, h->ev_join2, 0);
     }
     {
         PhaseTimer t(h, 4);
@@ -825,11 +836,11 @@ void drop_graphs(pic_handle *h) {
 
 void destroy_streams(pic_handle *h) {
     drop_graphs(h);
-    for (cudaEvent_t e : {h->ev_in, h->ev_out, h->ev_fork, h->ev_join})
+    for (cudaEvent_t e : {h->ev_in, h->ev_out, h->ev_fork, h->ev_join, h->ev_fork2, h->ev_join2})
         if (e) cudaEventDestroy(e);
     if (h->gst) cudaStreamDestroy(h->gst);
     if (h->gst2) cudaStreamDestroy(h->gst2);
-    h->ev_in = h->ev_out = h->ev_fork = h->ev_join = nullptr;
+    h->ev_in = h->ev_out = h->ev_fork = h->ev_join = h->ev_fork2 = h->ev_join2 = nullptr;
     h->gst = h->gst2 = nullptr;
 }
 
@@ -1184,7 +1195,7 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out) {
         h->gst = h->gst2 = nullptr;
         cudaGetLastError();
     }
-    for (cudaEvent_t *e : {&h->ev_in, &h->ev_out, &h->ev_fork, &h->ev_join})
+    for (cudaEvent_t *e : {&h->ev_in, &h->ev_out, &h->ev_fork, &h->ev_join, &h->ev_fork2, &h->ev_join2})
         cudaEventCreateWithFlags(e, cudaEventDisableTiming);
     for (int s = 0; s < 2; ++s) {
         const pic_xsec &x = cfg->xs[s];
