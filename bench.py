@@ -165,17 +165,21 @@ def run_gpu(args, rank, world):
         ck = clocks.stop() if clocks else None
         launches = pic.pic_timings(h, reset=True)["launches"]
         ms = ev0.elapsed_time(ev1)
-        cycles = int(pic.pic_moments(h)["counters"][pic.PIC_C_MGCYC])
+        cnt = pic.pic_moments(h, reset=True)["counters"]
+        cycles = int(cnt[pic.PIC_C_MGCYC])
         n1 = pic.pic_get_counts(h)["n_alive"].sum()
-        psteps = 0.5 * (n0 + n1) * steps
+        # particles the passes moved, counted on the device step by step (the
+        # count changes with losses, births and the periodic split)
+        psteps = float(cnt[pic.PIC_C_PSTEPS])
         # phase breakdown and the particle kernel's own time: the same number of
         # steps again, launched one by one with CUDA events around each phase
         pic.pic_profile(h, True)
         pic.pic_step(h, steps)
         pic.pic_profile(h, False)
         tm = pic.pic_timings(h, reset=True)
-        res = dict(ms=ms, psteps=psteps, n0=int(n0), n1=int(n1), timings=tm, clocks=ck, status=st,
-                   mg_cycles=cycles / steps, launches=launches)
+        prof_psteps = float(pic.pic_moments(h, reset=True)["counters"][pic.PIC_C_PSTEPS])
+        res = dict(ms=ms, psteps=psteps, prof_psteps=prof_psteps, n0=int(n0), n1=int(n1), timings=tm,
+                   clocks=ck, status=st, mg_cycles=cycles / steps, launches=launches)
         if prec == args.precision:
             # end to end through the public API with host buffers: per step the z = L
             # boundary row goes host -> device from pinned memory and the time-averaged
@@ -196,9 +200,8 @@ def run_gpu(args, rank, world):
                 pic.pic_moments_into(h, mo)
             torch.cuda.synchronize()
             e2e_s = time.perf_counter() - t0
-            n2 = pic.pic_get_counts(h)["n_alive"].sum()
-            res["e2e"] = dict(seconds=e2e_s, psteps=0.5 * (n1 + n2) * e_steps, steps=e_steps,
-                              h2d=nr * 8, d2h=5 * nz * nr * 8)
+            e_ps = float(pic.pic_moments(h)["counters"][pic.PIC_C_PSTEPS])
+            res["e2e"] = dict(seconds=e2e_s, psteps=e_ps, steps=e_steps, h2d=nr * 8, d2h=5 * nz * nr * 8)
         pic.pic_destroy(h)
         del h
         torch.cuda.empty_cache()
@@ -326,7 +329,8 @@ def batch_run(args):
         return sum(int(pic.pic_get_counts(h)["n_alive"].sum()) for h in hs)
 
     def timed(fn):
-        n0 = count()
+        for h in hs:
+            pic.pic_moments(h, reset=True)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -334,7 +338,8 @@ def batch_run(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        return 0.5 * (n0 + count()) * args.steps / (ms * 1e-3), ms / args.steps
+        ps = sum(float(pic.pic_moments(h)["counters"][pic.PIC_C_PSTEPS]) for h in hs)
+        return ps / (ms * 1e-3), ms / args.steps
 
     v_batch, ms_batch = timed(lambda: b.step(args.steps))
 
@@ -490,7 +495,7 @@ def main():
     peak, peak_kind = _peaks()
     tm = main_r["timings"]
     k_ms = tm["particle_e_ms"] + tm["particle_i_ms"]
-    k_bytes = BYTES_PER_PARTICLE[args.precision] * main_r["psteps"]
+    k_bytes = BYTES_PER_PARTICLE[args.precision] * main_r["prof_psteps"]
     achieved = k_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
     tb = _traffic(args.precision)
     line = {
@@ -507,7 +512,7 @@ def main():
                      "frac": achieved / peak if achieved else None,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_particle": BYTES_PER_PARTICLE[args.precision],
-                     "traffic": tb * main_r["psteps"] / (2 * args.steps) if tb else None,
+                     "traffic": tb * main_r["prof_psteps"] / (2 * args.steps) if tb else None,
                      "kernel_ms_per_step": k_ms / args.steps},
         "phases_ms_per_step": {k[:-3]: v / args.steps for k, v in tm.items() if k.endswith("_ms")},
         "mg_cycles_per_step": main_r["mg_cycles"],

@@ -55,7 +55,8 @@ enum { PIC_XS_ELASTIC = 0, PIC_XS_EXCITE = 1, PIC_XS_IONIZE = 2, PIC_XS_CX = 3 }
 #define PIC_C_ABS 16    /* [s*3+wall] absorbed at z=0, z=L, r=R               */
 #define PIC_C_MGCYC 22  /* multigrid V-cycles, summed over steps              */
 #define PIC_C_STEPS 23  /* steps taken                                        */
-#define PIC_NCOUNT 24
+#define PIC_C_PSTEPS 24 /* particles moved by the passes, summed over steps   */
+#define PIC_NCOUNT 25
 
 /* Mesh: uniform node-centred r-z mesh, z in [0, L], r in [0, R] (Sec. 2.4,
  * Sec. 3.2).  nz must be 2^k + 1 (z-semi-coarsening, Sec. 2.5); 3 <= nr <= 1025

@@ -300,11 +300,12 @@ __global__ void k_step_begin(StepCtl *c, const double *rf, int nrf, double dt, i
 
 // step epilogue: the pass wrote *nalive entries into the destination main
 // buffers; their cell sort is pending, and the step advances
-__global__ void k_step_end(StepCtl *c, int32_t *nmain0, const int32_t *nalive0, int32_t *nmain1,
+__global__ void k_step_end(StepCtl *c, DevScalars *ds, int32_t *nmain0, const int32_t *nalive0, int32_t *nmain1,
                            const int32_t *nalive1) {
     if (c->halt) return;
     *nmain0 = *nalive0;
     *nmain1 = *nalive1;
+    ds->cnt[PIC_C_PSTEPS] += (unsigned long long)(*nalive0) + (unsigned long long)(*nalive1);
     c->sort_pending = 1;
     c->step += 1;
 }
@@ -811,8 +812,8 @@ void one_step(pic_handle *h, cudaStream_t sb) {
         PhaseTimer t(h, 4);
         launch_moments(h->N[0], h->N[1], h->V, h->phi, h->Ez, h->Er, h->m_acc[0], h->m_acc[1],
                        h->m_acc[2], h->m_acc[3], h->m_acc[4], h->ng, h->sctl, st);
-        k_step_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nmain[dst], h->sp[0].d_nalive, h->sp[1].d_nmain[dst],
-                                     h->sp[1].d_nalive);
+        k_step_end<<<1, 1, 0, st>>>(h->sctl, h->ds, h->sp[0].d_nmain[dst], h->sp[0].d_nalive,
+                                     h->sp[1].d_nmain[dst], h->sp[1].d_nalive);
         h->launches += 2;
     }
     h->cur = dst;

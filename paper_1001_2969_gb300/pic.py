@@ -21,7 +21,7 @@ PIC_OK, PIC_ERR_ARG, PIC_ERR_CAPACITY, PIC_ERR_CUDA = 0, 1, 2, 3
 PIC_ERR_NOT_CONVERGED, PIC_ERR_NUMERIC, PIC_ERR_TIMEOUT, PIC_ERR_STATE = 4, 5, 6, 7
 PIC_FP64, PIC_MIXED = 0, 1
 PIC_C_COLL, PIC_C_CAND, PIC_C_NUOVER, PIC_C_BIRTHS = 0, 8, 10, 12
-PIC_C_SPLITS, PIC_C_ABS, PIC_C_MGCYC, PIC_C_STEPS, PIC_NCOUNT = 14, 16, 22, 23, 24
+PIC_C_SPLITS, PIC_C_ABS, PIC_C_MGCYC, PIC_C_STEPS, PIC_C_PSTEPS, PIC_NCOUNT = 14, 16, 22, 23, 24, 25
 PIC_MAX_CH = 4
 N_TIMING = 5
 KIND = {"elastic": 0, "excite": 1, "ionize": 2, "cx": 3}

@@ -86,13 +86,15 @@ def config(name: str, **over) -> dict:
                    dt=1.0 / F_RF / 400, steps=200, split_every=400)
     elif name == "c2":
         amp = [300.0]
-        cfg = dict(R=0.20, L=0.025, nz=129, nr=513, species=_species(5e15, 10_000_000),
+        # room for the periodic split (every 200 steps), which multiplies the
+        # particles that drifted to smaller radii
+        cfg = dict(R=0.20, L=0.025, nz=129, nr=513, species=_species(5e15, 10_000_000, cap_factor=3.0),
                    rf=dict(amp=amp, freq=[F_RF], phase=[0.0]),
                    gas=dict(p_Pa=4.0, T_K=300.0, m_gas=M_AR),
                    dt=1.0 / F_RF / 200, steps=2000, split_every=200)
     elif name == "c3":
         amp = [200.0, 500.0]
-        cfg = dict(R=0.30, L=0.03, nz=257, nr=1025, species=_species(5e15, 100_000_000),
+        cfg = dict(R=0.30, L=0.03, nz=257, nr=1025, species=_species(5e15, 100_000_000, cap_factor=3.0),
                    rf=dict(amp=amp, freq=[60e6, 2e6], phase=[0.0, 0.0]),
                    gas=dict(p_Pa=8.0, T_K=300.0, m_gas=M_AR),
                    dt=1.0 / 60e6 / 100, steps=1000, split_every=100)
@@ -184,12 +186,14 @@ def gaussian_weight(cfg: dict, centre=None, sigma=None) -> np.ndarray:
 
 
 def scaled(cfg: dict, n_per_species: int) -> dict:
-    """Same workload with a different particle count (capacity follows)."""
+    """Same workload with a different particle count (capacity follows, in the
+    same proportion)."""
     out = dict(cfg)
     out["species"] = [dict(sp) for sp in cfg["species"]]
     for sp in out["species"]:
+        ratio = (sp["capacity"] - 4096) / sp["n_init"] if sp.get("n_init") else 1.5
         sp["n_init"] = int(n_per_species)
-        sp["capacity"] = int(n_per_species * 1.5) + 4096
+        sp["capacity"] = int(n_per_species * ratio) + 4096
     return out
 
 
