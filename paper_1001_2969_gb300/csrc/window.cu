@@ -13,7 +13,8 @@
 // multigrid solve, E.  The forward keeps a checkpoint of the particles every
 // `ckpt` steps; the backward recomputes one segment at a time from its
 // checkpoint, keeping the segment's states and fields, and runs the reverse
-// of each step in FP64:
+// of each step (each particle's Jacobian in the forward's precision, every
+// adjoint stored and accumulated in FP64):
 //   particles: deposit at x~^n, first push (rotation), final push (axis
 //     reflection), gather of E at x~^{n-1}  ->  particle adjoints of step
 //     n-1 and the adjoint of E on the mesh;
@@ -63,22 +64,24 @@ __device__ __forceinline__ void store_w(const WinState<T> &s, int k, const PS<T>
     s.cell[k] = cell;
 }
 
-// shape factors in double and their derivatives per unit length
-__device__ __forceinline__ void shapes(int weighting, int j, double oz, double orr, double dz, double dr,
-                                       double sz[2], double sr[2], double dsz[2], double dsr[2]) {
+// shape factors and their derivatives per unit length (inv_dz = 1/dz,
+// inv_dr = 1/dr)
+template <typename A>
+__device__ __forceinline__ void shapes(int weighting, int j, A oz, A orr, A inv_dz, A inv_dr, A sz[2], A sr[2],
+                                       A dsz[2], A dsr[2]) {
     sz[1] = oz;
-    sz[0] = 1.0 - oz;
-    dsz[1] = 1.0 / dz;
-    dsz[0] = -1.0 / dz;
+    sz[0] = (A)1 - oz;
+    dsz[1] = inv_dz;
+    dsz[0] = -inv_dz;
     if (weighting == PIC_WEIGHT_ZR) {
         sr[1] = orr;
-        dsr[1] = 1.0 / dr;
+        dsr[1] = inv_dr;
     } else {
-        const double t = 2.0 * j + 1.0;
-        sr[1] = orr * (2.0 * j + orr) / t;
-        dsr[1] = (2.0 * j + 2.0 * orr) / (t * dr);
+        const A it = (A)1 / (A)(2 * j + 1);
+        sr[1] = orr * ((A)(2 * j) + orr) * it;
+        dsr[1] = ((A)(2 * j) + (A)2 * orr) * it * inv_dr;
     }
-    sr[0] = 1.0 - sr[1];
+    sr[0] = (A)1 - sr[1];
     dsr[0] = -dsr[1];
 }
 
@@ -198,14 +201,17 @@ __global__ void k_win_J(const double *N, const double *w, int ng, double scale, 
     }
 }
 
-// ---- reverse of one step of one species (FP64 adjoint) ----
+// ---- reverse of one step of one species ----
 // prev: the state before the step (x~^{n-1}), cur: after it (x~^n);
 // bin: adjoint of cur (read), bout: adjoint of prev (written);
-// Nb: adjoint of this species' deposit N^n; Eb: adjoint of E^n (added to)
+// Nb: adjoint of this species' deposit N^n; Eb: adjoint of E^n (added to).
+// The step's Jacobian is taken in the forward's precision T (the forward
+// ran in it); the adjoints are stored and accumulated in FP64.
 template <typename T>
 __global__ void k_win_back(StepArgs<T> a, WinState<T> prev, WinState<T> cur, int n, const double *Nb,
-                           WinAdj bin, WinAdj bout, double *Ebz, double *Ebr, double dz, double dr,
-                           double qm, double dt) {
+                           WinAdj bin, WinAdj bout, double *Ebz, double *Ebr, T dr, T inv_dz, T inv_dr, T qm,
+                           T dt) {
+    using A = T;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     PS<T> p, q;
@@ -218,101 +224,108 @@ __global__ void k_win_back(StepArgs<T> a, WinState<T> prev, WinState<T> cur, int
     }
     const int nr = a.nr;
     // adjoint of x~^n: the state's own plus its deposit
-    double zb2 = bin.z[k], rb2 = bin.r[k];
+    A zb2 = (A)bin.z[k], rb2 = (A)bin.r[k];
     {
-        double sz[2], sr[2], dsz[2], dsr[2];
-        shapes(a.weighting, q.j, (double)q.oz, (double)q.orr, dz, dr, sz, sr, dsz, dsr);
+        A sz[2], sr[2], dsz[2], dsr[2];
+        shapes<A>(a.weighting, q.j, q.oz, q.orr, inv_dz, inv_dr, sz, sr, dsz, dsr);
         const double *g = Nb + (size_t)q.i * nr + q.j;
-        const double nb[2][2] = {{g[0], g[1]}, {g[nr], g[nr + 1]}};
-        double az_ = 0.0, ar_ = 0.0;
+        const A nb[2][2] = {{(A)g[0], (A)g[1]}, {(A)g[nr], (A)g[nr + 1]}};
+        A az_ = 0, ar_ = 0;
+#pragma unroll
         for (int u = 0; u < 2; ++u)
+#pragma unroll
             for (int v = 0; v < 2; ++v) {
                 az_ += dsz[u] * sr[v] * nb[u][v];
                 ar_ += sz[u] * dsr[v] * nb[u][v];
             }
-        const double w = (double)q.w;
-        zb2 += w * az_;
-        rb2 += w * ar_;
+        zb2 += q.w * az_;
+        rb2 += q.w * ar_;
     }
-    const double vrb2 = bin.vr[k], vtb2 = bin.vt[k], vzb2 = bin.vz[k], arb2 = bin.ar[k], azb2 = bin.az[k];
-    // forward of the step again, in FP64, from x~^{n-1}
-    double sz[2], sr[2], dsz[2], dsr[2];
-    shapes(a.weighting, p.j, (double)p.oz, (double)p.orr, dz, dr, sz, sr, dsz, dsr);
+    const A vrb2 = (A)bin.vr[k], vtb2 = (A)bin.vt[k], vzb2 = (A)bin.vz[k], arb2 = (A)bin.ar[k],
+            azb2 = (A)bin.az[k];
+    // the step's forward again, from x~^{n-1}
+    A sz[2], sr[2], dsz[2], dsr[2];
+    shapes<A>(a.weighting, p.j, p.oz, p.orr, inv_dz, inv_dr, sz, sr, dsz, dsr);
     const auto *Ep = a.E + (size_t)p.i * nr + p.j;
-    const double ez[2][2] = {{(double)Ep[0].x, (double)Ep[1].x}, {(double)Ep[nr].x, (double)Ep[nr + 1].x}};
-    const double er[2][2] = {{(double)Ep[0].y, (double)Ep[1].y}, {(double)Ep[nr].y, (double)Ep[nr + 1].y}};
-    double Ez = 0.0, Er = 0.0;
+    const auto e00 = Ep[0], e01 = Ep[1], e10 = Ep[nr], e11 = Ep[nr + 1];
+    const A ez[2][2] = {{e00.x, e01.x}, {e10.x, e11.x}};
+    const A er[2][2] = {{e00.y, e01.y}, {e10.y, e11.y}};
+    A Ez = 0, Er = 0;
+#pragma unroll
     for (int u = 0; u < 2; ++u)
+#pragma unroll
         for (int v = 0; v < 2; ++v) {
             Ez += sz[u] * sr[v] * ez[u][v];
             Er += sz[u] * sr[v] * er[u][v];
         }
-    const double r = ((double)p.j + (double)p.orr) * dr;
-    const double kz = 0.5 * qm * dt * dt, kv = 0.5 * qm * dt;
-    const double rr = r + kz * Er;
-    const bool flip = rr < 0.0;
-    const double r1 = flip ? -rr : rr;
-    const double vr1u = (double)p.vr + kv * Er;
-    const double ar1u = 0.5 * (qm * Er + (double)p.ar);
-    const double vr1 = flip ? fabs(vr1u) : vr1u;
-    const double ar1 = flip ? fabs(ar1u) : ar1u;
-    const double vt1 = (double)p.vt;
+    const A r = ((A)p.j + p.orr) * dr;
+    const A kz = (A)0.5 * qm * dt * dt, kv = (A)0.5 * qm * dt;
+    const A rr = r + kz * Er;
+    const bool flip = rr < (A)0;
+    const A r1 = flip ? -rr : rr;
+    const A vr1u = p.vr + kv * Er;
+    const A ar1u = (A)0.5 * (qm * Er + p.ar);
+    const A vr1 = flip ? m_abs(vr1u) : vr1u;
+    const A ar1 = flip ? m_abs(ar1u) : ar1u;
+    const A vt1 = p.vt;
     // first push
-    const double vx = vr1 + 0.5 * ar1 * dt, vy = vt1;
-    const double xr = r1 + vx * dt, yr = vy * dt;
-    const double q2 = xr * xr + yr * yr;
-    double c = 1.0, s = 0.0, r2 = 0.0;
-    if (q2 > 0.0) {
-        r2 = sqrt(q2);
-        c = xr / r2;
-        s = yr / r2;
+    const A vx = vr1 + (A)0.5 * ar1 * dt, vy = vt1;
+    const A xr = r1 + vx * dt, yr = vy * dt;
+    const A q2 = xr * xr + yr * yr;
+    A c = 1, s = 0, ir2 = 0;
+    if (q2 > (A)0) {
+        ir2 = m_rsqrt(q2);
+        c = xr * ir2;
+        s = yr * ir2;
     }
     // reverse of the first push
-    double vxb = vrb2 * c - vtb2 * s;
-    double vyb = vrb2 * s + vtb2 * c;
-    const double cb = vrb2 * vx + vtb2 * vy + arb2 * ar1;
-    const double sb = vrb2 * vy - vtb2 * vx;
-    double ar1b = arb2 * c;
-    double xrb = 0.0, yrb = 0.0;
-    if (q2 > 0.0) {
-        xrb = rb2 * c + (cb * s * s - sb * c * s) / r2;
-        yrb = rb2 * s + (-cb * c * s + sb * c * c) / r2;
+    A vxb = vrb2 * c - vtb2 * s;
+    A vyb = vrb2 * s + vtb2 * c;
+    const A cb = vrb2 * vx + vtb2 * vy + arb2 * ar1;
+    const A sb = vrb2 * vy - vtb2 * vx;
+    A ar1b = arb2 * c;
+    A xrb = 0, yrb = 0;
+    if (q2 > (A)0) {
+        xrb = rb2 * c + (cb * s * s - sb * c * s) * ir2;
+        yrb = rb2 * s + (-cb * c * s + sb * c * c) * ir2;
     }
-    const double r1b = xrb;
+    const A r1b = xrb;
     vxb += dt * xrb;
     vyb += dt * yrb;
-    const double z1b = zb2;
-    const double vz2b = vzb2 + dt * zb2;
-    const double vz1b = vz2b;
-    const double az1b = azb2 + 0.5 * dt * vz2b;
-    const double vr1b = vxb;
-    ar1b += 0.5 * dt * vxb;
-    const double vt1b = vyb;
+    const A z1b = zb2;
+    const A vz2b = vzb2 + dt * zb2;
+    const A vz1b = vz2b;
+    const A az1b = azb2 + (A)0.5 * dt * vz2b;
+    const A vr1b = vxb;
+    ar1b += (A)0.5 * dt * vxb;
+    const A vt1b = vyb;
     // reverse of the final push (and the axis reflection)
-    const double rrb = flip ? -r1b : r1b;
-    const double vr1ub = flip ? (vr1u < 0.0 ? -vr1b : (vr1u > 0.0 ? vr1b : 0.0)) : vr1b;
-    const double ar1ub = flip ? (ar1u < 0.0 ? -ar1b : (ar1u > 0.0 ? ar1b : 0.0)) : ar1b;
-    const double Ezb = kz * z1b + kv * vz1b + 0.5 * qm * az1b;
-    const double Erb = kz * rrb + kv * vr1ub + 0.5 * qm * ar1ub;
-    double zb = z1b, rb = rrb;
+    const A rrb = flip ? -r1b : r1b;
+    const A vr1ub = flip ? (vr1u < (A)0 ? -vr1b : (vr1u > (A)0 ? vr1b : (A)0)) : vr1b;
+    const A ar1ub = flip ? (ar1u < (A)0 ? -ar1b : (ar1u > (A)0 ? ar1b : (A)0)) : ar1b;
+    const A Ezb = kz * z1b + kv * vz1b + (A)0.5 * qm * az1b;
+    const A Erb = kz * rrb + kv * vr1ub + (A)0.5 * qm * ar1ub;
+    A zb = z1b, rb = rrb;
     // reverse of the gather: E's adjoint on the mesh, positions' share
     double *gz = Ebz + (size_t)p.i * nr + p.j, *gr = Ebr + (size_t)p.i * nr + p.j;
+#pragma unroll
     for (int u = 0; u < 2; ++u)
+#pragma unroll
         for (int v = 0; v < 2; ++v) {
-            const double wgt = sz[u] * sr[v];
-            atomicAdd(gz + u * nr + v, wgt * Ezb);
-            atomicAdd(gr + u * nr + v, wgt * Erb);
-            const double f = ez[u][v] * Ezb + er[u][v] * Erb;
+            const A wgt = sz[u] * sr[v];
+            atomicAdd(gz + u * nr + v, (double)(wgt * Ezb));
+            atomicAdd(gr + u * nr + v, (double)(wgt * Erb));
+            const A f = ez[u][v] * Ezb + er[u][v] * Erb;
             zb += dsz[u] * sr[v] * f;
             rb += sz[u] * dsr[v] * f;
         }
-    bout.z[k] = zb;
-    bout.r[k] = rb;
-    bout.vr[k] = vr1ub;
-    bout.vt[k] = vt1b;
-    bout.vz[k] = vz1b;
-    bout.ar[k] = 0.5 * ar1ub;
-    bout.az[k] = 0.5 * az1b;
+    bout.z[k] = (double)zb;
+    bout.r[k] = (double)rb;
+    bout.vr[k] = (double)vr1ub;
+    bout.vt[k] = (double)vt1b;
+    bout.vz[k] = (double)vz1b;
+    bout.ar[k] = (double)((A)0.5 * ar1ub);
+    bout.az[k] = (double)((A)0.5 * az1b);
 }
 
 // adjoint of E = -grad phi (the stencils of k_efield) onto phi_bar
@@ -460,8 +473,10 @@ int window_run(const WindowIn<T> &in, int K, int ckpt, const double *w_host, dou
             if (grad)
                 for (int m = 0; m < ckpt; ++m) seg[s].push_back(new_state(in.n[s]));
         }
-        std::vector<double *> phi_ck(nseg + 1);
-        for (auto &g : phi_ck) g = dgrid();
+        // the potential of every step (the backward's recomputation takes it
+        // instead of solving again: K grids, small beside the particles)
+        std::vector<double *> phi_all(grad ? K + 1 : 0);
+        for (auto &g : phi_all) g = dgrid();
         double *rho = dgrid(), *chi = dgrid(), *phi = dgrid(), *Ez = dgrid(), *Er = dgrid();
         double *N[2][2] = {{dgrid(), dgrid()}, {dgrid(), dgrid()}};  // [rolling][species]
         V2T *E2 = (V2T *)take((size_t)ng * sizeof(V2T));
@@ -501,12 +516,19 @@ int window_run(const WindowIn<T> &in, int K, int ckpt, const double *w_host, dou
         };
         int L = 0;
         // one forward step: field from Nin, push states in -> out, deposit into Nout
-        auto fwd = [&](int n, const WinState<T> *Sin, const WinState<T> *Sout, double **Nin, double **Nout) {
+        // one forward step; `again`: the step's potential is the stored one
+        auto fwd = [&](int n, const WinState<T> *Sin, const WinState<T> *Sout, double **Nin, double **Nout,
+                       bool again) {
             launch_finalize(Nin[0], Nin[1], in.V, in.q[0], in.q[1], c_chi[0], c_chi[1], rho, chi, ng, nullptr, st);
-            const double t = (double)(in.step0 + n) * in.dt;
-            if (mg_fast_solve(fd, *in.mgf, rho, chi, voltage(t), pzl, phi, true, in.mixed, in.tol, in.max_cycles,
-                              nullptr, &L, wctl, st, false, true) == kSolveNoLaunch)
-                throw 1;
+            if (again) {
+                cudaMemcpyAsync(phi, phi_all[n], (size_t)ng * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            } else {
+                const double t = (double)(in.step0 + n) * in.dt;
+                if (mg_fast_solve(fd, *in.mgf, rho, chi, voltage(t), pzl, phi, true, in.mixed, in.tol,
+                                  in.max_cycles, nullptr, &L, wctl, st, false, true) == kSolveNoLaunch)
+                    throw 1;
+                if (grad) cudaMemcpyAsync(phi_all[n], phi, (size_t)ng * sizeof(double), cudaMemcpyDeviceToDevice, st);
+            }
             launch_efield<T>(phi, Ez, Er, E2, nz, nr, in.dz, in.dr, nullptr, st);
             for (int s = 0; s < 2; ++s) {
                 cudaMemsetAsync(Nout[s], 0, (size_t)ng * sizeof(double), st);
@@ -519,17 +541,14 @@ int window_run(const WindowIn<T> &in, int K, int ckpt, const double *w_host, dou
             WinState<T> cur[2] = {ck[0][0], ck[1][0]};
             double *Nc[2] = {N[0][0], N[0][1]}, *Nn[2] = {N[1][0], N[1][1]};
             deposit(cur, Nc);
-            cudaMemcpyAsync(phi_ck[0], phi, (size_t)ng * sizeof(double), cudaMemcpyDeviceToDevice, st);
             // two working states beyond the checkpoints: reuse the segment's (or
             // the next checkpoint slot when only the forward runs)
             for (int n = 1; n <= K; ++n) {
                 const int m = (n - 1) / ckpt;
                 WinState<T> nxt[2];
                 for (int s = 0; s < 2; ++s) nxt[s] = (n % ckpt == 0 || n == K) ? ck[s][m + 1] : (grad ? seg[s][(n - 1) % ckpt] : ck[s][m + 1]);
-                fwd(n, cur, nxt, Nc, Nn);
+                fwd(n, cur, nxt, Nc, Nn, false);
                 k_win_J<<<(ng + kWT * 8 - 1) / (kWT * 8), kWT, 0, st>>>(Nn[1], w_d, ng, 1.0 / K, acc);
-                if (n % ckpt == 0 || n == K)
-                    cudaMemcpyAsync(phi_ck[m + 1], phi, (size_t)ng * sizeof(double), cudaMemcpyDeviceToDevice, st);
                 for (int s = 0; s < 2; ++s) {
                     cur[s] = nxt[s];
                     std::swap(Nc[s], Nn[s]);
@@ -537,12 +556,11 @@ int window_run(const WindowIn<T> &in, int K, int ckpt, const double *w_host, dou
             }
         }
         if (grad) {
-            // per segment step: E, phi, chi of the recomputed forward
+            // per segment step: E and chi of the recomputed forward
             std::vector<V2T *> E2s(ckpt);
-            std::vector<double *> phis(ckpt), chis(ckpt);
+            std::vector<double *> chis(ckpt);
             for (int q = 0; q < ckpt; ++q) {
                 E2s[q] = (V2T *)take((size_t)ng * sizeof(V2T));
-                phis[q] = dgrid();
                 chis[q] = dgrid();
             }
             WinAdj b[2][2];
@@ -554,6 +572,7 @@ int window_run(const WindowIn<T> &in, int K, int ckpt, const double *w_host, dou
             }
             double *Nb[2] = {dgrid(), dgrid()};
             double *Ebz = dgrid(), *Ebr = dgrid(), *phib = dgrid(), *rhof = dgrid(), *lam = dgrid(), *chib = dgrid();
+            cudaMemsetAsync(lam, 0, (size_t)ng * sizeof(double), st);
             k_set_J_term<<<blocks(ng), kWT, 0, st>>>(Nb[0], Nb[1], w_d, ng, 1.0 / K);
             int pb = 0;  // b[pb] holds the adjoint of the current state
             for (int m = nseg - 1; m >= 0; --m) {
@@ -567,13 +586,11 @@ int window_run(const WindowIn<T> &in, int K, int ckpt, const double *w_host, dou
                 double *Nc[2] = {N[0][0], N[0][1]}, *Nn[2] = {N[1][0], N[1][1]};
                 WinState<T> c0[2] = {S[0][0], S[1][0]};
                 deposit(c0, Nc);
-                cudaMemcpyAsync(phi, phi_ck[m], (size_t)ng * sizeof(double), cudaMemcpyDeviceToDevice, st);
                 for (int n = a0 + 1; n <= b0; ++n) {
                     const int q = n - a0;
                     WinState<T> si[2] = {S[0][q - 1], S[1][q - 1]}, so[2] = {S[0][q], S[1][q]};
-                    fwd(n, si, so, Nc, Nn);
+                    fwd(n, si, so, Nc, Nn, true);
                     cudaMemcpyAsync(E2s[q - 1], E2, (size_t)ng * sizeof(V2T), cudaMemcpyDeviceToDevice, st);
-                    cudaMemcpyAsync(phis[q - 1], phi, (size_t)ng * sizeof(double), cudaMemcpyDeviceToDevice, st);
                     cudaMemcpyAsync(chis[q - 1], chi, (size_t)ng * sizeof(double), cudaMemcpyDeviceToDevice, st);
                     for (int s = 0; s < 2; ++s) std::swap(Nc[s], Nn[s]);
                 }
@@ -586,20 +603,22 @@ int window_run(const WindowIn<T> &in, int K, int ckpt, const double *w_host, dou
                         if (in.n[s] == 0) continue;
                         StepArgs<T> as = a[s];
                         as.E = E2s[q - 1];
-                        k_win_back<T><<<blocks(in.n[s]), kWT, 0, st>>>(as, S[s][q - 1], S[s][q], in.n[s], Nb[s],
-                                                                        b[pb][s], b[1 - pb][s], Ebz, Ebr, in.dz,
-                                                                        in.dr, in.q[s] / in.m[s], in.dt);
+                        k_win_back<T><<<blocks(in.n[s]), kWT, 0, st>>>(
+                            as, S[s][q - 1], S[s][q], in.n[s], Nb[s], b[pb][s], b[1 - pb][s], Ebz, Ebr, (T)in.dr,
+                            (T)(1.0 / in.dz), (T)(1.0 / in.dr), (T)(in.q[s] / in.m[s]), (T)in.dt);
                     }
                     pb = 1 - pb;
                     cudaMemsetAsync(phib, 0, (size_t)ng * sizeof(double), st);
                     k_efield_adj<<<blocks(ng), kWT, 0, st>>>(Ebz, Ebr, phib, nz, nr, in.dz, in.dr);
                     k_adj_rhs<<<blocks(ng), kWT, 0, st>>>(phib, rhof, nz, nr, in.dz, in.dr);
-                    if (mg_fast_solve(fd, *in.mgf, rhof, chis[q - 1], 0.0, nullptr, lam, false, in.mixed, in.tol,
+                    // warm start from the previous step's lambda (zero at first):
+                    // consecutive adjoint fields are close
+                    if (mg_fast_solve(fd, *in.mgf, rhof, chis[q - 1], 0.0, nullptr, lam, true, in.mixed, in.tol,
                                       in.max_cycles, nullptr, &L, wctl, st, false, true) == kSolveNoLaunch)
                         throw 1;
                     cudaMemsetAsync(chib, 0, (size_t)ng * sizeof(double), st);
                     k_face_adj<<<blocks((long long)(nz - 1) * nr + (long long)nz * (nr - 1)), kWT, 0, st>>>(
-                        lam, phis[q - 1], chis[q - 1], chib, nz, nr, in.dz, in.dr, in.chi_face == PIC_CHI_MEAN);
+                        lam, phi_all[n], chis[q - 1], chib, nz, nr, in.dz, in.dr, in.chi_face == PIC_CHI_MEAN);
                     const double t = (double)(in.step0 + n) * in.dt;
                     const double sin_t = std::sin(2.0 * kPi * in.rf_freq[0] * t + in.rf_phase[0]);
                     k_node_adj<<<blocks(ng), kWT, 0, st>>>(lam, chis[q - 1], phib, chib, in.V, w_d, Nb[0], Nb[1], nz,
