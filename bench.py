@@ -30,8 +30,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s and ms/step at 20M particles (mixed vs FP64); % of HBM peak"
 UNIT = "particle-steps/s"
-WORKLOAD = ("c2 production reactor: R 20 cm, L 2.5 cm, 129x513 nodes, 1e7 e- + 1e7 Ar+, "
-            "n0 5e15 m^-3, argon 4 Pa 300 K, 300 V at 13.56 MHz, dt = T_rf/200, seed 1")
+WORKLOADS = {
+    "c2": ("c2 production reactor: R 20 cm, L 2.5 cm, 129x513 nodes, 1e7 e- + 1e7 Ar+, "
+           "n0 5e15 m^-3, argon 4 Pa 300 K, 300 V at 13.56 MHz, dt = T_rf/200, seed 1"),
+    "c1": ("c1 small reactor: R 5 cm, L 2 cm, 33x65 nodes, 1e5 e- + 1e5 Ar+, n0 1e15 m^-3, "
+           "argon 4 Pa 300 K, 100 V at 13.56 MHz, dt = T_rf/400, seed 1"),
+    "c3": ("c3 large dual-frequency reactor: R 30 cm, L 3 cm, 257x1025 nodes, 1e8 e- + 1e8 Ar+, "
+           "n0 5e15 m^-3, argon 8 Pa 300 K, 200 V at 60 MHz + 500 V at 2 MHz, dt = T_60MHz/100, seed 1"),
+}
+WORKLOAD = WORKLOADS["c2"]
 # algorithmic bytes of the particle pass per particle: the state read once and
 # written once (mixed: cell 4 + offsets 8 + v 12 + a 8 + w 4 + id 8 = 44 B)
 BYTES_PER_PARTICLE = {"mixed": 88, "fp64": 152}
@@ -472,7 +479,7 @@ def main():
                 "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * dt / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "sample": sample},
+                "config": {"workload": WORKLOADS.get(args.config, args.config), "sample": sample},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -503,9 +510,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision,
+        "config": {"workload": WORKLOADS.get(args.config, args.config), "precision": args.precision,
                    "particles_per_rank": main_r["n0"],
-                   "l2": "no flush: particle state (880 MB mixed) is larger than L2 (129 MB)",
+                   "l2": f"no flush: particle state ({main_r['n0'] * BYTES_PER_PARTICLE[args.precision] // 2 // 1000000} "
+                         f"MB) is larger than L2 (129 MB)",
                    "parallelism": f"{world} independent reactor replica(s), one per GPU"},
         "roofline": {"bound": "hbm", "kernel": "k_step (fused particle pass, both species)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
