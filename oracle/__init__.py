@@ -71,6 +71,7 @@ class OrcConfig(C.Structure):
         ("split_every", C.c_int32), ("mg_max_cycles", C.c_int32), ("mg_tol", C.c_double),
         ("phi_zL", _dp), ("eedf_bins", C.c_int32), ("eedf_emax", C.c_double),
         ("circuit_C", C.c_double),
+        ("pusher", C.c_int32),
     ]
 
 
@@ -122,6 +123,8 @@ def _declare(L):
     L.orc_ejected_energy.restype = C.c_double
     L.orc_ejected_energy.argtypes = [C.c_double] * 4
     L.orc_get_circuit.argtypes = [vp, _dp]
+    L.orc_get_at.argtypes = [vp, C.c_int, _dp]
+    L.orc_set_at.argtypes = [vp, C.c_int, _dp]
     L.orc_w_ref.restype = C.c_double
     L.orc_w_ref.argtypes = [vp, C.c_int, C.c_int]
 
@@ -192,6 +195,7 @@ class Oracle:
         c.eedf_bins = cfg.get("eedf_bins", 0)
         c.eedf_emax = cfg.get("eedf_emax", 100.0)
         c.circuit_C = float(cfg.get("circuit_C", 0.0))
+        c.pusher = {"local": 0, "xyz": 1}[cfg.get("pusher", "local")]
         if capacity is None:
             capacity = max(int(1.5 * max(sp["capacity"] for sp in cfg["species"])), 64)
         self.capacity = capacity
@@ -235,6 +239,17 @@ class Oracle:
         lib().orc_get_particles(self.h, s, *[_ptr(arr[k]) for k in FIELDS], _ptr(idv, _u64p))
         arr["id"] = idv
         return arr
+
+    def get_at(self, s) -> np.ndarray:
+        """a_theta of species s (the X-Y-Z pusher carries it)."""
+        out = np.zeros(self.count(s))
+        lib().orc_get_at(self.h, s, _ptr(out))
+        return out
+
+    def set_at(self, s, at):
+        a = _d(at)
+        assert len(a) == self.count(s)
+        lib().orc_set_at(self.h, s, _ptr(a))
 
     def set_next_id(self, s, v):
         lib().orc_set_next_id(self.h, s, int(v))

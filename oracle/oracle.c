@@ -28,6 +28,7 @@ static const double ORC_PI = 3.14159265358979323846;
 typedef struct {
     int64_t n;
     double *r, *z, *vr, *vt, *vz, *ar, *az, *w;
+    double *at; /* a_theta: carried by the X-Y-Z pusher only */
     uint64_t *id;
 } orc_store;
 
@@ -36,7 +37,7 @@ typedef struct {
     int ps;       /* species of the parent               */
     uint64_t pid; /* parent id                           */
     int k;        /* birth slot within the parent's pass */
-    double r, z, vr, vt, vz, ar, az, w;
+    double r, z, vr, vt, vz, ar, az, w, at;
 } orc_birth;
 
 struct orc_state {
@@ -329,6 +330,7 @@ static void store_alloc(orc_store *s, int64_t cap) {
     s->ar = xmalloc(cap * sizeof(double));
     s->az = xmalloc(cap * sizeof(double));
     s->w = xmalloc(cap * sizeof(double));
+    s->at = xmalloc(cap * sizeof(double));
     s->id = xmalloc(cap * sizeof(uint64_t));
 }
 
@@ -341,6 +343,7 @@ static void store_free(orc_store *s) {
     free(s->ar);
     free(s->az);
     free(s->w);
+    free(s->at);
     free(s->id);
 }
 
@@ -462,12 +465,21 @@ void orc_set_particles(orc_state *st, int s, int64_t n, const double *r, const d
     memcpy(p->ar, ar, n * sizeof(double));
     memcpy(p->az, az, n * sizeof(double));
     memcpy(p->w, w, n * sizeof(double));
+    memset(p->at, 0, n * sizeof(double));
     memcpy(p->id, id, n * sizeof(uint64_t));
     uint64_t mx = 0;
     for (int64_t k = 0; k < n; ++k)
         if (id[k] + 1 > mx) mx = id[k] + 1;
     st->next_id[s] = mx;
     orc_deposit(st);
+}
+
+void orc_get_at(const orc_state *st, int s, double *at) {
+    memcpy(at, st->p[s].at, st->p[s].n * sizeof(double));
+}
+
+void orc_set_at(orc_state *st, int s, const double *at) {
+    memcpy(st->p[s].at, at, st->p[s].n * sizeof(double));
 }
 
 void orc_get_particles(const orc_state *st, int s, double *r, double *z, double *vr, double *vt,
@@ -960,6 +972,7 @@ void orc_efield(orc_state *st) {
 /* ------------------------------------------------------------------ */
 typedef struct {
     double r, z, vr, vt, vz, ar, az, w;
+    double at; /* a_theta (X-Y-Z pusher) */
 } orc_p;
 
 static void push_birth(orc_state *st, int ts, int ps, uint64_t pid, int k, const orc_p *q) {
@@ -980,6 +993,7 @@ static void push_birth(orc_state *st, int ts, int ps, uint64_t pid, int k, const
     b->ar = q->ar;
     b->az = q->az;
     b->w = q->w;
+    b->at = q->at;
 }
 
 /* wall test on a position (READING: domain 0 < z < L, 0 <= r < R; the
@@ -993,14 +1007,19 @@ static int wall_of(const orc_state *st, double r, double z) {
 
 /*
  * First push in the local X-Y frame and rotation back to r-theta
- * (Sec. 2.3, Eqs. (4)-(5)).  READING: a_theta = 0 (the record has no
- * a_theta and its accumulation is ignored, Sec. 2.3), so v_y' = v_theta;
- * the rotated a_theta' is dropped.  At r' = 0, cos = 1 and sin = 0.
+ * (Sec. 2.3, Eqs. (4)-(5)).  Local pusher, READING: a_theta = 0 (the record
+ * has no a_theta and its accumulation is ignored, Sec. 2.3), so
+ * v_y' = v_theta and the rotated a_theta' is dropped.  X-Y-Z pusher (Sec.
+ * 2.3, end), READING: the Cartesian push of a particle taken at azimuth 0
+ * (the field is axisymmetric, so the azimuth itself never matters):
+ * v_y' = v_theta + a_theta dt / 2, and both (v_x, v_y) and (a_r, a_theta)
+ * rotate onto the new local frame.  At r' = 0, cos = 1 and sin = 0.
  */
 static void first_push(const orc_state *st, orc_p *q) {
     double dt = st->c.dt;
+    const int xyz = st->c.pusher == 1;
     double vx = q->vr + 0.5 * q->ar * dt;
-    double vy = q->vt;
+    double vy = xyz ? q->vt + 0.5 * q->at * dt : q->vt;
     double vz = q->vz + 0.5 * q->az * dt;
     double x = q->r + vx * dt;
     double y = vy * dt;
@@ -1016,7 +1035,13 @@ static void first_push(const orc_state *st, orc_p *q) {
     q->vr = vx * c + vy * s;
     q->vt = -vx * s + vy * c;
     q->vz = vz;
-    q->ar = q->ar * c;
+    if (xyz) {
+        double ar = q->ar * c + q->at * s;
+        q->at = -q->ar * s + q->at * c;
+        q->ar = ar;
+    } else {
+        q->ar = q->ar * c;
+    }
     /* a_z unchanged */
 }
 
@@ -1171,6 +1196,7 @@ static void collide(orc_state *st, int s, uint64_t id, orc_p *q, uint32_t step) 
         double fac = (st->c.q[1] * st->c.m[0]) / (st->c.q[0] * st->c.m[1]);
         ion.ar = q->ar * fac;
         ion.az = q->az * fac;
+        ion.at = q->at * fac;
         newborn(st, 0, s, id, 0, e2);
         newborn(st, 1, s, id, 1, ion);
     }
@@ -1231,7 +1257,7 @@ void orc_particle_pass(orc_state *st) {
         double qm = st->c.q[s] / st->c.m[s];
         int64_t out = 0;
         for (int64_t k = 0; k < P->n; ++k) {
-            orc_p q = {P->r[k], P->z[k], P->vr[k], P->vt[k], P->vz[k], P->ar[k], P->az[k], P->w[k]};
+            orc_p q = {P->r[k], P->z[k], P->vr[k], P->vt[k], P->vz[k], P->ar[k], P->az[k], P->w[k], P->at[k]};
             uint64_t id = P->id[k];
             /* gather E at x~ (Sec. 2.4, same weights as the deposit) */
             int i = cell_z(st, q.z), j = cell_r(st, q.r);
@@ -1250,11 +1276,21 @@ void orc_particle_pass(orc_state *st) {
             q.vr = q.vr + 0.5 * qm * Er * dt;
             q.az = 0.5 * (qm * Ez + q.az);
             q.ar = 0.5 * (qm * Er + q.ar);
-            /* axis crossing: absolute values in r (Sec. 2.3) */
+            q.at = 0.5 * q.at; /* no E_theta */
             if (q.r < 0.0) {
                 q.r = -q.r;
-                q.vr = fabs(q.vr);
-                q.ar = fabs(q.ar);
+                if (st->c.pusher == 1) {
+                    /* X-Y-Z: through the axis to the opposite azimuth, whose
+                     * local r and theta directions are the reversed ones */
+                    q.vr = -q.vr;
+                    q.ar = -q.ar;
+                    q.vt = -q.vt;
+                    q.at = -q.at;
+                } else {
+                    /* axis crossing: absolute values in r (Sec. 2.3) */
+                    q.vr = fabs(q.vr);
+                    q.ar = fabs(q.ar);
+                }
             }
             int wall = wall_of(st, q.r, q.z);
             if (wall >= 0) {
@@ -1281,6 +1317,7 @@ void orc_particle_pass(orc_state *st) {
             P->vz[out] = q.vz;
             P->ar[out] = q.ar;
             P->az[out] = q.az;
+            P->at[out] = q.at;
             P->w[out] = q.w;
             P->id[out] = id;
             ++out;
@@ -1300,6 +1337,7 @@ void orc_particle_pass(orc_state *st) {
         P->vt[o] = b->vt;
         P->vz[o] = b->vz;
         P->ar[o] = b->ar;
+        P->at[o] = b->at;
         P->az[o] = b->az;
         P->w[o] = b->w;
         P->id[o] = st->next_id[b->ts]++;

@@ -88,12 +88,18 @@ typedef struct {
     /* external circuit (Sec. 2.5, end): blocking capacitor (F) between the
      * rf source and the z = 0 electrode; 0 drives the electrode directly */
     double circuit_C;
+    /* pusher (Sec. 2.3): 0 the local X-Y frame with a_theta dropped, 1 the
+     * global X-Y-Z form (a_theta carried) */
+    int32_t pusher;
 } orc_config;
 
 typedef struct orc_state orc_state;
 
 /* lifetime */
 orc_state *orc_create(const orc_config *cfg, int64_t capacity);
+/* a_theta of species s (X-Y-Z pusher; zero otherwise and for set/loaded particles) */
+void orc_get_at(const orc_state *st, int s, double *at);
+void orc_set_at(orc_state *st, int s, const double *at);
 void orc_destroy(orc_state *st);
 
 /* Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) */
