@@ -41,6 +41,9 @@ typedef enum pic_status {
 enum { PIC_FP64 = 0, PIC_MIXED = 1 };
 enum { PIC_WEIGHT_ZR2 = 0, PIC_WEIGHT_ZR = 1 };
 enum { PIC_CHI_MAX = 0, PIC_CHI_MEAN = 1 };
+/* pusher (Sec. 2.3): the local X-Y frame with a_theta dropped (the paper's
+ * choice for its 2D runs), or the global X-Y-Z form, which carries a_theta */
+enum { PIC_PUSH_LOCAL = 0, PIC_PUSH_XYZ = 1 };
 enum { PIC_SCATTER_VS = 0, PIC_SCATTER_ISOTROPIC = 1 };
 enum { PIC_XS_ELASTIC = 0, PIC_XS_EXCITE = 1, PIC_XS_IONIZE = 2, PIC_XS_CX = 3 };
 
@@ -132,6 +135,7 @@ typedef struct pic_config {
      * between the rf source and the z = 0 electrode, solved by Vahedi's
      * superposition each step; 0 drives the electrode directly */
     double circuit_C;
+    int32_t pusher;       /* PIC_PUSH_LOCAL or PIC_PUSH_XYZ (Sec. 2.3)          */
 } pic_config;
 
 typedef struct pic_handle pic_handle;
@@ -139,12 +143,14 @@ typedef struct pic_batch pic_batch;
 
 /* Host particle arrays, absolute coordinates, FP64.  cell (nullable) is
  * filled by pic_get_particles with the stored cell index j (nz-1) + i and
- * ignored by pic_set_particles. */
+ * ignored by pic_set_particles.  at (nullable): a_theta, carried by the
+ * X-Y-Z pusher only (zero for the local pusher; NULL on set: zeros). */
 typedef struct pic_particles_view {
     int64_t n;
     double *r, *z, *vr, *vt, *vz, *ar, *az, *w;
     uint64_t *id;
     int32_t *cell;
+    double *at;
 } pic_particles_view;
 
 typedef struct pic_solve_info {

@@ -151,7 +151,10 @@ template <typename T>
 __device__ void emit_birth(const StepArgs<T> &a, BlockTally *bt, int ts, int ps, uint64_t pid,
                            int k, PS<T> q) {
     atomicAdd(&bt->cnt[PIC_C_BIRTHS + ts], 1ull);
-    first_push(a, q);
+    if (a.xyz)
+        first_push_xyz(a, q);
+    else
+        first_push(a, q);
     const int wall = wall_of(q.i, q.oz, q.j, a.nz, a.nr);
     if (wall >= 0) {
         atomicAdd(&bt->cnt[PIC_C_ABS + ts * 3 + wall], 1ull);
@@ -167,6 +170,7 @@ __device__ void emit_birth(const StepArgs<T> &a, BlockTally *bt, int ts, int ps,
     const int cell = q.j * a.ncz + q.i;
     atomicAdd(a.counts[ts] + cell, 1);
     store_p(a.births[ts], slot, q, cell, 0ull);
+    if (a.xyz) a.births[ts].at[slot] = q.at;
     a.bkey[ts][slot] = ((uint64_t)ps << 63) | (pid << 16) | (uint64_t)k;
 }
 
@@ -296,6 +300,7 @@ __device__ __forceinline__ void scatter(const StepArgs<T> &a, BlockTally *bt, ui
         ion.vz = a.v_gas * n2;
         ion.ar = p.ar * a.ion_acc;
         ion.az = p.az * a.ion_acc;
+        ion.at = a.xyz ? p.at * a.ion_acc : (T)0;
         emit_birth(a, bt, 0, a.s, id, 0, e2);
         emit_birth(a, bt, 1, a.s, id, 1, ion);
     }
@@ -346,7 +351,8 @@ constexpr int kEedfCopies = 8;
 // PF: the chunk's particles come into shared memory by cp.async a chunk at
 // a time, ahead of their use (for latency-bound passes)
 // PPT: particles per thread in a chunk (kThreads * PPT particles)
-template <typename T, bool PF, int kPPT>
+// XYZ: the global X-Y-Z pusher (a_theta carried; a.xyz set)
+template <typename T, bool PF, int kPPT, bool XYZ>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepArgs<T> a) {
     constexpr int kChunk = kThreads * kPPT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -357,7 +363,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     V *st_q1 = st_q0 + kChunk;
     uint64_t *st_id = reinterpret_cast<uint64_t *>(st_q1 + kChunk);
     int32_t *st_cell = reinterpret_cast<int32_t *>(st_id + kChunk);
-    T *s_eedf = PF ? reinterpret_cast<T *>(st_cell + kChunk) : reinterpret_cast<T *>(smem_raw);
+    T *st_at = reinterpret_cast<T *>(st_cell + kChunk);  // PF and XYZ
+    T *s_eedf = PF ? (XYZ ? st_at + kChunk : reinterpret_cast<T *>(st_cell + kChunk))
+                   : reinterpret_cast<T *>(smem_raw);
     __shared__ BlockTally bt;
     const int tid = threadIdx.x, lane = tid & 31;
     if (a.ctl->halt) return;  // an earlier failure of this step
@@ -404,6 +412,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                     }
                     cpa8(st_id + slot, src.id + si);
                     cpa4(st_cell + slot, src.cell + si);
+                    if (XYZ) {
+                        if (sizeof(T) == 8)
+                            cpa8(st_at + slot, src.at + si);
+                        else
+                            cpa4(st_at + slot, src.at + si);
+                    }
                 }
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
@@ -430,6 +444,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                     ld4(st_q1 + slot, p.vz, p.ar, p.az, p.w);
                     decode_cell(st_cell[slot], a.ncz, a.inv_ncz, p.i, p.j);
                     id = st_id[slot];
+                    if (XYZ) p.at = st_at[slot];
                 } else {
                     const int pidx = a.perm[k];
                     const bool from_main = pidx < nmain;
@@ -437,7 +452,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                     const int si = from_main ? pidx : pidx - nmain;
                     p = load_p_fast(src, si, a.ncz, a.inv_ncz);
                     id = src.id[si];
+                    if (XYZ) p.at = src.at[si];
                 }
+                // a stored cell outside the mesh (never written by a pass)
+                // is reported and the record dropped, never followed
+                const bool in_mesh = (unsigned)p.i < (unsigned)a.ncz && (unsigned)p.j < (unsigned)a.ncr;
+                if (!in_mesh) p.i = p.j = 0;
                 // gather E at x~ with the deposit's shape factors (Sec. 2.4)
                 T s0, s1;
                 shape_r(a.weighting, p.j, p.orr, s0, s1);
@@ -467,14 +487,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                 p.vr += a.kv * Er;
                 p.az = (T)0.5 * (a.ka * Ez + p.az);
                 p.ar = (T)0.5 * (a.ka * Er + p.ar);
+                if (XYZ) p.at = (T)0.5 * p.at;  // no E_theta
                 if (axis) {
-                    p.vr = m_abs(p.vr);
-                    p.ar = m_abs(p.ar);
+                    if (XYZ) {  // through the axis to the opposite azimuth
+                        p.vr = -p.vr;
+                        p.ar = -p.ar;
+                        p.vt = -p.vt;
+                        p.at = -p.at;
+                    } else {  // |v_r|, |a_r| (Sec. 2.3)
+                        p.vr = m_abs(p.vr);
+                        p.ar = m_abs(p.ar);
+                    }
                 }
                 bool alive = true;
                 // one test for all: a NaN or infinity anywhere makes the sum
                 // non-finite (the values are far below overflow)
-                if (!m_finite(p.oz + p.orr + p.vr + p.vt + p.vz + p.w)) {
+                if (!in_mesh || !m_finite(p.oz + p.orr + p.vr + p.vt + p.vz + p.w)) {
                     atomicOr(&a.ds->status, ST_NAN);
                     alive = false;
                 }
@@ -512,7 +540,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                             }
                         }
                     }
-                    first_push(a, p);
+                    if (XYZ)
+                        first_push_xyz(a, p);
+                    else
+                        first_push(a, p);
                     wall = wall_of(p.i, p.oz, p.j, a.nz, a.nr);
                     if (wall >= 0) {
                         atomicAdd(&bt.cnt[PIC_C_ABS + a.s * 3 + wall], 1ull);
@@ -532,6 +563,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                     c11 = p.w * y1 * r1;
                 }
                 store_p(a.dst_main, k, p, out_cell, id);
+                if (XYZ) a.dst_main.at[k] = p.at;
             }
             // runs of lanes with one output cell: sum each run into its first
             // lane, which makes the four deposit reductions and the histogram count
@@ -580,15 +612,27 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
         }
 }
 
-template <typename T, bool PF, int PPT>
-void launch_variant(const StepArgs<T> &a, int grid, cudaStream_t st) {
+template <typename T, bool PF, int PPT, bool XYZ>
+void launch_shape(const StepArgs<T> &a, int grid, cudaStream_t st) {
     const size_t stage =
-        PF ? (size_t)kThreads * PPT * (2 * sizeof(typename V4<T>::type) + sizeof(uint64_t) + sizeof(int32_t)) : 0;
+        PF ? (size_t)kThreads * PPT *
+                 (2 * sizeof(typename V4<T>::type) + sizeof(uint64_t) + sizeof(int32_t) + (XYZ ? sizeof(T) : 0))
+           : 0;
     const size_t eedf = (size_t)(a.eedf ? a.eedf_bins : 0) * kEedfCopies * sizeof(T);
     const size_t smem = stage + eedf;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_step<T, PF, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_step<T, PF, PPT><<<grid, kThreads, smem, st>>>(a);
+    // dynamic plus static shared memory above 48 KB needs the opt-in: set
+    // it for every size (the static tallies come on top of `smem`)
+    if (smem > 0)
+        cudaFuncSetAttribute(k_step<T, PF, PPT, XYZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_step<T, PF, PPT, XYZ><<<grid, kThreads, smem, st>>>(a);
+}
+
+template <typename T, bool PF, int PPT>
+void launch_variant(const StepArgs<T> &a, int grid, cudaStream_t st) {
+    if (a.xyz)
+        launch_shape<T, PF, PPT, true>(a, grid, st);
+    else
+        launch_shape<T, PF, PPT, false>(a, grid, st);
 }
 
 // variant: bit 0 = prefetch the chunk into shared memory, bit 1 = 8
@@ -644,6 +688,7 @@ __global__ void k_load(PBuf<T> dst, int64_t n, int s, int nz, int nr, double dz,
     q.ar = q.az = (T)0;
     q.w = (T)w;
     store_p(dst, (int)p, q, (int)c, (uint64_t)p);
+    if (dst.at) dst.at[p] = (T)0;
 }
 
 template <typename T>
@@ -678,8 +723,8 @@ void launch_deposit(PBuf<T> src, const int32_t *n_dev, int nz, int nr, int weigh
 template <typename T>
 __global__ void k_from_abs(PBuf<T> dst, int64_t n, const double *r, const double *z,
                            const double *vr, const double *vt, const double *vz, const double *ar,
-                           const double *az, const double *w, const uint64_t *id, int nz, int nr,
-                           double dz, double dr) {
+                           const double *az, const double *w, const uint64_t *id, const double *at,
+                           int nz, int nr, double dz, double dr) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const double xz = z[k] / dz, xr = r[k] / dr;
@@ -699,24 +744,25 @@ __global__ void k_from_abs(PBuf<T> dst, int64_t n, const double *r, const double
     q.az = (T)az[k];
     q.w = (T)w[k];
     store_p(dst, (int)k, q, j * (nz - 1) + i, id[k]);
+    if (dst.at) dst.at[k] = at ? (T)at[k] : (T)0;
 }
 
 template <typename T>
 void launch_from_abs(PBuf<T> dst, int64_t n, const double *r, const double *z, const double *vr,
                      const double *vt, const double *vz, const double *ar, const double *az,
-                     const double *w, const uint64_t *id, int nz, int nr, double dz, double dr,
-                     cudaStream_t st) {
+                     const double *w, const uint64_t *id, const double *at, int nz, int nr, double dz,
+                     double dr, cudaStream_t st) {
     if (n <= 0) return;
     k_from_abs<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, n, r, z, vr, vt, vz, ar, az, w,
-                                                                id, nz, nr, dz, dr);
+                                                                id, at, nz, nr, dz, dr);
 }
 
 // cell + offsets -> absolute, in perm order
 template <typename T>
 __global__ void k_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, const int32_t *perm,
                          int64_t n, double *r, double *z, double *vr, double *vt, double *vz,
-                         double *ar, double *az, double *w, uint64_t *id, int32_t *cell, int nz,
-                         double dz, double dr) {
+                         double *ar, double *az, double *w, uint64_t *id, int32_t *cell, double *at,
+                         int nz, double dz, double dr) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int nmain = *n_main_src;
@@ -734,16 +780,17 @@ __global__ void k_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, cons
     w[k] = q.w;
     id[k] = src.id[si];
     cell[k] = src.cell[si];
+    if (at) at[k] = src.at ? (double)src.at[si] : 0.0;
 }
 
 template <typename T>
 void launch_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, const int32_t *perm,
                    int64_t n, double *r, double *z, double *vr, double *vt, double *vz, double *ar,
-                   double *az, double *w, uint64_t *id, int32_t *cell, int nz, double dz, double dr,
-                   cudaStream_t st) {
+                   double *az, double *w, uint64_t *id, int32_t *cell, double *at, int nz, double dz,
+                   double dr, cudaStream_t st) {
     if (n <= 0) return;
     k_to_abs<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sm, sb, n_main_src, perm, n, r, z, vr,
-                                                              vt, vz, ar, az, w, id, cell, nz, dz,
+                                                              vt, vz, ar, az, w, id, cell, at, nz, dz,
                                                               dr);
 }
 
@@ -756,11 +803,12 @@ void launch_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, const int3
     template void launch_from_abs<T>(PBuf<T>, int64_t, const double *, const double *,          \
                                      const double *, const double *, const double *,            \
                                      const double *, const double *, const double *,            \
-                                     const uint64_t *, int, int, double, double, cudaStream_t);  \
+                                     const uint64_t *, const double *, int, int, double, double, \
+                                     cudaStream_t);                                              \
     template void launch_to_abs<T>(PBuf<T>, PBuf<T>, const int32_t *, const int32_t *, int64_t,  \
                                    double *, double *, double *, double *, double *, double *,   \
-                                   double *, double *, uint64_t *, int32_t *, int, double,       \
-                                   double, cudaStream_t);
+                                   double *, double *, uint64_t *, int32_t *, double *, int,     \
+                                   double, double, cudaStream_t);
 PIC_INST(float)
 PIC_INST(double)
 

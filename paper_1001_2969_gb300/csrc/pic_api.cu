@@ -26,6 +26,7 @@ struct RawBuf {
     void *q0 = nullptr, *q1 = nullptr;
     int32_t *cell = nullptr;
     uint64_t *id = nullptr;
+    void *at = nullptr;  // a_theta (X-Y-Z pusher only)
 };
 
 template <typename T>
@@ -35,6 +36,7 @@ PBuf<T> view(const RawBuf &b) {
     p.q1 = reinterpret_cast<typename V4<T>::type *>(b.q1);
     p.cell = b.cell;
     p.id = b.id;
+    p.at = reinterpret_cast<T *>(b.at);
     return p;
 }
 
@@ -220,6 +222,7 @@ pic_status validate(const pic_config *c, std::string &why) {
     if (c->scatter != PIC_SCATTER_VS && c->scatter != PIC_SCATTER_ISOTROPIC) return bad("scatter");
     if (c->split_every < 0) return bad("split_every must be >= 0");
     if (c->mg_max_cycles < 1) return bad("mg_max_cycles must be >= 1");
+    if (c->pusher != PIC_PUSH_LOCAL && c->pusher != PIC_PUSH_XYZ) return bad("pusher must be PIC_PUSH_LOCAL or PIC_PUSH_XYZ");
     if (!(c->circuit_C >= 0.0) || !std::isfinite(c->circuit_C))
         return bad("circuit_C must be finite and >= 0 (0: the electrode follows the source)");
     if (c->eedf_bins < 0 || c->eedf_bins > 4096) return bad("eedf_bins must be in [0, 4096]");
@@ -454,6 +457,7 @@ void alloc_rawbuf(pic_handle *h, RawBuf &b, int64_t n, size_t tsize) {
     b.q1 = dalloc(h, (size_t)n * 4 * tsize);
     b.cell = (int32_t *)dalloc(h, (size_t)n * sizeof(int32_t));
     b.id = (uint64_t *)dalloc(h, (size_t)n * sizeof(uint64_t));
+    if (h->cfg.pusher == PIC_PUSH_XYZ) b.at = dalloc(h, (size_t)n * tsize);
 }
 
 void setup_device(pic_handle *h) {
@@ -634,6 +638,7 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     a.qch[1] = h->cfg.sp[1].q;
     a.weighting = h->cfg.weighting;
     a.scatter = h->cfg.scatter;
+    a.xyz = h->cfg.pusher == PIC_PUSH_XYZ ? 1 : 0;
     a.kz = (T)(0.5 * qm * dt * dt / h->dz);
     a.kr = (T)(0.5 * qm * dt * dt / h->dr);
     a.kv = (T)(0.5 * qm * dt);
@@ -708,7 +713,7 @@ void sort_branch(pic_handle *h, int par, cudaStream_t st) {
     for (int s = 0; s < 2; ++s) {
         SpecDev &d = h->sp[s];
         launch_rank<T>(view<T>(d.main[par]), d.d_nmain[par], view<T>(d.births[par]), d.d_nbirths[par],
-                       d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->sctl, st);
+                       d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->sctl, h->ncell, st);
     }
     h->launches += 9;
 }
@@ -983,9 +988,14 @@ pic_status set_particles_t(pic_handle *h, int s, const pic_particles_view *v) {
         cudaMemcpyAsync(stage + (size_t)f * n, srcs[f], (size_t)n * sizeof(double),
                         cudaMemcpyHostToDevice, h->st);
     if (n > 0) cudaMemcpyAsync(sid, v->id, (size_t)n * sizeof(uint64_t), cudaMemcpyHostToDevice, h->st);
+    double *sat = nullptr;
+    if (n > 0 && v->at && h->cfg.pusher == PIC_PUSH_XYZ) {
+        sat = (double *)dalloc(h, (size_t)n * sizeof(double));
+        cudaMemcpyAsync(sat, v->at, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->st);
+    }
     const int c = h->cur;
     launch_from_abs<T>(view<T>(d.main[c]), n, stage, stage + n, stage + 2 * n, stage + 3 * n,
-                       stage + 4 * n, stage + 5 * n, stage + 6 * n, stage + 7 * n, sid, h->nz, h->nr,
+                       stage + 4 * n, stage + 5 * n, stage + 6 * n, stage + 7 * n, sid, sat, h->nz, h->nr,
                        h->dz, h->dr, h->st);
     const int32_t nn = (int32_t)n, zero = 0;
     cudaMemcpyAsync(d.d_nmain[c], &nn, 4, cudaMemcpyHostToDevice, h->st);
@@ -994,7 +1004,7 @@ pic_status set_particles_t(pic_handle *h, int s, const pic_particles_view *v) {
     launch_hist<T>(view<T>(d.main[c]), d.d_nmain[c], d.counts, h->st);
     launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, nullptr, h->st);
     launch_rank<T>(view<T>(d.main[c]), d.d_nmain[c], view<T>(d.births[c]), d.d_nbirths[c],
-                   d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, nullptr, h->st);
+                   d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, nullptr, h->ncell, h->st);
     cudaMemcpyAsync(d.d_nalive, d.d_ntotal, 4, cudaMemcpyDeviceToDevice, h->st);
     h->launches += 6;
     d.next_id = mx;
@@ -1002,6 +1012,7 @@ pic_status set_particles_t(pic_handle *h, int s, const pic_particles_view *v) {
     cudaStreamSynchronize(h->st);
     if (stage) release(h, stage);
     if (sid) release(h, sid);
+    if (sat) release(h, sat);
     push_ctl(h);
     return cuda_check(h, "set_particles");
 }
@@ -1018,10 +1029,12 @@ pic_status get_particles_t(pic_handle *h, int s, pic_particles_view *v, int64_t 
     double *stage = (double *)dalloc(h, (size_t)n * 8 * sizeof(double));
     uint64_t *sid = (uint64_t *)dalloc(h, (size_t)n * sizeof(uint64_t));
     int32_t *scell = (int32_t *)dalloc(h, (size_t)n * sizeof(int32_t));
+    double *sat = v->at ? (double *)dalloc(h, (size_t)n * sizeof(double)) : nullptr;
     const int c = h->cur;
     launch_to_abs<T>(view<T>(d.main[c]), view<T>(d.births[c]), d.d_nmain[c], d.perm, n, stage + n,
                      stage, stage + 2 * n, stage + 3 * n, stage + 4 * n, stage + 5 * n,
-                     stage + 6 * n, stage + 7 * n, sid, scell, h->nz, h->dz, h->dr, h->st);
+                     stage + 6 * n, stage + 7 * n, sid, scell, sat, h->nz, h->dz, h->dr, h->st);
+    if (sat) cudaMemcpyAsync(v->at, sat, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     h->launches += 1;
     double *dsts[8] = {v->z, v->r, v->vr, v->vt, v->vz, v->ar, v->az, v->w};
     for (int f = 0; f < 8; ++f)
@@ -1035,6 +1048,7 @@ pic_status get_particles_t(pic_handle *h, int s, pic_particles_view *v, int64_t 
     release(h, stage);
     release(h, sid);
     release(h, scell);
+    if (sat) release(h, sat);
     return cuda_check(h, "get_particles");
 }
 
@@ -1634,6 +1648,7 @@ pic_status pic_window(pic_handle *h, int32_t nsteps, int32_t ckpt, const double 
                       const double *phi_zL, int32_t grad, double *J, double *dJ_damp, double *dJ_dphi_zL) {
     if (!h || !w || nsteps < 1 || ckpt < 1) return fail(h, PIC_ERR_ARG, "bad window arguments");
     if (h->cfg.rf.n < 1) return fail(h, PIC_ERR_ARG, "the window needs an rf component");
+    if (h->cfg.pusher != PIC_PUSH_LOCAL) return fail(h, PIC_ERR_ARG, "the window takes the local pusher");
     return h->mixed ? window_t<float>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL)
                     : window_t<double>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL);
 }
@@ -1645,7 +1660,8 @@ pic_status pic_save(pic_handle *h, const char *path) {
     FILE *f = fopen(path, "wb");
     if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint for writing");
     const int circuit = h->cfg.circuit_C > 0.0 ? 1 : 0;
-    int64_t hdr[8] = {(int64_t)kCkptMagic, h->nz, h->nr, h->step, h->mixed ? 1 : 0, circuit, 0, 0};
+    const int xyz = h->cfg.pusher == PIC_PUSH_XYZ ? 1 : 0;
+    int64_t hdr[8] = {(int64_t)kCkptMagic, h->nz, h->nr, h->step, h->mixed ? 1 : 0, circuit, xyz, 0};
     uint64_t ids[2] = {h->sp[0].next_id, h->sp[1].next_id};
     fwrite(hdr, sizeof(hdr), 1, f);
     fwrite(ids, sizeof(ids), 1, f);
@@ -1660,7 +1676,7 @@ pic_status pic_save(pic_handle *h, const char *path) {
         int32_t n32 = 0;
         cudaMemcpy(&n32, h->sp[s].d_nalive, 4, cudaMemcpyDeviceToHost);
         n = n32;
-        std::vector<double> a((size_t)std::max<int64_t>(n, 1) * 8);
+        std::vector<double> a((size_t)std::max<int64_t>(n, 1) * 9);
         std::vector<uint64_t> id((size_t)std::max<int64_t>(n, 1));
         pic_particles_view v;
         v.n = n;
@@ -1674,10 +1690,12 @@ pic_status pic_save(pic_handle *h, const char *path) {
         v.w = a.data() + 7 * n;
         v.id = id.data();
         v.cell = nullptr;
+        v.at = xyz ? a.data() + 8 * n : nullptr;
         st = pic_get_particles(h, s, &v, n);
         fwrite(&n, 8, 1, f);
         fwrite(a.data(), 8, (size_t)n * 8, f);
         fwrite(id.data(), 8, (size_t)n, f);
+        if (xyz) fwrite(a.data() + 8 * n, 8, (size_t)n, f);
     }
     if (circuit && st == PIC_OK) {
         // circuit state, the charge collected since the last circuit solve,
@@ -1702,8 +1720,9 @@ pic_status pic_load(pic_handle *h, const char *path) {
     int64_t hdr[8];
     uint64_t ids[2];
     const int circuit = h->cfg.circuit_C > 0.0 ? 1 : 0;
+    const int xyz = h->cfg.pusher == PIC_PUSH_XYZ ? 1 : 0;
     if (fread(hdr, sizeof(hdr), 1, f) != 1 || (uint64_t)hdr[0] != kCkptMagic || hdr[1] != h->nz ||
-        hdr[2] != h->nr || hdr[5] != circuit || fread(ids, sizeof(ids), 1, f) != 1) {
+        hdr[2] != h->nr || hdr[5] != circuit || hdr[6] != xyz || fread(ids, sizeof(ids), 1, f) != 1) {
         fclose(f);
         return fail(h, PIC_ERR_ARG, "checkpoint does not match this handle");
     }
@@ -1717,9 +1736,10 @@ pic_status pic_load(pic_handle *h, const char *path) {
             st = fail(h, PIC_ERR_ARG, "bad particle count in checkpoint");
             break;
         }
-        std::vector<double> a((size_t)std::max<int64_t>(n, 1) * 8);
+        std::vector<double> a((size_t)std::max<int64_t>(n, 1) * 9);
         std::vector<uint64_t> id((size_t)std::max<int64_t>(n, 1));
-        if (fread(a.data(), 8, (size_t)n * 8, f) != (size_t)n * 8 || fread(id.data(), 8, (size_t)n, f) != (size_t)n) {
+        if (fread(a.data(), 8, (size_t)n * 8, f) != (size_t)n * 8 || fread(id.data(), 8, (size_t)n, f) != (size_t)n ||
+            (xyz && fread(a.data() + 8 * n, 8, (size_t)n, f) != (size_t)n)) {
             st = fail(h, PIC_ERR_ARG, "truncated checkpoint");
             break;
         }
@@ -1735,6 +1755,7 @@ pic_status pic_load(pic_handle *h, const char *path) {
         v.w = a.data() + 7 * n;
         v.id = id.data();
         v.cell = nullptr;
+        v.at = xyz ? a.data() + 8 * n : nullptr;
         st = pic_set_particles(h, s, &v);
     }
     double cs[6] = {0, 0, 0, 0, 0, 0};

@@ -149,6 +149,7 @@ struct PBuf {
     typename V4<T>::type *q1;
     int32_t *cell;
     uint64_t *id;
+    T *at;  // a_theta (X-Y-Z pusher), null otherwise
 };
 
 // device-side scalars of one handle
@@ -188,6 +189,7 @@ struct StepArgs {
     double qch[2];  // species charges (absorbed-charge tallies)
     int weighting;  // PIC_WEIGHT_*
     int scatter;    // PIC_SCATTER_*
+    int xyz;        // the X-Y-Z pusher (a_theta carried)
     // final push: offsets/velocities/accelerations change per unit E
     T kz, kr, kv, ka;
     // first push
@@ -242,13 +244,13 @@ void launch_deposit(PBuf<T> src, const int32_t *n_dev, int nz, int nr, int weigh
 template <typename T>
 void launch_from_abs(PBuf<T> dst, int64_t n, const double *r, const double *z, const double *vr,
                      const double *vt, const double *vz, const double *ar, const double *az,
-                     const double *w, const uint64_t *id, int nz, int nr, double dz, double dr,
-                     cudaStream_t st);
+                     const double *w, const uint64_t *id, const double *at, int nz, int nr, double dz,
+                     double dr, cudaStream_t st);
 template <typename T>
 void launch_to_abs(PBuf<T> src_main, PBuf<T> src_births, const int32_t *n_main_src,
                    const int32_t *perm, int64_t n, double *r, double *z, double *vr, double *vt,
                    double *vz, double *ar, double *az, double *w, uint64_t *id, int32_t *cell,
-                   int nz, double dz, double dr, cudaStream_t st);
+                   double *at, int nz, double dz, double dr, cudaStream_t st);
 
 // ---- launchers (sortk.cu) ----
 template <typename T>
@@ -262,7 +264,7 @@ void launch_step_check(const DevScalars *ds, StepCtl *ctl, cudaStream_t st);
 template <typename T>
 void launch_rank(PBuf<T> main, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,
                  int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
-                 const int32_t *status, const StepCtl *ctl, cudaStream_t st);
+                 const int32_t *status, const StepCtl *ctl, int ncell, cudaStream_t st);
 // births of species s get ids next_id[s] + rank of their key among the
 // *nb births (one cooperative launch; next_id[s] advances by *nb)
 struct RadixTmp {

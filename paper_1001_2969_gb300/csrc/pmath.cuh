@@ -76,6 +76,7 @@ template <typename T>
 struct PS {
     int i, j;
     T oz, orr, vr, vt, vz, ar, az, w;
+    T at;  // a_theta: read and written by the X-Y-Z pusher only
 };
 
 // c = j ncz + i -> (i, j) without an integer division: (c + 1/2)/ncz lies
@@ -203,6 +204,53 @@ __device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p) {
     p.vt = -vx * sn + vy * c;
     p.vz = vz;
     p.ar = p.ar * c;
+}
+
+// the same in the global X-Y-Z form (Sec. 2.3, end) for a particle taken at
+// azimuth 0 (the field is axisymmetric): v_y' = v_theta + a_theta dt / 2,
+// and (a_r, a_theta) rotate onto the new local frame with (v_x, v_y)
+template <typename T>
+__device__ __forceinline__ void first_push_xyz(const StepArgs<T> &a, PS<T> &p) {
+    const T vx = p.vr + (T)0.5 * p.ar * a.dt;
+    const T vy = p.vt + (T)0.5 * p.at * a.dt;
+    const T vz = p.vz + (T)0.5 * p.az * a.dt;
+    p.oz += vz * a.dt_dz;
+    carry(p.oz, p.i);
+    const T r = ((T)p.j + p.orr) * a.dr;
+    const T dx = vx * a.dt, dy = vy * a.dt;
+    const T xr = r + dx;
+    const T q2 = xr * xr + dy * dy;
+    T c = (T)1, sn = (T)0, rn = (T)0;
+    if (q2 > (T)0) {
+        if (sizeof(T) == 4) {
+            const T inv = m_rsqrt(q2);
+            rn = q2 * inv;
+            c = xr * inv;
+            sn = dy * inv;
+        } else {
+            rn = m_sqrt(q2);
+            c = xr / rn;
+            sn = dy / rn;
+        }
+    }
+    const T den = rn + r;
+    const T drr = den > (T)0 ? m_div((T)2 * r * dx + dx * dx + dy * dy, den) : (T)0;
+    T ro = p.orr + drr * a.inv_dr;
+    const T fl = m_floor(ro);
+    int jn = p.j + (int)fl;
+    ro -= fl;
+    if (jn < 0) {
+        jn = 0;
+        ro = (T)0;
+    }
+    p.j = jn;
+    p.orr = ro;
+    p.vr = vx * c + vy * sn;
+    p.vt = -vx * sn + vy * c;
+    p.vz = vz;
+    const T arn = p.ar * c + p.at * sn;
+    p.at = -p.ar * sn + p.at * c;
+    p.ar = arn;
 }
 
 }  // namespace pic

@@ -138,7 +138,8 @@ void launch_step_check(const DevScalars *ds, StepCtl *ctl, cudaStream_t st) {
 template <typename T>
 __global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
                        const int32_t *n_births_dev, int32_t *cursor, int32_t *perm,
-                       const int32_t *n_alive, int64_t cap, const int32_t *status, const StepCtl *ctl) {
+                       const int32_t *n_alive, int64_t cap, const int32_t *status, const StepCtl *ctl,
+                       int ncell) {
     // a failed step keeps the previous permutation
     if (sort_skip(ctl) || (int64_t)*n_alive > cap || (*status & (ST_CAPACITY | ST_BIRTH_OVERFLOW))) return;
     const int nm = *n_main_dev, nb = *n_births_dev;
@@ -151,6 +152,7 @@ __global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
             c = mainb.cell[e];
         else if (e < total)
             c = births.cell[e - nm];
+        if (c >= ncell) c = -1;  // never a cell of the mesh: no place is taken for it
         // the input is in (old) cell order, so equal cells sit in runs of
         // lanes: the first lane of a run reserves places for the whole run
         const int cprev = __shfl_up_sync(0xffffffffu, c, 1);
@@ -162,18 +164,20 @@ __global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
         int pos = 0;
         if (c >= 0 && head) pos = atomicAdd(cursor + c, rend - lane);
         pos = __shfl_sync(0xffffffffu, pos, first);
-        if (c >= 0) perm[pos + (lane - first)] = e;
+        // (cells and counts agree, so pos < *n_alive <= cap; the bound keeps
+        // an inconsistent pass from writing past the permutation)
+        if (c >= 0 && (int64_t)pos + (lane - first) < cap) perm[pos + (lane - first)] = e;
     }
 }
 
 template <typename T>
 void launch_rank(PBuf<T> mainb, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,
                  int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
-                 const int32_t *status, const StepCtl *ctl, cudaStream_t st) {
+                 const int32_t *status, const StepCtl *ctl, int ncell, cudaStream_t st) {
     // short-lived blocks (a few tiles each): beside the field solve they
     // retire often, so the solve's blocks find SMs early
     k_rank<T><<<152 * 32, 256, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap,
-                                         status, ctl);
+                                         status, ctl, ncell);
 }
 
 // ---- newborn numbering ----
@@ -349,9 +353,9 @@ template void launch_hist<float>(PBuf<float>, const int32_t *, int32_t *, cudaSt
 template void launch_hist<double>(PBuf<double>, const int32_t *, int32_t *, cudaStream_t);
 template void launch_rank<float>(PBuf<float>, const int32_t *, PBuf<float>, const int32_t *,
                                  int32_t *, int32_t *, const int32_t *, int64_t, const int32_t *,
-                                 const StepCtl *, cudaStream_t);
+                                 const StepCtl *, int, cudaStream_t);
 template void launch_rank<double>(PBuf<double>, const int32_t *, PBuf<double>, const int32_t *,
                                   int32_t *, int32_t *, const int32_t *, int64_t, const int32_t *,
-                                  const StepCtl *, cudaStream_t);
+                                  const StepCtl *, int, cudaStream_t);
 
 }  // namespace pic

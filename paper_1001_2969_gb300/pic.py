@@ -65,12 +65,12 @@ class pic_config(C.Structure):
                 ("mg_tol", C.c_double), ("phi_zL", _dp), ("births_capacity", C.c_int64),
                 ("eedf_bins", C.c_int32), ("eedf_emax_eV", C.c_double), ("load", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p), ("circuit_C", C.c_double)]
+                ("stream", C.c_void_p), ("circuit_C", C.c_double), ("pusher", C.c_int32)]
 
 
 class pic_particles_view(C.Structure):
     _fields_ = [("n", C.c_int64), ("r", _dp), ("z", _dp), ("vr", _dp), ("vt", _dp), ("vz", _dp),
-                ("ar", _dp), ("az", _dp), ("w", _dp), ("id", _u64p), ("cell", _ip)]
+                ("ar", _dp), ("az", _dp), ("w", _dp), ("id", _u64p), ("cell", _ip), ("at", _dp)]
 
 
 class pic_solve_info(C.Structure):
@@ -246,6 +246,7 @@ def pic_init(cfg: dict, load: bool = True, stream=None, torch_memory: bool = Tru
             c.alloc, c.free = a, f
     c.stream = stream
     c.circuit_C = float(cfg.get("circuit_C", 0.0))
+    c.pusher = {"local": 0, "xyz": 1}[cfg.get("pusher", "local")]
     ptr = C.c_void_p()
     st = L.pic_init(C.byref(c), C.byref(ptr))
     if st != PIC_OK:
@@ -414,10 +415,12 @@ def pic_get_particles(h: Handle, s: int) -> dict:
     arr = {k: np.zeros(n) for k in FIELDS}
     ids = np.zeros(n, dtype=np.uint64)
     cell = np.zeros(n, dtype=np.int32)
-    v = pic_particles_view(n, *[_p(arr[k]) for k in FIELDS], _p(ids, _u64p), _p(cell, _ip))
+    at = np.zeros(n)
+    v = pic_particles_view(n, *[_p(arr[k]) for k in FIELDS], _p(ids, _u64p), _p(cell, _ip), _p(at))
     _check(h, lib().pic_get_particles(h.ptr, s, C.byref(v), n))
     arr["id"] = ids[: v.n]
     arr["cell"] = cell[: v.n]
+    arr["at"] = at[: v.n]
     for k in FIELDS:
         arr[k] = arr[k][: v.n]
     return arr
@@ -427,7 +430,9 @@ def pic_set_particles(h: Handle, s: int, p: dict) -> int:
     n = len(p["r"])
     arrs = [_d(p[k]) for k in FIELDS]
     ids = np.ascontiguousarray(p["id"], dtype=np.uint64)
-    v = pic_particles_view(n, *[_p(a) for a in arrs], _p(ids, _u64p), None)
+    at = _d(p["at"]) if p.get("at") is not None else None
+    v = pic_particles_view(n, *[_p(a) for a in arrs], _p(ids, _u64p), None,
+                           _p(at) if at is not None else None)
     return _check(h, lib().pic_set_particles(h.ptr, s, C.byref(v)))
 
 
