@@ -929,7 +929,7 @@ void mg_fast_upload(MGFast &m, cudaStream_t st) {
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
-                  bool v_from_ctl, bool setup, cudaEvent_t at_solve) {
+                  bool v_from_ctl, bool setup, cudaEvent_t at_solve, bool wide) {
     const int nz = fd.nz, nr = fd.nr, n = nr - 1, ng = nz * nr;
     const int M = line_chunk(n);
     const int nlev = m.nlev;
@@ -985,12 +985,14 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     const size_t es = mixed ? sizeof(float) : sizeof(double);
     const size_t LFE = (size_t)line_factor_elems(M);
     SolveLayout lay{};
-    // residual tiles of 4 columns over two blocks per black line: the
+    // wide: residual tiles of 4 columns over two blocks per black line: the
     // residual phase (FP64 stencil, restriction chain) runs on twice the SMs
     // the line phases need; the remaining SMs stay free for the cell sort
     // that runs beside the solve in a timestep (measured on c2: 0.551 ->
-    // 0.518 ms per solve; three blocks per line leave the sort too few SMs)
-    lay.tw = 4;
+    // 0.518 ms per solve; three blocks per line leave the sort too few SMs).
+    // Narrow (one block per black line, tiles of 8): many reactors solving
+    // side by side each take fewer SMs.
+    lay.tw = wide ? 4 : 8;
     size_t off = 0;
     auto take = [&](size_t b) {
         const size_t o = off;
@@ -1014,7 +1016,7 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
         if (launches) *launches += L;
         return kSolveNoLaunch;
     }
-    const int grid = std::max(1, std::min(nsm * per_sm, std::min(nsm, 2 * ((nz - 1) / 2))));
+    const int grid = std::max(1, std::min(nsm * per_sm, std::min(nsm, (wide ? 2 : 1) * ((nz - 1) / 2))));
     int first_cycle = 1, nrv = nr, mc = max_cycles;
     double tv = tol;
     const StepCtl *sc = sctl;

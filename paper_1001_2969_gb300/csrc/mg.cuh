@@ -64,10 +64,12 @@ void mg_fast_upload(MGFast &m, cudaStream_t st);
 // once sctl->halt is set, reports cycles, residual and failures to sctl, and
 // returns 0 (or kSolveNoLaunch).  at_solve (optional) is recorded on st just
 // before the one-launch solve, after the set-up: work that waits for it runs
-// beside the solve.
+// beside the solve.  wide: two blocks per black line (a reactor alone on the
+// GPU); else one (many reactors solving side by side).
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
-                  bool v_from_ctl = true, bool setup = true, cudaEvent_t at_solve = nullptr);
+                  bool v_from_ctl = true, bool setup = true, cudaEvent_t at_solve = nullptr,
+                  bool wide = true);
 
 }  // namespace pic

@@ -108,6 +108,7 @@ struct pic_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
     StepGraph graphs[2];
     StepGraph sort_graphs[2];  // the last pass's cell sort at the end of a call
+    bool in_batch = false;     // stepped with other reactors (pic_batch): narrow solves
     double ngas = 0.0, nu_max[2] = {0, 0}, p_null[2] = {0, 0};
     unsigned long long t_null[2] = {0, 0};
     std::string err;
@@ -762,9 +763,10 @@ void one_step(pic_handle *h, cudaStream_t sb) {
             // electrode at 1, every other boundary at 0; same operator
             mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi_P,
                           true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st,
-                          false, true, fork);
+                          false, true, fork, !h->in_batch);
             mg_fast_solve(fd, h->mgf, h->zero_grid, h->chi, 1.0, nullptr, h->phi_L, true, h->mixed,
-                          h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, false, false);
+                          h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, false, false, nullptr,
+                          !h->in_batch);
             k_circuit<<<1, 256, 0, st>>>(h->sctl, h->ds, h->mgf.cz[0], h->phi_P, h->phi_L, h->rho, h->V,
                                          h->nr, h->cfg.circuit_C);
             k_superpose<<<(h->ng + 255) / 256, 256, 0, st>>>(h->sctl, h->phi_P, h->phi_L, h->phi, h->ng);
@@ -772,7 +774,7 @@ void one_step(pic_handle *h, cudaStream_t sb) {
         } else {
             mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi,
                           true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, true,
-                          true, fork);
+                          true, fork, !h->in_batch);
         }
         if (sb) {
             cudaStreamWaitEvent(sb, h->ev_fork, 0);
@@ -939,10 +941,14 @@ void capture_batch(pic_batch *b, pic_batch::Graph &g) {
             cudaStreamWaitEvent(h->gst, b->ev_fork, 0);
             cudaStream_t keep = h->st;
             h->st = h->gst;
+            // the reactors' branches run side by side; inside a branch the
+            // step stays in order (its own second branch adds nodes, not speed)
+            h->in_batch = true;
             if (h->mixed)
-                one_step<float>(h, h->gst2);
+                one_step<float>(h, nullptr);
             else
-                one_step<double>(h, h->gst2);
+                one_step<double>(h, nullptr);
+            h->in_batch = false;
             h->st = keep;
             h->cur = cur;  // the replays flip it
             g.launches[k] = h->launches - L0;
@@ -1422,10 +1428,12 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
         for (pic_handle *h : b->hs) {
             cudaStream_t keep = h->st;
             h->st = b->origin;
+            h->in_batch = true;
             if (h->mixed)
                 one_step<float>(h, nullptr);
             else
                 one_step<double>(h, nullptr);
+            h->in_batch = false;
             h->st = keep;
         }
     }
