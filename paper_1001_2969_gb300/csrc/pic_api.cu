@@ -806,8 +806,10 @@ void one_step(pic_handle *h, cudaStream_t sb) {
         PhaseTimer t(h, 1 + s);
         StepArgs<T> a;
         fill_step_args<T>(h, a, s, src, dst);
-        // blocks walk the chunks of the count on the device
-        launch_step<T>(a, h->step_grid, h->variant[s], (sb && s == 1) ? sb : st);
+        // blocks walk the chunks of the count on the device; a small store
+        // takes no more blocks than its capacity has chunks
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->step_grid, (h->sp[s].cap + 1023) / 1024));
+        launch_step<T>(a, grid, h->variant[s], (sb && s == 1) ? sb : st);
         h->launches += 1;
         h->particle_launches += 1;
     }

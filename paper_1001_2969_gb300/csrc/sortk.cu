@@ -175,9 +175,11 @@ void launch_rank(PBuf<T> mainb, const int32_t *n_main, PBuf<T> births, const int
                  int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
                  const int32_t *status, const StepCtl *ctl, int ncell, cudaStream_t st) {
     // short-lived blocks (a few tiles each): beside the field solve they
-    // retire often, so the solve's blocks find SMs early
-    k_rank<T><<<152 * 32, 256, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap,
-                                         status, ctl, ncell);
+    // retire often, so the solve's blocks find SMs early; a small store
+    // takes no more blocks than its capacity fills (blocks stride on)
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(152 * 32, (cap + 255) / 256));
+    k_rank<T><<<grid, 256, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap, status,
+                                     ctl, ncell);
 }
 
 // ---- newborn numbering ----
@@ -346,7 +348,10 @@ void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, Step
     }
     cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned) + sizeof(int32_t), st);  // counter and timeout flag
     void *args[] = {(void *)&key, (void *)&id, (void *)&nb, (void *)&ctl, (void *)&s, (void *)&tmp};
-    cudaLaunchCooperativeKernel((void *)k_birth_ids, grid, kRadixThreads, args, 0, st);
+    // no more blocks than tiles of the largest batch of births (a small
+    // reactor's numbering does not hold the whole GPU)
+    const int g = std::max(1, std::min(grid, (tmp.max_n + kRadixTile - 1) / kRadixTile));
+    cudaLaunchCooperativeKernel((void *)k_birth_ids, g, kRadixThreads, args, 0, st);
 }
 
 template void launch_hist<float>(PBuf<float>, const int32_t *, int32_t *, cudaStream_t);
