@@ -104,3 +104,36 @@ def test_uniform_weight_makes_the_gradient_vanish():
     _, dA, dP = window_grad(cfg, parts, weight(cfg), K)
     assert abs(dA1) <= 1e-9 * abs(dA)
     assert np.abs(dP1).max() <= 1e-9 * np.abs(dP).max()
+
+
+def test_tiny_mesh_full_steps_against_the_dense_forward():
+    """Brute force on the smallest case: 8 particles per species on the 5 x 5
+    mesh, several full (collisionless) steps of the oracle against the window
+    forward written out with a dense solve of the field."""
+    cfg = W.collisionless(W.config("tiny"))
+    parts = [W.random_particles(cfg, s, 8, seed=50 + s, hot=1.0 + 9.0 * s, margin=2e-4) for s in (0, 1)]
+    K, step0 = 4, 2
+    w = np.ones((cfg["nz"], cfg["nr"]))
+    o = Oracle(cfg)
+    for s in (0, 1):
+        o.set_particles(s, parts[s])
+    o.set_step(step0)
+    o.deposit()
+    o.reset_moments()
+    o.step(K)
+    trace = []
+    J_t = window_J(cfg, parts, w, K, step0=step0, trace=trace)
+    V = Window(cfg).V.numpy()
+    assert abs(J_t - float((w * V * o.moments()["ni"]).sum())) <= 1e-12 * abs(J_t)
+    o.finalize()
+    assert np.abs(trace[-1]["phi"].numpy() - o.grid("phi")).max() <= 1e-9 * np.abs(o.grid("phi")).max()
+    for s in (0, 1):
+        ref = o.get_particles(s)
+        st = trace[-1]["st"][s]
+        alive = st[7].numpy()
+        ids = np.asarray(parts[s]["id"])[alive]
+        assert np.array_equal(np.sort(ids), np.sort(ref["id"]))
+        oi, ti = np.argsort(ref["id"]), np.argsort(ids)
+        for k, name in enumerate(("r", "z", "vr", "vt", "vz", "ar", "az")):
+            a, b = st[k].numpy()[alive][ti], ref[name][oi]
+            assert np.abs(a - b).max() <= 1e-9 * max(np.abs(b).max(), 1e-300), (s, name)
