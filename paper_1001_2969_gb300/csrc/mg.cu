@@ -68,8 +68,7 @@ __global__ void k_chi_levels(const MGFast *__restrict__ mp, int nr, const StepCt
 }
 
 // face coefficients of every level (flat index over all levels' nodes)
-__global__ void k_coefs_levels(const MGFast *__restrict__ mp, int nr, double dr, int face_mean, int total,
-                               const StepCtl *ctl) {
+__global__ void k_coefs_levels(const MGFast *__restrict__ mp, int nr, int face_mean, int total, const StepCtl *ctl) {
     const MGFast &m = *mp;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total || (ctl && ctl->halt)) return;
@@ -79,20 +78,18 @@ __global__ void k_coefs_levels(const MGFast *__restrict__ mp, int nr, double dr,
         ++l;
     }
     const int nz = m.nz[l], i = k / nr, j = k % nr;
-    const double dz = m.dz[l];
     const double *chi = m.chi[l];
     const double c = chi[k];
     double vz = 0.0, vr = 0.0;
     if (i + 1 < nz) {
         const double cn = chi[k + nr];
         const double f = face_mean ? 0.5 * (c + cn) : fmax(c, cn);
-        const double rp = (j + 0.5) * dr, rm = j > 0 ? (j - 0.5) * dr : 0.0;
-        vz = (1.0 + f) * (kPi * (rp * rp - rm * rm)) / dz;
+        vz = (1.0 + f) * m.gz[l][j];
     }
     if (j + 1 < nr) {
         const double cn = chi[k + 1];
         const double f = face_mean ? 0.5 * (c + cn) : fmax(c, cn);
-        vr = (1.0 + f) * 2.0 * kPi * ((j + 0.5) * dr) * dz / dr;
+        vr = (1.0 + f) * m.gr[l][j];
     }
     m.cz[l][k] = vz;
     m.cr[l][k] = vr;
@@ -302,8 +299,7 @@ __device__ __forceinline__ void warp_line_solve(const Ts *__restrict__ F, Ts *Bs
 
 // right-hand side rho A_j dz / eps0 and the Dirichlet data of phi
 __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, double *phi, const double *phi_zL,
-                         double V_arg, int nz, int nr, double dz, double dr, int cold, const StepCtl *ctl,
-                         int v_from_ctl) {
+                         double V_arg, int nz, int nr, int cold, const StepCtl *ctl, int v_from_ctl) {
     const MGFast &m = *mp;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nz * nr || (ctl && ctl->halt)) return;
@@ -311,8 +307,7 @@ __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, doubl
     const int i = k / nr, j = k % nr;
     double v = 0.0, dg = 0.0;
     if (i > 0 && i < nz - 1 && j < nr - 1) {
-        const double rp = (j + 0.5) * dr, rm = j > 0 ? (j - 0.5) * dr : 0.0;
-        v = rho[k] * (kPi * (rp * rp - rm * rm)) * dz / kEps0;
+        v = rho[k] * m.ga[j];
         const double *cz = m.cz[0], *cr = m.cr[0];
         dg = cz[k - nr] + cz[k] + (j > 0 ? cr[k - 1] : 0.0) + cr[k];
     }
@@ -921,6 +916,27 @@ __global__ void k_solve_done(const MGCtl *c, StepCtl *s, int cont) {
 
 }  // namespace
 
+void mg_fast_geometry(const MGFast &m, int nr, double dr, std::vector<double> &out) {
+    // FV face areas of the annuli (z faces) and cylinder sides (r faces)
+    // over the node distances, Sec. 2.4: the set-up kernels only scale them
+    // by 1 + chi of the face
+    out.assign((size_t)(2 * m.nlev + 1) * nr, 0.0);
+    for (int l = 0; l < m.nlev; ++l) {
+        const double dz = m.dz[l];
+        double *gz = out.data() + (size_t)2 * l * nr, *gr = gz + nr;
+        for (int j = 0; j < nr; ++j) {
+            const double rp = (j + 0.5) * dr, rm = j > 0 ? (j - 0.5) * dr : 0.0;
+            gz[j] = (kPi * (rp * rp - rm * rm)) / dz;
+            gr[j] = 2.0 * kPi * rp * dz / dr;
+        }
+    }
+    double *ga = out.data() + (size_t)2 * m.nlev * nr;
+    for (int j = 0; j < nr; ++j) {
+        const double rp = (j + 0.5) * dr, rm = j > 0 ? (j - 0.5) * dr : 0.0;
+        ga[j] = (kPi * (rp * rp - rm * rm)) * m.dz[0] / kEps0;
+    }
+}
+
 void mg_fast_upload(MGFast &m, cudaStream_t st) {
     cudaMemcpyAsync(m.self, &m, sizeof(MGFast), cudaMemcpyHostToDevice, st);
     cudaStreamSynchronize(st);
@@ -947,8 +963,7 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     }
     int total = 0;
     for (int l = 0; l < nlev; ++l) total += m.nz[l] * nr;
-    k_coefs_levels<<<(total + 255) / 256, 256, 0, st>>>(mp, nr, fd.dr, fd.chi_face == PIC_CHI_MEAN,
-                                                         total, sctl);
+    k_coefs_levels<<<(total + 255) / 256, 256, 0, st>>>(mp, nr, fd.chi_face == PIC_CHI_MEAN, total, sctl);
     ++L;
     {
         // line factors in the V-cycle's type; one warp per line
@@ -967,8 +982,8 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
         }
     }
     }
-    k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(mp, rho, phi, phi_zL, V, nz, nr, fd.dz, fd.dr,
-                                               warm ? 0 : 1, sctl, v_from_ctl ? 1 : 0);
+    k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(mp, rho, phi, phi_zL, V, nz, nr, warm ? 0 : 1, sctl,
+                                               v_from_ctl ? 1 : 0);
     ++L;
     // the solve alternates between phi and a copy (both carry the boundary values)
     cudaMemcpyAsync(m.phi2, phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st);

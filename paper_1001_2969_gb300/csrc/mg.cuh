@@ -1,6 +1,8 @@
 // mg.cuh -- workspace and control block of the multigrid solve in mg.cu.
 #pragma once
 
+#include <vector>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -35,6 +37,11 @@ struct MGFast {
     double dz[kMaxLevels];
     double *chi[kMaxLevels], *cz[kMaxLevels], *cr[kMaxLevels];
     float *cz32[kMaxLevels], *cr32[kMaxLevels];
+    // face geometry per level, by column j (filled once by mg_fast_geometry):
+    // gz = pi (r_{j+1/2}^2 - r_{j-1/2}^2) / dz_l, gr = 2 pi r_{j+1/2} dz_l / dr;
+    // ga = pi (r_{j+1/2}^2 - r_{j-1/2}^2) dz / eps0 (level 0's right-hand side)
+    double *gz[kMaxLevels], *gr[kMaxLevels];
+    double *ga;
     // V-cycle correction and right-hand side per level (level 0: the
     // correction of phi and the residual), FP64 path / FP32 (mixed) path
     double *u64[kMaxLevels], *f64[kMaxLevels];
@@ -57,6 +64,9 @@ size_t mg_line_factor_elems(int nr);
 
 // copy the level table to the device (once: its pointers do not change)
 void mg_fast_upload(MGFast &m, cudaStream_t st);
+// host values of gz, gr (every level) and ga, laid out [gz_0 gr_0 gz_1 gr_1 ... ga]
+// with nr entries each; the caller copies them to one device array
+void mg_fast_geometry(const MGFast &m, int nr, double dr, std::vector<double> &out);
 
 // Solve into phi.  Alone (sctl null): returns the cycles (>= 0, converged)
 // or -cycles-1, after a host synchronisation.  Inside a timestep (sctl set):

@@ -568,6 +568,18 @@ void setup_device(pic_handle *h) {
         if (z == 3) break;
     }
     m.nlev = nl;
+    {
+        std::vector<double> geo;
+        mg_fast_geometry(m, h->nr, h->dr, geo);
+        double *g = (double *)dalloc(h, geo.size() * sizeof(double));
+        cudaMemcpyAsync(g, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice, h->st);
+        for (int l = 0; l < nl; ++l) {
+            m.gz[l] = g + (size_t)2 * l * h->nr;
+            m.gr[l] = m.gz[l] + h->nr;
+        }
+        m.ga = g + (size_t)2 * nl * h->nr;
+        cudaStreamSynchronize(h->st);  // geo is a local
+    }
     m.fc64 = (double *)dalloc(h, (size_t)3 * h->nr * sizeof(double));
     m.f0 = (double *)dalloc(h, gb);
     m.dg0 = (double *)dalloc(h, gb);
