@@ -72,6 +72,7 @@ class OrcConfig(C.Structure):
         ("phi_zL", _dp), ("eedf_bins", C.c_int32), ("eedf_emax", C.c_double),
         ("circuit_C", C.c_double),
         ("pusher", C.c_int32),
+        ("ion_subcycle", C.c_int32),
     ]
 
 
@@ -91,6 +92,8 @@ def _declare(L):
     L.orc_set_step.argtypes = [vp, C.c_int64]
     L.orc_get_step.restype = C.c_int64
     L.orc_get_step.argtypes = [vp]
+    L.orc_ion_pass.restype = C.c_int
+    L.orc_ion_pass.argtypes = [vp]
     L.orc_load.argtypes = [vp]
     L.orc_load_range.argtypes = [vp, C.c_int, C.c_int64, C.c_int64] + [_dp] * 8 + [_u64p]
     L.orc_deposit.argtypes = [vp]
@@ -196,6 +199,7 @@ class Oracle:
         c.eedf_emax = cfg.get("eedf_emax", 100.0)
         c.circuit_C = float(cfg.get("circuit_C", 0.0))
         c.pusher = {"local": 0, "xyz": 1}[cfg.get("pusher", "local")]
+        c.ion_subcycle = int(cfg.get("ion_subcycle", 1))
         if capacity is None:
             capacity = max(int(1.5 * max(sp["capacity"] for sp in cfg["species"])), 64)
         self.capacity = capacity
@@ -262,6 +266,10 @@ class Oracle:
 
     def step_index(self):
         return lib().orc_get_step(self.h)
+
+    def ion_pass(self):
+        """True when the next pass moves the ions (ion subcycling)."""
+        return bool(lib().orc_ion_pass(self.h))
 
     # grids
     def deposit(self):

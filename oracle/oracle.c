@@ -347,6 +347,28 @@ static void store_free(orc_store *s) {
     free(s->id);
 }
 
+/*
+ * Ion subcycling (Sec. 2.7, Vahedi's method, named there without a form for
+ * the implicit scheme).  READING: the ions move in the passes n with
+ * n mod K = K - 1 (so a split pass, n mod split_every = split_every - 1
+ * with K dividing split_every, is always one of them) and are held still,
+ * state and deposit, in the others.  A moving pass takes the whole D1
+ * cycle with dt_i = K dt: final push, Monte Carlo with
+ * P_null = 1 - exp(-nu_max dt_i), first push.  So the ions respond to the
+ * field only in the solves that precede their moving passes: their
+ * susceptibility enters those solves with dt_i^2 and the others not at
+ * all.  Ions born in any pass (ionisation by electrons, splits) take
+ * their first push with dt_i, like the ions moved in a pass.
+ */
+static int subcycle(const orc_state *st) { return st->c.ion_subcycle > 1 ? st->c.ion_subcycle : 1; }
+
+int orc_ion_pass(const orc_state *st) {
+    const int K = subcycle(st);
+    return (int)(st->step % K) == K - 1;
+}
+
+static double dt_of(const orc_state *st, int s) { return s == 1 ? st->c.dt * subcycle(st) : st->c.dt; }
+
 orc_state *orc_create(const orc_config *cfg, int64_t capacity) {
     orc_state *st = xmalloc(sizeof(orc_state));
     st->c = *cfg;
@@ -408,7 +430,7 @@ orc_state *orc_create(const orc_config *cfg, int64_t capacity) {
     st->ng = cfg->p_Pa / (ORC_KB * cfg->T_K);
     for (int s = 0; s < 2; ++s) {
         st->nu_max[s] = orc_compute_nu_max(st, s);
-        st->p_null[s] = 1.0 - exp(-st->nu_max[s] * cfg->dt);
+        st->p_null[s] = 1.0 - exp(-st->nu_max[s] * dt_of(st, s));
     }
     st->bcap = 1024;
     st->b = xmalloc(st->bcap * sizeof(orc_birth));
@@ -450,6 +472,7 @@ void orc_set_next_id(orc_state *st, int s, uint64_t v) { st->next_id[s] = v; }
 uint64_t orc_get_next_id(const orc_state *st, int s) { return st->next_id[s]; }
 void orc_set_step(orc_state *st, int64_t step) { st->step = step; }
 int64_t orc_get_step(const orc_state *st) { return st->step; }
+
 
 void orc_set_particles(orc_state *st, int s, int64_t n, const double *r, const double *z,
                        const double *vr, const double *vt, const double *vz, const double *ar,
@@ -604,17 +627,22 @@ void orc_deposit(orc_state *st) {
 /*
  * rho = sum_s q_s N_s / V (Eq. (10)); chi = sum_s (q_s / m_s) rho_s dt^2 / 2
  * (Sec. 2.1) -- in SI units chi = dt^2/(2 eps0) sum_s q_s^2 N_s / (m_s V).
+ * With ion subcycling the ions' term takes dt_i and counts only before a
+ * pass that moves them (READING, at subcycle() above).
  */
 void orc_finalize(orc_state *st) {
     int64_t ng = (int64_t)st->c.nz * st->c.nr;
     double *V = xmalloc(ng * sizeof(double));
     orc_node_volumes(st, V);
+    const int moves_ions = orc_ion_pass(st);
     for (int64_t k = 0; k < ng; ++k) {
         double rho = 0.0, chi = 0.0;
         for (int s = 0; s < 2; ++s) {
             double rho_s = st->c.q[s] * st->N[s][k] / V[k];
             rho += rho_s;
-            chi += 0.5 * (st->c.q[s] / st->c.m[s]) * rho_s * st->c.dt * st->c.dt / ORC_EPS0;
+            if (s == 1 && !moves_ions) continue;
+            double dts = dt_of(st, s);
+            chi += 0.5 * (st->c.q[s] / st->c.m[s]) * rho_s * dts * dts / ORC_EPS0;
         }
         st->rho[k] = rho;
         st->chi[k] = chi;
@@ -1015,8 +1043,7 @@ static int wall_of(const orc_state *st, double r, double z) {
  * v_y' = v_theta + a_theta dt / 2, and both (v_x, v_y) and (a_r, a_theta)
  * rotate onto the new local frame.  At r' = 0, cos = 1 and sin = 0.
  */
-static void first_push(const orc_state *st, orc_p *q) {
-    double dt = st->c.dt;
+static void first_push(const orc_state *st, orc_p *q, double dt) {
     const int xyz = st->c.pusher == 1;
     double vx = q->vr + 0.5 * q->ar * dt;
     double vy = xyz ? q->vt + 0.5 * q->at * dt : q->vt;
@@ -1054,7 +1081,7 @@ static void absorb(orc_state *st, int s, int wall, double w) {
 /* newborn: first push, wall test, record */
 static void newborn(orc_state *st, int ts, int ps, uint64_t pid, int k, orc_p q) {
     st->cnt[ORC_C_BIRTHS + ts] += 1;
-    first_push(st, &q);
+    first_push(st, &q, dt_of(st, ts));
     int wall = wall_of(st, q.r, q.z);
     if (wall >= 0) {
         absorb(st, ts, wall, q.w);
@@ -1246,15 +1273,17 @@ static int eedf_bin(const orc_state *st, double E) {
  * from next_id; they are appended after the survivors.
  */
 void orc_particle_pass(orc_state *st) {
-    double dt = st->c.dt;
     uint32_t step = (uint32_t)st->step;
+    const int moves_ions = orc_ion_pass(st);
     int do_split = st->c.split_every > 0 && (st->step % st->c.split_every) == st->c.split_every - 1;
     st->nb = 0;
     memset(st->qpass, 0, sizeof(st->qpass));
     if (st->c.eedf_bins > 0) memset(st->eedf_pass, 0, st->c.eedf_bins * sizeof(double));
     for (int s = 0; s < 2; ++s) {
+        if (s == 1 && !moves_ions) continue; /* held still (subcycling) */
         orc_store *P = &st->p[s];
         double qm = st->c.q[s] / st->c.m[s];
+        double dt = dt_of(st, s);
         int64_t out = 0;
         for (int64_t k = 0; k < P->n; ++k) {
             orc_p q = {P->r[k], P->z[k], P->vr[k], P->vt[k], P->vz[k], P->ar[k], P->az[k], P->w[k], P->at[k]};
@@ -1304,7 +1333,7 @@ void orc_particle_pass(orc_state *st) {
                 if (bi >= 0) st->eedf_pass[bi] += q.w;
             }
             if (do_split) split(st, s, id, &q);
-            first_push(st, &q);
+            first_push(st, &q, dt);
             wall = wall_of(st, q.r, q.z);
             if (wall >= 0) {
                 absorb(st, s, wall, q.w);

@@ -91,6 +91,9 @@ typedef struct {
     /* pusher (Sec. 2.3): 0 the local X-Y frame with a_theta dropped, 1 the
      * global X-Y-Z form (a_theta carried) */
     int32_t pusher;
+    /* ion subcycling (Sec. 2.7): ions move in every K-th pass only, with
+     * dt_i = K dt; 0 or 1 moves them every pass */
+    int32_t ion_subcycle;
 } orc_config;
 
 typedef struct orc_state orc_state;
@@ -116,6 +119,8 @@ void orc_set_next_id(orc_state *st, int s, uint64_t next_id);
 uint64_t orc_get_next_id(const orc_state *st, int s);
 void orc_set_step(orc_state *st, int64_t step);
 int64_t orc_get_step(const orc_state *st);
+/* 1 when the next pass moves the ions (always without subcycling) */
+int orc_ion_pass(const orc_state *st);
 
 /* external circuit state: out[0] electrode voltage V, out[1] electrode
  * charge Q, out[2] capacitor charge Q_c (C, after the last step) */
