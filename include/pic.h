@@ -136,6 +136,16 @@ typedef struct pic_config {
      * superposition each step; 0 drives the electrode directly */
     double circuit_C;
     int32_t pusher;       /* PIC_PUSH_LOCAL or PIC_PUSH_XYZ (Sec. 2.3)          */
+    /* ion subcycling (Sec. 2.7, Vahedi's method; the implicit form is this
+     * library's reading): with K = ion_subcycle > 1 the ions move only in
+     * the passes n with n mod K = K - 1, by one D1 cycle with dt_i = K dt
+     * (final push, Monte Carlo with P_null = 1 - exp(-nu_max dt_i), first
+     * push), and are held still, state and deposit, in the others; their
+     * susceptibility enters the solve before a moving pass with dt_i^2 and
+     * no other.  Ions born in any pass take their first push with dt_i.
+     * 0 or 1: no subcycling.  split_every must be a multiple of K.  Not
+     * with pic_batch_init or pic_window (PIC_ERR_ARG). */
+    int32_t ion_subcycle;
 } pic_config;
 
 typedef struct pic_handle pic_handle;
@@ -213,7 +223,8 @@ pic_status pic_step(pic_handle *h, int32_t nsteps);
  * the call synchronises once.  statuses (NULL or n entries) receives what
  * pic_step would have returned for each handle; the return value is the
  * first non-OK one.  Handles must have profiling off.  Errors: PIC_ERR_ARG
- * (null, repeated handle, n < 1), PIC_ERR_CUDA (streams, events).
+ * (null, repeated handle, n < 1, a handle that subcycles its ions),
+ * PIC_ERR_CUDA (streams, events).
  */
 pic_status pic_batch_init(pic_handle *const *handles, int32_t n, void *stream, pic_batch **out);
 
@@ -351,8 +362,8 @@ pic_status pic_get_circuit(pic_handle *h, double *out);
  * (nsteps/ckpt + ckpt) particle states).  Particles keep their slots (no
  * sort) and one that reaches a wall leaves the sums.  The handle's own
  * state (particles, fields, step, counters) is unchanged.
- * Errors: PIC_ERR_ARG (nsteps < 1, ckpt < 1, null w, no rf component),
- * PIC_ERR_NOT_CONVERGED / PIC_ERR_TIMEOUT (a solve of the window),
+ * Errors: PIC_ERR_ARG (nsteps < 1, ckpt < 1, null w, no rf component, the
+ * X-Y-Z pusher, ion subcycling), PIC_ERR_NOT_CONVERGED / PIC_ERR_TIMEOUT (a solve of the window),
  * PIC_ERR_CUDA (device memory).
  */
 pic_status pic_window(pic_handle *h, int32_t nsteps, int32_t ckpt, const double *w, double amp0,

@@ -152,9 +152,9 @@ __device__ void emit_birth(const StepArgs<T> &a, BlockTally *bt, int ts, int ps,
                            int k, PS<T> q) {
     atomicAdd(&bt->cnt[PIC_C_BIRTHS + ts], 1ull);
     if (a.xyz)
-        first_push_xyz(a, q);
+        first_push_xyz(a, q, a.bdt[ts], a.bdt_dz[ts]);
     else
-        first_push(a, q);
+        first_push(a, q, a.bdt[ts], a.bdt_dz[ts]);
     const int wall = wall_of(q.i, q.oz, q.j, a.nz, a.nr);
     if (wall >= 0) {
         atomicAdd(&bt->cnt[PIC_C_ABS + ts * 3 + wall], 1ull);

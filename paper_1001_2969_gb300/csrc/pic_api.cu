@@ -46,6 +46,9 @@ struct SpecDev {
     int32_t *perm = nullptr, *counts = nullptr, *cursor = nullptr, *block_sums = nullptr;
     int32_t *d_nmain[2] = {nullptr, nullptr}, *d_nbirths[2] = {nullptr, nullptr};
     int32_t *d_nalive = nullptr, *d_ntotal = nullptr;
+    // births already in the buffer when the last pass began (held ions
+    // collect newborns over several passes; each pass numbers its own)
+    int32_t *d_nb0 = nullptr;
     void *sigma = nullptr;  // T[n_ch][n_e]
     void *sig4 = nullptr;   // T[n_e][4], channels interleaved
     void *w_ref = nullptr;  // T[ncr]
@@ -81,7 +84,9 @@ struct pic_handle {
     double *rf_d = nullptr;   // rf table on the device: amplitudes, frequencies, phases
     int32_t *scal = nullptr;  // per-species device scalars (n_main, n_births, n_alive, n_total)
     SpecDev sp[2];
-    int cur = 0;
+    int cur = 0;    // buffer set holding the electrons (and, without subcycling, the ions)
+    int cur_i = 0;  // buffer set holding the ions (flips only in passes that move them)
+    int K = 1;      // ion subcycling: the ions move every K-th pass
     double *N[2] = {nullptr, nullptr};
     double *rho = nullptr, *chi = nullptr, *phi = nullptr, *Ez = nullptr, *Er = nullptr, *V = nullptr;
     void *E2 = nullptr;
@@ -106,8 +111,8 @@ struct pic_handle {
     cudaStream_t gst2 = nullptr;     // the step graph's second branch (the previous pass's cell sort)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
-    StepGraph graphs[2];
-    StepGraph sort_graphs[2];  // the last pass's cell sort at the end of a call
+    StepGraph graphs[8];       // per (cur, cur_i, the pass moves the ions)
+    StepGraph sort_graphs[4];  // the last pass's cell sort at the end of a call, per (cur, cur_i)
     bool in_batch = false;     // stepped with other reactors (pic_batch): narrow solves
     double ngas = 0.0, nu_max[2] = {0, 0}, p_null[2] = {0, 0};
     unsigned long long t_null[2] = {0, 0};
@@ -137,6 +142,29 @@ struct pic_batch {
 };
 
 namespace {
+
+// Ion subcycling (Sec. 2.7, Vahedi's method; the implicit form is a
+// reading): the ions move in the passes n with n mod K = K - 1, with
+// dt_i = K dt, and are held still, state and deposit, in the others.
+bool moves_ions(const pic_handle *h, int64_t step) {
+    const int64_t K = h->K;
+    return K == 1 || ((step % K) + K) % K == K - 1;
+}
+// passes that moved the ions among steps [0, n) (floor(n / K))
+int64_t ion_passes_before(const pic_handle *h, int64_t n) {
+    const int64_t K = h->K;
+    return n >= 0 ? n / K : -((-n + K - 1) / K);
+}
+double dt_of(const pic_handle *h, int s) { return s == 1 ? h->cfg.dt * h->K : h->cfg.dt; }
+// susceptibility factor q^2 dt_s^2 / (2 eps0 m) of species s before a pass
+// (Sec. 2.1); zero for ions the pass holds still
+double chi_coef(const pic_handle *h, int s, bool moves) {
+    if (s == 1 && !moves) return 0.0;
+    const double dt = dt_of(h, s);
+    return h->cfg.sp[s].q * h->cfg.sp[s].q * dt * dt / (2.0 * kEps0 * h->cfg.sp[s].m);
+}
+// the buffer set holding species s
+int par_of(const pic_handle *h, int s) { return s == 1 ? h->cur_i : h->cur; }
 
 pic_status fail(pic_handle *h, pic_status s, const std::string &msg) {
     if (h) h->err = msg;
@@ -224,6 +252,9 @@ pic_status validate(const pic_config *c, std::string &why) {
     if (c->split_every < 0) return bad("split_every must be >= 0");
     if (c->mg_max_cycles < 1) return bad("mg_max_cycles must be >= 1");
     if (c->pusher != PIC_PUSH_LOCAL && c->pusher != PIC_PUSH_XYZ) return bad("pusher must be PIC_PUSH_LOCAL or PIC_PUSH_XYZ");
+    if (c->ion_subcycle < 0 || c->ion_subcycle > 1024) return bad("ion_subcycle must be in [0, 1024]");
+    if (c->ion_subcycle > 1 && c->split_every % c->ion_subcycle != 0)
+        return bad("split_every must be a multiple of ion_subcycle");
     if (!(c->circuit_C >= 0.0) || !std::isfinite(c->circuit_C))
         return bad("circuit_C must be finite and >= 0 (0: the electrode follows the source)");
     if (c->eedf_bins < 0 || c->eedf_bins > 4096) return bad("eedf_bins must be in [0, 4096]");
@@ -304,12 +335,17 @@ __global__ void k_step_begin(StepCtl *c, const double *rf, int nrf, double dt, i
 
 // step epilogue: the pass wrote *nalive entries into the destination main
 // buffers; their cell sort is pending, and the step advances
+// nmain1 / nalive1 null: the pass held the ions still (subcycling)
 __global__ void k_step_end(StepCtl *c, DevScalars *ds, int32_t *nmain0, const int32_t *nalive0, int32_t *nmain1,
                            const int32_t *nalive1) {
     if (c->halt) return;
     *nmain0 = *nalive0;
-    *nmain1 = *nalive1;
-    ds->cnt[PIC_C_PSTEPS] += (unsigned long long)(*nalive0) + (unsigned long long)(*nalive1);
+    unsigned long long n = (unsigned long long)(*nalive0);
+    if (nmain1) {
+        *nmain1 = *nalive1;
+        n += (unsigned long long)(*nalive1);
+    }
+    ds->cnt[PIC_C_PSTEPS] += n;
     c->sort_pending = 1;
     c->step += 1;
 }
@@ -498,6 +534,7 @@ void setup_device(pic_handle *h) {
         d.d_nbirths[1] = sc + 3;
         d.d_nalive = sc + 4;
         d.d_ntotal = sc + 5;
+        d.d_nb0 = sc + 6;
     }
     const size_t gb = (size_t)h->ng * sizeof(double);
     for (int s = 0; s < 2; ++s) h->N[s] = (double *)dalloc(h, gb);
@@ -607,10 +644,10 @@ void deposit_current(pic_handle *h) {
     for (int s = 0; s < 2; ++s) cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), h->st);
     for (int s = 0; s < 2; ++s) {
         SpecDev &d = h->sp[s];
-        launch_deposit<T>(view<T>(d.main[h->cur]), d.d_nmain[h->cur], h->nz, h->nr,
-                          h->cfg.weighting, h->N[s], h->st);
-        launch_deposit<T>(view<T>(d.births[h->cur]), d.d_nbirths[h->cur], h->nz, h->nr,
-                          h->cfg.weighting, h->N[s], h->st);
+        const int c = par_of(h, s);
+        launch_deposit<T>(view<T>(d.main[c]), d.d_nmain[c], h->nz, h->nr, h->cfg.weighting, h->N[s], h->st);
+        launch_deposit<T>(view<T>(d.births[c]), d.d_nbirths[c], h->nz, h->nr, h->cfg.weighting, h->N[s],
+                          h->st);
         h->launches += 2;
     }
 }
@@ -630,17 +667,20 @@ pic_status load_all(pic_handle *h) {
         d.next_id = (uint64_t)n;
         h->launches += 2;
     }
-    h->cur = 0;
+    h->cur = h->cur_i = 0;
     deposit_current<T>(h);
     cudaStreamSynchronize(h->st);
     push_ctl(h);
     return cuda_check(h, "load");
 }
 
+
+// the pass of species s from buffer set src_set to dst_set; newborn ions go
+// to the ions' set ion_set (the one their next moving pass reads)
 template <typename T>
-void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_set) {
+void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_set, int ion_set) {
     const pic_species &p = h->cfg.sp[s];
-    const double dt = h->cfg.dt, qm = p.q / p.m;
+    const double dt = dt_of(h, s), qm = p.q / p.m;
     a.nz = h->nz;
     a.nr = h->nr;
     a.ncz = h->ncz;
@@ -694,11 +734,14 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     a.n_alive = d.d_nalive;
     a.dst_main = view<T>(d.main[dst_set]);
     for (int t = 0; t < 2; ++t) {
-        a.births[t] = view<T>(h->sp[t].births[dst_set]);
-        a.bkey[t] = h->sp[t].bkey[dst_set];
-        a.nb[t] = h->sp[t].d_nbirths[dst_set];
+        const int bs = t == 1 ? ion_set : dst_set;
+        a.births[t] = view<T>(h->sp[t].births[bs]);
+        a.bkey[t] = h->sp[t].bkey[bs];
+        a.nb[t] = h->sp[t].d_nbirths[bs];
         a.N[t] = h->N[t];
         a.counts[t] = h->sp[t].counts;
+        a.bdt[t] = (T)dt_of(h, t);
+        a.bdt_dz[t] = (T)(dt_of(h, t) / h->dz);
     }
     a.bcap = (int)std::min(h->sp[0].bcap, h->sp[1].bcap);
     a.ds = h->ds;
@@ -715,28 +758,34 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
 // pass's cell counts, the capacity check, the rank into the permutation the
 // next pass reads through.  Regular kernels only, so it can run beside the
 // cooperative field solve.
+// With ion subcycling the ions are sorted only before a pass that moves
+// them (ions = false otherwise): held ions keep their order, and their
+// counts and births collect until then.
 template <typename T>
-void sort_branch(pic_handle *h, int par, cudaStream_t st) {
-    for (int s = 0; s < 2; ++s) {
+void sort_branch(pic_handle *h, int par_e, int par_i, bool ions, cudaStream_t st) {
+    const int ns = ions ? 2 : 1;
+    for (int s = 0; s < ns; ++s) {
         SpecDev &d = h->sp[s];
         launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, h->sctl, st);
     }
     // capacity and births overflow: the sort fails before any permutation changes
     launch_step_check(h->ds, h->sctl, st);
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < ns; ++s) {
         SpecDev &d = h->sp[s];
+        const int par = s == 1 ? par_i : par_e;
         launch_rank<T>(view<T>(d.main[par]), d.d_nmain[par], view<T>(d.births[par]), d.d_nbirths[par],
                        d.cursor, d.perm, d.d_ntotal, d.cap, &h->ds->status, h->sctl, h->ncell, st);
     }
-    h->launches += 9;
+    h->launches += 4 * ns + 1;
 }
 
 // the rest of the sort: newborn numbering (a cooperative launch, after the
 // field solve's), then the sorted counts take effect
-void sort_finish(pic_handle *h, int par, cudaStream_t st) {
+void sort_finish(pic_handle *h, int par_e, int par_i, cudaStream_t st) {
     for (int s = 0; s < 2; ++s) {
         SpecDev &d = h->sp[s];
-        launch_birth_ids(d.bkey[par], d.births[par].id, d.d_nbirths[par], h->sctl, s, h->rtmp, st);
+        const int par = s == 1 ? par_i : par_e;
+        launch_birth_ids(d.bkey[par], d.births[par].id, d.d_nbirths[par], d.d_nb0, h->sctl, s, h->rtmp, st);
     }
     k_sort_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nalive, h->sp[0].d_ntotal, h->sp[1].d_nalive,
                                  h->sp[1].d_ntotal);
@@ -747,16 +796,19 @@ void sort_finish(pic_handle *h, int par, cudaStream_t st) {
 // new time (finalize, solve, E) beside the previous pass's cell sort (on
 // sb, forked and joined; in order on h->st when sb is null), then the
 // particle passes, the time averages and the step's end.  The pass's own
-// sort is left pending for the next step or the end of the call.
+// sort is left pending for the next step or the end of the call.  mv: the
+// pass moves the ions (always without subcycling); otherwise they stay in
+// their buffer set with their deposit, and newborn ions join their births.
 template <typename T>
-void one_step(pic_handle *h, cudaStream_t sb) {
+void one_step(pic_handle *h, cudaStream_t sb, bool mv) {
     cudaStream_t st = h->st;
     const int src = h->cur, dst = 1 - h->cur;
+    const int isrc = h->cur_i, idst = mv ? 1 - h->cur_i : h->cur_i;
     k_step_begin<<<1, 1, 0, st>>>(h->sctl, h->rf_d, h->cfg.rf.n, h->cfg.dt, h->cfg.split_every);
     h->launches += 1;
     if (!sb) {
         PhaseTimer t(h, 3);
-        sort_branch<T>(h, src, st);
+        sort_branch<T>(h, src, isrc, mv, st);
     }
     // with a second branch, the sort forks off right before the one-launch
     // solve (after its set-up): the solve, at the highest priority, takes
@@ -764,10 +816,8 @@ void one_step(pic_handle *h, cudaStream_t sb) {
     cudaEvent_t fork = sb ? h->ev_fork : nullptr;
     {
         PhaseTimer t(h, 0);
-        launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q,
-                        h->cfg.sp[0].q * h->cfg.sp[0].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[0].m),
-                        h->cfg.sp[1].q * h->cfg.sp[1].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[1].m),
-                        h->rho, h->chi, h->ng, h->sctl, st);
+        launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q, chi_coef(h, 0, true),
+                        chi_coef(h, 1, mv), h->rho, h->chi, h->ng, h->sctl, st);
         FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
         int L = 0;
         if (h->cfg.circuit_C > 0.0) {
@@ -790,7 +840,7 @@ void one_step(pic_handle *h, cudaStream_t sb) {
         }
         if (sb) {
             cudaStreamWaitEvent(sb, h->ev_fork, 0);
-            sort_branch<T>(h, src, sb);
+            sort_branch<T>(h, src, isrc, mv, sb);
             cudaEventRecord(h->ev_join, sb);
         }
         launch_efield<T>(h->phi, h->Ez, h->Er, (typename V2<T>::type *)h->E2, h->nz, h->nr, h->dz,
@@ -800,32 +850,44 @@ void one_step(pic_handle *h, cudaStream_t sb) {
     if (sb) cudaStreamWaitEvent(st, h->ev_join, 0);
     {
         PhaseTimer t(h, 3);
-        sort_finish(h, src, st);
+        sort_finish(h, src, isrc, st);
     }
     for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        if (s == 1 && !mv) {
+            // held ions: deposit, counts and births stay; this pass's
+            // newborns are numbered from the births already there
+            cudaMemcpyAsync(d.d_nb0, d.d_nbirths[idst], sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+            continue;
+        }
         cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), st);
-        cudaMemsetAsync(h->sp[s].counts, 0, (size_t)h->ncell * sizeof(int32_t), st);
-        cudaMemsetAsync(h->sp[s].d_nbirths[dst], 0, sizeof(int32_t), st);
+        cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), st);
+        cudaMemsetAsync(d.d_nbirths[s == 1 ? idst : dst], 0, sizeof(int32_t), st);
+        if (s == 1 && h->K > 1) cudaMemsetAsync(d.d_nb0, 0, sizeof(int32_t), st);  // else always 0
     }
     // the two species' passes are independent (what they share -- the other
     // species' births, deposit and counts -- takes atomics or reserved
     // slots): with a second branch the ion pass runs beside the electrons'
-    if (sb) {
+    const bool fork2 = sb && mv;
+    if (fork2) {
         cudaEventRecord(h->ev_fork2, st);
         cudaStreamWaitEvent(sb, h->ev_fork2, 0);
     }
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < (mv ? 2 : 1); ++s) {
         PhaseTimer t(h, 1 + s);
         StepArgs<T> a;
-        fill_step_args<T>(h, a, s, src, dst);
+        if (s == 0)
+            fill_step_args<T>(h, a, 0, src, dst, idst);
+        else
+            fill_step_args<T>(h, a, 1, isrc, idst, idst);
         // blocks walk the chunks of the count on the device; a small store
         // takes no more blocks than its capacity has chunks
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->step_grid, (h->sp[s].cap + 1023) / 1024));
-        launch_step<T>(a, grid, h->variant[s], (sb && s == 1) ? sb : st);
+        launch_step<T>(a, grid, h->variant[s], (fork2 && s == 1) ? sb : st);
         h->launches += 1;
         h->particle_launches += 1;
     }
-    if (sb) {
+    if (fork2) {
         cudaEventRecord(h->ev_join2, sb);
         cudaStreamWaitEvent(st, h->ev_join2, 0);
     }
@@ -834,26 +896,30 @@ void one_step(pic_handle *h, cudaStream_t sb) {
         launch_moments(h->N[0], h->N[1], h->V, h->phi, h->Ez, h->Er, h->m_acc[0], h->m_acc[1],
                        h->m_acc[2], h->m_acc[3], h->m_acc[4], h->ng, h->sctl, st);
         k_step_end<<<1, 1, 0, st>>>(h->sctl, h->ds, h->sp[0].d_nmain[dst], h->sp[0].d_nalive,
-                                     h->sp[1].d_nmain[dst], h->sp[1].d_nalive);
+                                     mv ? h->sp[1].d_nmain[idst] : nullptr, mv ? h->sp[1].d_nalive : nullptr);
         h->launches += 2;
     }
     h->cur = dst;
+    h->cur_i = idst;
 }
 
 // the pending sort of the last pass (end of a call), on h->st
 template <typename T>
 void sort_tail(pic_handle *h) {
     PhaseTimer t(h, 3);
-    sort_branch<T>(h, h->cur, h->st);
-    sort_finish(h, h->cur, h->st);
+    sort_branch<T>(h, h->cur, h->cur_i, true, h->st);
+    sort_finish(h, h->cur, h->cur_i, h->st);
 }
 
 void drop_graphs(pic_handle *h) {
-    for (StepGraph *gs : {h->graphs, h->sort_graphs})
-        for (int k = 0; k < 2; ++k) {
-            if (gs[k].exec) cudaGraphExecDestroy(gs[k].exec);
-            gs[k] = StepGraph();
-        }
+    for (StepGraph &g : h->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = StepGraph();
+    }
+    for (StepGraph &g : h->sort_graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = StepGraph();
+    }
 }
 
 void destroy_streams(pic_handle *h) {
@@ -866,21 +932,22 @@ void destroy_streams(pic_handle *h) {
     h->gst = h->gst2 = nullptr;
 }
 
-// capture one step (from the current parity) on the private stream
+// capture one step (from the current parities) on the private stream
 template <typename T>
-void capture_step(pic_handle *h, StepGraph &g) {
-    const int cur = h->cur;
+void capture_step(pic_handle *h, StepGraph &g, bool mv) {
+    const int cur = h->cur, cur_i = h->cur_i;
     const int64_t L0 = h->launches, P0 = h->particle_launches;
     cudaStream_t keep = h->st;
     h->st = h->gst;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        one_step<T>(h, h->gst2);
+        one_step<T>(h, h->gst2, mv);
         e = cudaStreamEndCapture(h->gst, &graph);
     }
     h->st = keep;
     h->cur = cur;
+    h->cur_i = cur_i;
     g.launches = h->launches - L0;
     h->launches = L0;
     h->particle_launches = P0;
@@ -919,7 +986,7 @@ void capture_sort(pic_handle *h, StepGraph &g) {
 
 // enqueue the pending sort on stream `on` (private stream: as a graph)
 void enqueue_sort_tail(pic_handle *h, cudaStream_t on) {
-    StepGraph &g = h->sort_graphs[h->cur];
+    StepGraph &g = h->sort_graphs[h->cur + 2 * h->cur_i];
     if (on == h->gst && !g.exec && !g.failed) {
         if (h->mixed)
             capture_sort<float>(h, g);
@@ -950,7 +1017,7 @@ void capture_batch(pic_batch *b, pic_batch::Graph &g) {
         cudaEventRecord(b->ev_fork, b->origin);
         for (size_t k = 0; k < nh; ++k) {
             pic_handle *h = b->hs[k];
-            const int cur = h->cur;
+            const int cur = h->cur, cur_i = h->cur_i;
             const int64_t L0 = h->launches, P0 = h->particle_launches;
             cudaStreamWaitEvent(h->gst, b->ev_fork, 0);
             cudaStream_t keep = h->st;
@@ -959,12 +1026,13 @@ void capture_batch(pic_batch *b, pic_batch::Graph &g) {
             // step stays in order (its own second branch adds nodes, not speed)
             h->in_batch = true;
             if (h->mixed)
-                one_step<float>(h, nullptr);
+                one_step<float>(h, nullptr, true);
             else
-                one_step<double>(h, nullptr);
+                one_step<double>(h, nullptr, true);
             h->in_batch = false;
             h->st = keep;
-            h->cur = cur;  // the replays flip it
+            h->cur = cur;  // the replays flip them
+            h->cur_i = cur_i;
             g.launches[k] = h->launches - L0;
             h->launches = L0;
             h->particle_launches = P0;
@@ -1013,13 +1081,14 @@ pic_status set_particles_t(pic_handle *h, int s, const pic_particles_view *v) {
         sat = (double *)dalloc(h, (size_t)n * sizeof(double));
         cudaMemcpyAsync(sat, v->at, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->st);
     }
-    const int c = h->cur;
+    const int c = par_of(h, s);
     launch_from_abs<T>(view<T>(d.main[c]), n, stage, stage + n, stage + 2 * n, stage + 3 * n,
                        stage + 4 * n, stage + 5 * n, stage + 6 * n, stage + 7 * n, sid, sat, h->nz, h->nr,
                        h->dz, h->dr, h->st);
     const int32_t nn = (int32_t)n, zero = 0;
     cudaMemcpyAsync(d.d_nmain[c], &nn, 4, cudaMemcpyHostToDevice, h->st);
     cudaMemcpyAsync(d.d_nbirths[c], &zero, 4, cudaMemcpyHostToDevice, h->st);
+    cudaMemsetAsync(d.d_nb0, 0, sizeof(int32_t), h->st);
     cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), h->st);
     launch_hist<T>(view<T>(d.main[c]), d.d_nmain[c], d.counts, h->st);
     launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, nullptr, h->st);
@@ -1050,7 +1119,7 @@ pic_status get_particles_t(pic_handle *h, int s, pic_particles_view *v, int64_t 
     uint64_t *sid = (uint64_t *)dalloc(h, (size_t)n * sizeof(uint64_t));
     int32_t *scell = (int32_t *)dalloc(h, (size_t)n * sizeof(int32_t));
     double *sat = v->at ? (double *)dalloc(h, (size_t)n * sizeof(double)) : nullptr;
-    const int c = h->cur;
+    const int c = par_of(h, s);
     launch_to_abs<T>(view<T>(d.main[c]), view<T>(d.births[c]), d.d_nmain[c], d.perm, n, stage + n,
                      stage, stage + 2 * n, stage + 3 * n, stage + 4 * n, stage + 5 * n,
                      stage + 6 * n, stage + 7 * n, sid, scell, sat, h->nz, h->dz, h->dr, h->st);
@@ -1106,7 +1175,7 @@ pic_status window_t(pic_handle *h, int32_t nsteps, int32_t ckpt, const double *w
         in.main[s] = view<T>(d.main[cur]);
         in.births[s] = view<T>(d.births[cur]);
         in.perm[s] = d.perm;
-        fill_step_args<T>(h, in.args[s], s, cur, 1 - cur);
+        fill_step_args<T>(h, in.args[s], s, cur, 1 - cur, 1 - cur);
     }
     in.V = h->V;
     in.phi0 = h->phi;
@@ -1131,7 +1200,7 @@ pic_status window_t(pic_handle *h, int32_t nsteps, int32_t ckpt, const double *w
     return cuda_check(h, "window");
 }
 
-pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int32_t nsteps) {
+pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int cur_i0, int32_t nsteps) {
     StepCtl c;
     int32_t status = 0;
     cudaMemcpyAsync(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
@@ -1142,6 +1211,7 @@ pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int32_t nsteps) {
     // a failed sort ends the call at the pass it sorts, before any later failure
     const int64_t done = c.sort_fail ? c.sort_fail_step - step0 : c.halt ? c.halt_step - step0 : (int64_t)nsteps;
     h->cur = (int)(cur0 ^ (int)(done & 1));
+    h->cur_i = (int)(cur_i0 ^ (int)((ion_passes_before(h, step0 + done) - ion_passes_before(h, step0)) & 1));
     h->step = step0 + done;
     h->nsamples += done;
     h->steps_total += done;
@@ -1261,9 +1331,10 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out) {
     h->dr = cfg->mesh.R / h->ncr;
     h->mixed = cfg->precision == PIC_MIXED;
     h->ngas = cfg->gas.p_Pa / (kKB * cfg->gas.T_K);
+    h->K = cfg->ion_subcycle > 1 ? cfg->ion_subcycle : 1;
     for (int s = 0; s < 2; ++s) {
         h->nu_max[s] = nu_max_of(h, s);
-        h->p_null[s] = 1.0 - exp(-h->nu_max[s] * cfg->dt);
+        h->p_null[s] = 1.0 - exp(-h->nu_max[s] * dt_of(h, s));
         // candidate iff (x + 1/2) 2^-32 < P_null  <=>  x < ceil(P_null 2^32 - 1/2)
         const double c = ldexp(h->p_null[s], 32) - 0.5;
         h->t_null[s] = c <= 0.0 ? 0ull : (unsigned long long)ceil(c);
@@ -1294,18 +1365,19 @@ pic_status pic_step(pic_handle *h, int32_t nsteps) {
     if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return PIC_OK;
     const int64_t step0 = h->step;
-    const int cur0 = h->cur;
+    const int cur0 = h->cur, cur_i0 = h->cur_i;
     // steps run as graph replays on the private stream, ordered after the
     // caller's stream and before it again; with profiling on they launch
     // one by one on the caller's stream (phase timers)
     bool on_gst = false;
     for (int k = 0; k < nsteps; ++k) {
-        StepGraph &g = h->graphs[h->cur];
+        const bool mv = moves_ions(h, step0 + k);
+        StepGraph &g = h->graphs[h->cur + 2 * h->cur_i + (mv ? 4 : 0)];
         if (!h->prof && h->gst && !g.exec && !g.failed) {
             if (h->mixed)
-                capture_step<float>(h, g);
+                capture_step<float>(h, g, mv);
             else
-                capture_step<double>(h, g);
+                capture_step<double>(h, g, mv);
         }
         if (!h->prof && g.exec) {
             if (!on_gst) {
@@ -1315,8 +1387,9 @@ pic_status pic_step(pic_handle *h, int32_t nsteps) {
             }
             cudaGraphLaunch(g.exec, h->gst);
             h->launches += g.launches;
-            h->particle_launches += 2;
+            h->particle_launches += mv ? 2 : 1;
             h->cur ^= 1;
+            if (mv) h->cur_i ^= 1;
             continue;
         }
         if (on_gst) {
@@ -1325,9 +1398,9 @@ pic_status pic_step(pic_handle *h, int32_t nsteps) {
             on_gst = false;
         }
         if (h->mixed)
-            one_step<float>(h, nullptr);
+            one_step<float>(h, nullptr, mv);
         else
-            one_step<double>(h, nullptr);
+            one_step<double>(h, nullptr, mv);
     }
     // the last pass's sort: the state between calls is sorted
     enqueue_sort_tail(h, on_gst ? h->gst : h->st);
@@ -1335,7 +1408,7 @@ pic_status pic_step(pic_handle *h, int32_t nsteps) {
         cudaEventRecord(h->ev_out, h->gst);
         cudaStreamWaitEvent(h->st, h->ev_out, 0);
     }
-    return finish_call(h, step0, cur0, nsteps);
+    return finish_call(h, step0, cur0, cur_i0, nsteps);
 }
 
 pic_status pic_tune(pic_handle *h, int32_t steps_per_variant, int32_t *variants) {
@@ -1385,6 +1458,7 @@ pic_status pic_batch_init(pic_handle *const *handles, int32_t n, void *stream, p
     if (!handles || n < 1) return PIC_ERR_ARG;
     for (int k = 0; k < n; ++k) {
         if (!handles[k] || !handles[k]->gst) return PIC_ERR_ARG;
+        if (handles[k]->K > 1) return fail(handles[k], PIC_ERR_ARG, "batched reactors move their ions every step");
         for (int q = 0; q < k; ++q)
             if (handles[q] == handles[k]) return PIC_ERR_ARG;
     }
@@ -1433,6 +1507,7 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
             cudaGraphLaunch(g.exec, b->origin);
             for (size_t k = 0; k < nh; ++k) {
                 b->hs[k]->cur ^= 1;
+                b->hs[k]->cur_i ^= 1;
                 b->hs[k]->particle_launches += 2;
                 b->hs[k]->launches += g.launches[k];
             }
@@ -1444,9 +1519,9 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
             h->st = b->origin;
             h->in_batch = true;
             if (h->mixed)
-                one_step<float>(h, nullptr);
+                one_step<float>(h, nullptr, true);
             else
-                one_step<double>(h, nullptr);
+                one_step<double>(h, nullptr, true);
             h->in_batch = false;
             h->st = keep;
         }
@@ -1454,7 +1529,7 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
     if (nsteps > 0) {
         // every reactor's last sort, side by side on the reactors' streams
         for (pic_handle *h : b->hs) {
-            StepGraph &g = h->sort_graphs[h->cur];
+            StepGraph &g = h->sort_graphs[h->cur + 2 * h->cur_i];
             if (!g.exec && !g.failed) {
                 if (h->mixed)
                     capture_sort<float>(h, g);
@@ -1477,7 +1552,7 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
     cudaStreamSynchronize(b->st);
     pic_status first = PIC_OK;
     for (size_t k = 0; k < nh; ++k) {
-        const pic_status r = nsteps > 0 ? finish_call(b->hs[k], step0[k], cur0[k], nsteps) : PIC_OK;
+        const pic_status r = nsteps > 0 ? finish_call(b->hs[k], step0[k], cur0[k], cur0[k], nsteps) : PIC_OK;
         if (statuses) statuses[k] = r;
         if (first == PIC_OK && r != PIC_OK) first = r;
     }
@@ -1623,10 +1698,9 @@ pic_status pic_set_boundary(pic_handle *h, const double *phi_zL, int32_t on_devi
 pic_status pic_get_fields(pic_handle *h, double *rho, double *chi, double *phi, double *Ez,
                           double *Er, int32_t on_device) {
     if (!h) return PIC_ERR_ARG;
-    launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q,
-                    h->cfg.sp[0].q * h->cfg.sp[0].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[0].m),
-                    h->cfg.sp[1].q * h->cfg.sp[1].q * h->cfg.dt * h->cfg.dt / (2.0 * kEps0 * h->cfg.sp[1].m),
-                    h->rho, h->chi, h->ng, nullptr, h->st);
+    // rho and chi as the next step's solve takes them
+    launch_finalize(h->N[0], h->N[1], h->V, h->cfg.sp[0].q, h->cfg.sp[1].q, chi_coef(h, 0, true),
+                    chi_coef(h, 1, moves_ions(h, h->step)), h->rho, h->chi, h->ng, nullptr, h->st);
     h->launches += 1;
     const size_t gb = (size_t)h->ng * sizeof(double);
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -1671,6 +1745,7 @@ pic_status pic_window(pic_handle *h, int32_t nsteps, int32_t ckpt, const double 
     if (!h || !w || nsteps < 1 || ckpt < 1) return fail(h, PIC_ERR_ARG, "bad window arguments");
     if (h->cfg.rf.n < 1) return fail(h, PIC_ERR_ARG, "the window needs an rf component");
     if (h->cfg.pusher != PIC_PUSH_LOCAL) return fail(h, PIC_ERR_ARG, "the window takes the local pusher");
+    if (h->K > 1) return fail(h, PIC_ERR_ARG, "the window moves the ions every step (no subcycling)");
     return h->mixed ? window_t<float>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL)
                     : window_t<double>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL);
 }
@@ -1683,7 +1758,8 @@ pic_status pic_save(pic_handle *h, const char *path) {
     if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint for writing");
     const int circuit = h->cfg.circuit_C > 0.0 ? 1 : 0;
     const int xyz = h->cfg.pusher == PIC_PUSH_XYZ ? 1 : 0;
-    int64_t hdr[8] = {(int64_t)kCkptMagic, h->nz, h->nr, h->step, h->mixed ? 1 : 0, circuit, xyz, 0};
+    int64_t hdr[8] = {(int64_t)kCkptMagic, h->nz, h->nr, h->step, h->mixed ? 1 : 0, circuit, xyz,
+                      h->K > 1 ? h->K : 0};
     uint64_t ids[2] = {h->sp[0].next_id, h->sp[1].next_id};
     fwrite(hdr, sizeof(hdr), 1, f);
     fwrite(ids, sizeof(ids), 1, f);
@@ -1744,7 +1820,8 @@ pic_status pic_load(pic_handle *h, const char *path) {
     const int circuit = h->cfg.circuit_C > 0.0 ? 1 : 0;
     const int xyz = h->cfg.pusher == PIC_PUSH_XYZ ? 1 : 0;
     if (fread(hdr, sizeof(hdr), 1, f) != 1 || (uint64_t)hdr[0] != kCkptMagic || hdr[1] != h->nz ||
-        hdr[2] != h->nr || hdr[5] != circuit || hdr[6] != xyz || fread(ids, sizeof(ids), 1, f) != 1) {
+        hdr[2] != h->nr || hdr[5] != circuit || hdr[6] != xyz || hdr[7] != (h->K > 1 ? h->K : 0) ||
+        fread(ids, sizeof(ids), 1, f) != 1) {
         fclose(f);
         return fail(h, PIC_ERR_ARG, "checkpoint does not match this handle");
     }

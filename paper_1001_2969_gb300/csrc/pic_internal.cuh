@@ -194,6 +194,7 @@ struct StepArgs {
     T kz, kr, kv, ka;
     // first push
     T dt, dt_dz, dt_dr, dr, inv_dr;
+    T bdt[2], bdt_dz[2];  // first push of a newborn of species t (ion subcycling: dt_i)
     // Monte Carlo
     unsigned long long t_null;  // candidate iff word < t_null
     T nu_max, ng, half_m_e;     // half_m_e = m / (2 e): E[eV] = half_m_e g^2
@@ -274,8 +275,9 @@ struct RadixTmp {
     int *flag;
     int max_n;
 };
-void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, StepCtl *ctl, int s,
-                      RadixTmp tmp, cudaStream_t st);
+// numbers the births key/id[*nb0 .. *nb) (nb0 nullable: from 0)
+void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, const int32_t *nb0, StepCtl *ctl,
+                      int s, RadixTmp tmp, cudaStream_t st);
 
 // ---- multigrid (field.cu) ----
 struct MGLevel {

@@ -165,14 +165,14 @@ __device__ __forceinline__ int wall_of(int i, T oz, int j, int nz, int nr) {
 // The radial step is formed without cancellation:
 // r' - r = (2 r dx + dx^2 + dy^2) / (r' + r).
 template <typename T>
-__device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p) {
-    const T vx = p.vr + (T)0.5 * p.ar * a.dt;
+__device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p, const T dt, const T dt_dz) {
+    const T vx = p.vr + (T)0.5 * p.ar * dt;
     const T vy = p.vt;
-    const T vz = p.vz + (T)0.5 * p.az * a.dt;
-    p.oz += vz * a.dt_dz;
+    const T vz = p.vz + (T)0.5 * p.az * dt;
+    p.oz += vz * dt_dz;
     carry(p.oz, p.i);
     const T r = ((T)p.j + p.orr) * a.dr;
-    const T dx = vx * a.dt, dy = vy * a.dt;
+    const T dx = vx * dt, dy = vy * dt;
     const T xr = r + dx;
     const T q2 = xr * xr + dy * dy;
     T c = (T)1, sn = (T)0, rn = (T)0;
@@ -205,19 +205,24 @@ __device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p) {
     p.vz = vz;
     p.ar = p.ar * c;
 }
+// the species' own step (a newborn of another species passes that one's)
+template <typename T>
+__device__ __forceinline__ void first_push(const StepArgs<T> &a, PS<T> &p) {
+    first_push(a, p, a.dt, a.dt_dz);
+}
 
 // the same in the global X-Y-Z form (Sec. 2.3, end) for a particle taken at
 // azimuth 0 (the field is axisymmetric): v_y' = v_theta + a_theta dt / 2,
 // and (a_r, a_theta) rotate onto the new local frame with (v_x, v_y)
 template <typename T>
-__device__ __forceinline__ void first_push_xyz(const StepArgs<T> &a, PS<T> &p) {
-    const T vx = p.vr + (T)0.5 * p.ar * a.dt;
-    const T vy = p.vt + (T)0.5 * p.at * a.dt;
-    const T vz = p.vz + (T)0.5 * p.az * a.dt;
-    p.oz += vz * a.dt_dz;
+__device__ __forceinline__ void first_push_xyz(const StepArgs<T> &a, PS<T> &p, const T dt, const T dt_dz) {
+    const T vx = p.vr + (T)0.5 * p.ar * dt;
+    const T vy = p.vt + (T)0.5 * p.at * dt;
+    const T vz = p.vz + (T)0.5 * p.az * dt;
+    p.oz += vz * dt_dz;
     carry(p.oz, p.i);
     const T r = ((T)p.j + p.orr) * a.dr;
-    const T dx = vx * a.dt, dy = vy * a.dt;
+    const T dx = vx * dt, dy = vy * dt;
     const T xr = r + dx;
     const T q2 = xr * xr + dy * dy;
     T c = (T)1, sn = (T)0, rn = (T)0;
@@ -251,6 +256,11 @@ __device__ __forceinline__ void first_push_xyz(const StepArgs<T> &a, PS<T> &p) {
     const T arn = p.ar * c + p.at * sn;
     p.at = -p.ar * sn + p.at * c;
     p.ar = arn;
+}
+// the species' own step (a newborn of another species passes that one's)
+template <typename T>
+__device__ __forceinline__ void first_push_xyz(const StepArgs<T> &a, PS<T> &p) {
+    first_push_xyz(a, p, a.dt, a.dt_dz);
 }
 
 }  // namespace pic

@@ -195,7 +195,8 @@ constexpr int kRadixPer = 2;
 constexpr int kRadixTile = kRadixThreads * kRadixPer;
 
 __global__ void __launch_bounds__(kRadixThreads)
-    k_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb_dev, StepCtl *ctl, int s, RadixTmp t) {
+    k_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb_dev, const int32_t *nb0_dev, StepCtl *ctl, int s,
+                RadixTmp t) {
     // the small path's keys and the scatter's per-warp digit counts share space
     constexpr int kBuf = kSmallBirths * 8 > (kRadixThreads / 32) * 256 * 4 ? kSmallBirths * 8
                                                                             : (kRadixThreads / 32) * 256 * 4;
@@ -206,8 +207,12 @@ __global__ void __launch_bounds__(kRadixThreads)
     __shared__ int s_warp[32];
     __shared__ int s_carry;
     if (sort_skip(ctl)) return;
-    const int nb = *nb_dev;
-    if (nb <= 0) return;
+    // the births of the last pass: the buffer's entries from *nb0_dev on
+    const int first = nb0_dev ? *nb0_dev : 0;
+    const int nb = *nb_dev - first;
+    if (nb <= 0 || first < 0) return;
+    key += first;
+    id += first;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (nb <= kSmallBirths) {
         if (blockIdx.x != 0) return;
@@ -333,8 +338,8 @@ __global__ void __launch_bounds__(kRadixThreads)
     if (blockIdx.x == 0 && tid == 0) ctl->next_id[s] = base + (uint64_t)nb;
 }
 
-void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, StepCtl *ctl, int s,
-                      RadixTmp tmp, cudaStream_t st) {
+void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, const int32_t *nb0, StepCtl *ctl,
+                      int s, RadixTmp tmp, cudaStream_t st) {
     // one block per SM (the launch needs them co-resident), per device
     static int grids[64] = {0};
     int dev = 0;
@@ -347,7 +352,7 @@ void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, Step
         grid = std::max(1, std::min(nsm, nsm * per));
     }
     cudaMemsetAsync(&ctl->bar, 0, sizeof(unsigned) + sizeof(int32_t), st);  // counter and timeout flag
-    void *args[] = {(void *)&key, (void *)&id, (void *)&nb, (void *)&ctl, (void *)&s, (void *)&tmp};
+    void *args[] = {(void *)&key, (void *)&id, (void *)&nb, (void *)&nb0, (void *)&ctl, (void *)&s, (void *)&tmp};
     // no more blocks than tiles of the largest batch of births (a small
     // reactor's numbering does not hold the whole GPU)
     const int g = std::max(1, std::min(grid, (tmp.max_n + kRadixTile - 1) / kRadixTile));

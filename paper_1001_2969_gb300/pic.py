@@ -65,7 +65,8 @@ class pic_config(C.Structure):
                 ("mg_tol", C.c_double), ("phi_zL", _dp), ("births_capacity", C.c_int64),
                 ("eedf_bins", C.c_int32), ("eedf_emax_eV", C.c_double), ("load", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p), ("circuit_C", C.c_double), ("pusher", C.c_int32)]
+                ("stream", C.c_void_p), ("circuit_C", C.c_double), ("pusher", C.c_int32),
+                ("ion_subcycle", C.c_int32)]
 
 
 class pic_particles_view(C.Structure):
@@ -247,6 +248,7 @@ def pic_init(cfg: dict, load: bool = True, stream=None, torch_memory: bool = Tru
     c.stream = stream
     c.circuit_C = float(cfg.get("circuit_C", 0.0))
     c.pusher = {"local": 0, "xyz": 1}[cfg.get("pusher", "local")]
+    c.ion_subcycle = int(cfg.get("ion_subcycle", 1))
     ptr = C.c_void_p()
     st = L.pic_init(C.byref(c), C.byref(ptr))
     if st != PIC_OK:
