@@ -148,7 +148,7 @@ def run_gpu(args, rank, world):
     results = {}
     for prec in (args.precision, "fp64") if args.fp64_steps > 0 else (args.precision,):
         steps = args.steps if prec == args.precision else args.fp64_steps
-        cfg = W.config(args.config, precision=prec, seed=1 + rank)
+        cfg = W.config(args.config, precision=prec, seed=1 + rank, ion_subcycle=args.ion_subcycle)
         if args.particles:
             cfg = W.scaled(cfg, args.particles)
         h = pic.pic_init(cfg, stream=stream.cuda_stream)
@@ -443,6 +443,9 @@ def main():
                     help="particles per species (default: the workload's; smaller for profiling)")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the adjoint window (workload c5) instead")
+    ap.add_argument("--ion-subcycle", type=int, default=1,
+                    help="move the ions every K-th step with K dt (Sec. 2.7); the count of particle-steps "
+                         "then holds each moved ion once per K steps")
     ap.add_argument("--batch", type=int, default=0,
                     help="time a batch of this many independent reactors instead (batched sweep)")
     args = ap.parse_args()
@@ -514,7 +517,8 @@ def main():
                    "particles_per_rank": main_r["n0"],
                    "l2": f"no flush: particle state ({main_r['n0'] * BYTES_PER_PARTICLE[args.precision] // 2 // 1000000} "
                          f"MB) is larger than L2 (129 MB)",
-                   "parallelism": f"{world} independent reactor replica(s), one per GPU"},
+                   "parallelism": f"{world} independent reactor replica(s), one per GPU",
+                   **({"ion_subcycle": args.ion_subcycle} if args.ion_subcycle > 1 else {})},
         "roofline": {"bound": "hbm", "kernel": "k_step (fused particle pass, both species)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,

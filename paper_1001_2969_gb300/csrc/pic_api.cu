@@ -351,6 +351,13 @@ __global__ void k_step_end(StepCtl *c, DevScalars *ds, int32_t *nmain0, const in
 }
 
 // sort epilogue: the sorted counts take effect for the next pass
+// a pass that holds the ions: the births its newborn ions join start at
+// the buffer's present count (skipped once the step has failed, so that a
+// dropped pass's newborns can be cut off again)
+__global__ void k_hold_ions(const StepCtl *c, int32_t *nb0, const int32_t *nb) {
+    if (c->halt) return;
+    *nb0 = *nb;
+}
 __global__ void k_sort_end(StepCtl *c, int32_t *nalive0, const int32_t *ntotal0, int32_t *nalive1,
                            const int32_t *ntotal1) {
     if (sort_skip(c)) return;
@@ -664,8 +671,12 @@ pic_status load_all(pic_handle *h) {
         if (n > 0) k_iota<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(d.perm, (int)n);
         const int32_t vals[8] = {(int32_t)n, 0, 0, 0, (int32_t)n, (int32_t)n, 0, 0};
         cudaMemcpyAsync(h->scal + s * 8, vals, sizeof(vals), cudaMemcpyHostToDevice, h->st);
+        // the stored state's cell counts (held ions keep them until their
+        // next moving pass; otherwise the first pass recounts)
+        cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), h->st);
+        launch_hist<T>(view<T>(d.main[0]), d.d_nmain[0], d.counts, h->st);
         d.next_id = (uint64_t)n;
-        h->launches += 2;
+        h->launches += 3;
     }
     h->cur = h->cur_i = 0;
     deposit_current<T>(h);
@@ -857,7 +868,8 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv) {
         if (s == 1 && !mv) {
             // held ions: deposit, counts and births stay; this pass's
             // newborns are numbered from the births already there
-            cudaMemcpyAsync(d.d_nb0, d.d_nbirths[idst], sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+            k_hold_ions<<<1, 1, 0, st>>>(h->sctl, d.d_nb0, d.d_nbirths[idst]);
+            h->launches += 1;
             continue;
         }
         cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), st);
@@ -1200,6 +1212,27 @@ pic_status window_t(pic_handle *h, int32_t nsteps, int32_t ckpt, const double *w
     return cuda_check(h, "window");
 }
 
+// After a failed call with ion subcycling: the ions as the last completed
+// step left them.  A dropped pass that held them had appended its newborn
+// ions to their births (cut off again); a dropped pass that moved them had
+// recounted their cells.  So the counts, the permutation and the count of
+// ions are rebuilt from the state, and the deposit with them.
+template <typename T>
+void resync_ions(pic_handle *h, bool cut_births) {
+    SpecDev &d = h->sp[1];
+    const int c = h->cur_i;
+    if (cut_births) cudaMemcpyAsync(d.d_nbirths[c], d.d_nb0, sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
+    cudaMemsetAsync(d.d_nb0, 0, sizeof(int32_t), h->st);
+    cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), h->st);
+    launch_hist<T>(view<T>(d.main[c]), d.d_nmain[c], d.counts, h->st);
+    launch_hist<T>(view<T>(d.births[c]), d.d_nbirths[c], d.counts, h->st);
+    launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, nullptr, h->st);
+    launch_rank<T>(view<T>(d.main[c]), d.d_nmain[c], view<T>(d.births[c]), d.d_nbirths[c], d.cursor, d.perm,
+                   d.d_ntotal, d.cap, &h->ds->status, nullptr, h->ncell, h->st);
+    cudaMemcpyAsync(d.d_nalive, d.d_ntotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
+    h->launches += 6;
+}
+
 pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int cur_i0, int32_t nsteps) {
     StepCtl c;
     int32_t status = 0;
@@ -1240,6 +1273,19 @@ pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int cur_i0, int32
         cudaMemcpyAsync(&h->sctl->sort_pending, z, 3 * sizeof(int32_t), cudaMemcpyHostToDevice, h->st);
         cudaMemsetAsync(&h->ds->status, 0, 4, h->st);
         const int why = c.sort_fail ? c.sort_fail_status : c.halt_status;
+        if (h->K > 1) {
+            const bool cut = c.sort_fail && !moves_ions(h, c.sort_fail_step);
+            if (h->mixed)
+                resync_ions<float>(h, cut);
+            else
+                resync_ions<double>(h, cut);
+            if (!(why & (ST_CAPACITY | ST_BIRTH_OVERFLOW))) {
+                if (h->mixed)
+                    deposit_current<float>(h);
+                else
+                    deposit_current<double>(h);
+            }
+        }
         if (why & (ST_CAPACITY | ST_BIRTH_OVERFLOW)) {
             if (h->mixed)
                 deposit_current<float>(h);

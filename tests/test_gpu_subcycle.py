@@ -180,6 +180,31 @@ def test_checkpoint_while_newborn_ions_wait(pic, tmp_path):
         pic.pic_load(pic.pic_init(other, load=False), path)
 
 
+def test_births_overflow_in_a_holding_pass_keeps_the_last_completed_step(pic):
+    """Held ions collect newborns over passes 0, 1 and 2 (about 400 a pass
+    here) in a births buffer of 900: pass 2 overflows it, the call fails
+    with the capacity status, and the state is the one after pass 1 -- the
+    ions' births, counts, order and deposit included."""
+    cfg = dict(_cfg("fp64"), births_capacity=900)
+    e, i = _state(cfg, 60_001, 40_003, seed=5)
+    h, _ = _pair(pic, cfg, e, i, 0)
+    ref, _ = _pair(pic, _cfg("fp64"), e, i, 0)
+    with pytest.raises(pic.PicError) as err:
+        pic.pic_step(h, 3)
+    assert err.value.status == pic.PIC_ERR_CAPACITY
+    assert pic.pic_step(ref, 2) == 0
+    assert pic.pic_get_counts(h)["step"] == 2
+    assert list(pic.pic_get_counts(h)["n_alive"]) == list(pic.pic_get_counts(ref)["n_alive"])
+    for s in (0, 1):
+        u, v = by_id(pic.pic_get_particles(ref, s)), by_id(pic.pic_get_particles(h, s))
+        assert np.array_equal(u["id"], v["id"]), s
+        for k in FIELDS:
+            assert nerr(v[k], u[k]) < 1e-12, (s, k)
+    fh, fr = pic.pic_get_fields(h), pic.pic_get_fields(ref)
+    for name in ("rho", "chi"):
+        assert nerr(fh[name], fr[name]) < 1e-12, name
+
+
 def test_particle_steps_count_moved_ions_only(pic):
     cfg = W.collisionless(_cfg("fp64"))
     n = 10_000
