@@ -206,7 +206,13 @@ pic_status pic_init(const pic_config *cfg, pic_handle **out);
  * once at the end.  Returns the first non-OK status of the steps;
  * PIC_ERR_NOT_CONVERGED is non-fatal (the step completes).  On
  * PIC_ERR_CAPACITY and PIC_ERR_TIMEOUT the particle state is left at the last
- * completed step.
+ * completed step.  The last pass's re-sort is checked for capacity before
+ * the call returns; its rank and births numbering run beside the next
+ * step's solve, or at the start of the next call that reads or replaces the
+ * particle state (pic_get_particles, pic_set_particles, pic_get_counts,
+ * pic_set_step, pic_save, pic_load, pic_window).  Should that numbering time
+ * out (PIC_ERR_TIMEOUT from that call), the pass is dropped and the state is
+ * left at the step before it.
  */
 pic_status pic_step(pic_handle *h, int32_t nsteps);
 

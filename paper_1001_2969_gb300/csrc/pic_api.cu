@@ -113,6 +113,8 @@ struct pic_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
     StepGraph graphs[8];       // per (cur, cur_i, the pass moves the ions)
     StepGraph sort_graphs[4];  // the last pass's cell sort at the end of a call, per (cur, cur_i)
+    StepGraph check_graphs[4];  // its capacity check alone (the rest deferred), per (cur, cur_i)
+    bool sort_deferred = false;  // the last pass's rank and births numbering are still to run
     bool in_batch = false;     // stepped with other reactors (pic_batch): narrow solves
     double ngas = 0.0, nu_max[2] = {0, 0}, p_null[2] = {0, 0};
     unsigned long long t_null[2] = {0, 0};
@@ -915,6 +917,21 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv) {
     h->cur_i = idst;
 }
 
+// the capacity check of the last pass's sort alone (end of a call): the
+// scans of the cell counts and the check.  Rank, births numbering and the
+// sorted counts stay pending; the next step's graph runs them beside its
+// solve, or complete_sort() before the state is read.  Scans and check are
+// idempotent on unchanged counts, so running them again there is harmless.
+void check_tail(pic_handle *h) {
+    PhaseTimer t(h, 3);
+    for (int s = 0; s < 2; ++s) {
+        SpecDev &d = h->sp[s];
+        launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, h->sctl, h->st);
+    }
+    launch_step_check(h->ds, h->sctl, h->st);
+    h->launches += 7;
+}
+
 // the pending sort of the last pass (end of a call), on h->st
 template <typename T>
 void sort_tail(pic_handle *h) {
@@ -929,6 +946,10 @@ void drop_graphs(pic_handle *h) {
         g = StepGraph();
     }
     for (StepGraph &g : h->sort_graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = StepGraph();
+    }
+    for (StepGraph &g : h->check_graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g = StepGraph();
     }
@@ -972,16 +993,20 @@ void capture_step(pic_handle *h, StepGraph &g, bool mv) {
     }
 }
 
-// capture the pending sort of the current parity (the end of a call)
+// capture the pending sort of the current parity (the end of a call), or
+// its capacity check alone
 template <typename T>
-void capture_sort(pic_handle *h, StepGraph &g) {
+void capture_sort(pic_handle *h, StepGraph &g, bool check_only) {
     const int64_t L0 = h->launches;
     cudaStream_t keep = h->st;
     h->st = h->gst;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        sort_tail<T>(h);
+        if (check_only)
+            check_tail(h);
+        else
+            sort_tail<T>(h);
         e = cudaStreamEndCapture(h->gst, &graph);
     }
     h->st = keep;
@@ -996,14 +1021,15 @@ void capture_sort(pic_handle *h, StepGraph &g) {
     }
 }
 
-// enqueue the pending sort on stream `on` (private stream: as a graph)
-void enqueue_sort_tail(pic_handle *h, cudaStream_t on) {
-    StepGraph &g = h->sort_graphs[h->cur + 2 * h->cur_i];
+// enqueue the pending sort, or its capacity check alone, on stream `on`
+// (private stream: as a graph)
+void enqueue_sort_tail(pic_handle *h, cudaStream_t on, bool check_only = false) {
+    StepGraph &g = (check_only ? h->check_graphs : h->sort_graphs)[h->cur + 2 * h->cur_i];
     if (on == h->gst && !g.exec && !g.failed) {
         if (h->mixed)
-            capture_sort<float>(h, g);
+            capture_sort<float>(h, g, check_only);
         else
-            capture_sort<double>(h, g);
+            capture_sort<double>(h, g, check_only);
     }
     if (on == h->gst && g.exec) {
         cudaGraphLaunch(g.exec, h->gst);
@@ -1012,7 +1038,9 @@ void enqueue_sort_tail(pic_handle *h, cudaStream_t on) {
     }
     cudaStream_t keep = h->st;
     h->st = on;
-    if (h->mixed)
+    if (check_only)
+        check_tail(h);
+    else if (h->mixed)
         sort_tail<float>(h);
     else
         sort_tail<double>(h);
@@ -1303,6 +1331,16 @@ pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int cur_i0, int32
     return result;
 }
 
+// Finish the last pass's deferred sort (rank, births numbering, sorted
+// counts) before the particle state is read or replaced.  A failure there
+// (the numbering's grid barrier timing out) drops that pass, as in a call.
+pic_status complete_sort(pic_handle *h) {
+    if (!h->sort_deferred) return PIC_OK;
+    h->sort_deferred = false;
+    enqueue_sort_tail(h, h->st);
+    return finish_call(h, h->step, h->cur, h->cur_i, 0);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1448,13 +1486,18 @@ pic_status pic_step(pic_handle *h, int32_t nsteps) {
         else
             one_step<double>(h, nullptr, mv);
     }
-    // the last pass's sort: the state between calls is sorted
-    enqueue_sort_tail(h, on_gst ? h->gst : h->st);
+    // the last pass's sort: its capacity check now (a failure is this
+    // call's); its rank and births numbering run beside the next step's
+    // solve, or before the particle state is read (complete_sort)
+    enqueue_sort_tail(h, on_gst ? h->gst : h->st, true);
     if (on_gst) {
         cudaEventRecord(h->ev_out, h->gst);
         cudaStreamWaitEvent(h->st, h->ev_out, 0);
     }
-    return finish_call(h, step0, cur0, cur_i0, nsteps);
+    const pic_status r = finish_call(h, step0, cur0, cur_i0, nsteps);
+    // a failed step leaves the state at the last completed step, sorted
+    h->sort_deferred = r == PIC_OK || r == PIC_ERR_NOT_CONVERGED || r == PIC_ERR_NUMERIC;
+    return r;
 }
 
 pic_status pic_tune(pic_handle *h, int32_t steps_per_variant, int32_t *variants) {
@@ -1578,9 +1621,9 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
             StepGraph &g = h->sort_graphs[h->cur + 2 * h->cur_i];
             if (!g.exec && !g.failed) {
                 if (h->mixed)
-                    capture_sort<float>(h, g);
+                    capture_sort<float>(h, g, false);
                 else
-                    capture_sort<double>(h, g);
+                    capture_sort<double>(h, g, false);
             }
         }
         cudaEventRecord(b->ev_fork, b->origin);
@@ -1599,6 +1642,7 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
     pic_status first = PIC_OK;
     for (size_t k = 0; k < nh; ++k) {
         const pic_status r = nsteps > 0 ? finish_call(b->hs[k], step0[k], cur0[k], cur0[k], nsteps) : PIC_OK;
+        if (nsteps > 0) b->hs[k]->sort_deferred = false;  // the batch ends with the whole sort
         if (statuses) statuses[k] = r;
         if (first == PIC_OK && r != PIC_OK) first = r;
     }
@@ -1699,6 +1743,8 @@ pic_status pic_moments(pic_handle *h, pic_moments_out *out, int32_t reset) {
 
 pic_status pic_get_particles(pic_handle *h, int32_t s, pic_particles_view *view_, int64_t capacity) {
     if (!h || !view_ || s < 0 || s > 1) return fail(h, PIC_ERR_ARG, "bad argument");
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
     try {
         return h->mixed ? get_particles_t<float>(h, s, view_, capacity)
                         : get_particles_t<double>(h, s, view_, capacity);
@@ -1711,6 +1757,8 @@ pic_status pic_set_particles(pic_handle *h, int32_t s, const pic_particles_view 
     if (!h || !v || s < 0 || s > 1 || v->n < 0) return fail(h, PIC_ERR_ARG, "bad argument");
     if (v->n > 0 && (!v->r || !v->z || !v->vr || !v->vt || !v->vz || !v->ar || !v->az || !v->w || !v->id))
         return fail(h, PIC_ERR_ARG, "null particle array");
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
     try {
         pic_status st = h->mixed ? set_particles_t<float>(h, s, v) : set_particles_t<double>(h, s, v);
         return st;
@@ -1721,6 +1769,8 @@ pic_status pic_set_particles(pic_handle *h, int32_t s, const pic_particles_view 
 
 pic_status pic_set_step(pic_handle *h, int64_t step) {
     if (!h || step < 0) return fail(h, PIC_ERR_ARG, "bad step");
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
     h->step = step;
     push_ctl(h);
     return cuda_check(h, "set_step");
@@ -1760,6 +1810,8 @@ pic_status pic_get_fields(pic_handle *h, double *rho, double *chi, double *phi, 
 
 pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64_t *next_id) {
     if (!h) return PIC_ERR_ARG;
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
     int32_t n[2] = {0, 0};
     for (int s = 0; s < 2; ++s) cudaMemcpyAsync(&n[s], h->sp[s].d_nalive, 4, cudaMemcpyDeviceToHost, h->st);
     cudaStreamSynchronize(h->st);
@@ -1792,6 +1844,8 @@ pic_status pic_window(pic_handle *h, int32_t nsteps, int32_t ckpt, const double 
     if (h->cfg.rf.n < 1) return fail(h, PIC_ERR_ARG, "the window needs an rf component");
     if (h->cfg.pusher != PIC_PUSH_LOCAL) return fail(h, PIC_ERR_ARG, "the window takes the local pusher");
     if (h->K > 1) return fail(h, PIC_ERR_ARG, "the window moves the ions every step (no subcycling)");
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
     return h->mixed ? window_t<float>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL)
                     : window_t<double>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL);
 }
@@ -1800,6 +1854,8 @@ static const uint64_t kCkptMagic = 0x50494352475a3031ull;  // "PICRGZ01"
 
 pic_status pic_save(pic_handle *h, const char *path) {
     if (!h || !path) return PIC_ERR_ARG;
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
     FILE *f = fopen(path, "wb");
     if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint for writing");
     const int circuit = h->cfg.circuit_C > 0.0 ? 1 : 0;
@@ -1859,6 +1915,8 @@ pic_status pic_save(pic_handle *h, const char *path) {
 
 pic_status pic_load(pic_handle *h, const char *path) {
     if (!h || !path) return PIC_ERR_ARG;
+    const pic_status pending = complete_sort(h);
+    if (pending != PIC_OK) return pending;
     FILE *f = fopen(path, "rb");
     if (!f) return fail(h, PIC_ERR_ARG, "cannot open checkpoint");
     int64_t hdr[8];
