@@ -48,9 +48,11 @@ struct StepCtl {
     int32_t bar_timeout;  // a bounded wait of the births numbering gave up
     double circ_V, circ_Q, circ_Qc;  // external circuit: electrode voltage and charge, capacitor charge
     // The cell sort of a pass (scan, capacity check, rank, births numbering)
-    // runs in the next step beside its field solve, or at the end of the
-    // call: pending from the end of the pass until it is done.  A failed sort
-    // (capacity, births overflow, a wait that gave up) also halts the step.
+    // runs in the next step beside its field solve, or before the particle
+    // state is read (the end of a call runs its scans and capacity check
+    // only): pending from the end of the pass until it is done.  A failed
+    // sort (capacity, births overflow, a wait that gave up) also halts the
+    // step.
     int32_t sort_pending;
     int32_t sort_fail;         // the sort failed: later sort kernels do nothing
     int32_t sort_fail_status;  // ST_* bits of the failure
