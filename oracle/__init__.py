@@ -94,6 +94,8 @@ def _declare(L):
     L.orc_get_step.argtypes = [vp]
     L.orc_ion_pass.restype = C.c_int
     L.orc_ion_pass.argtypes = [vp]
+    L.orc_merge.restype = C.c_int64
+    L.orc_merge.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_double)]
     L.orc_load.argtypes = [vp]
     L.orc_load_range.argtypes = [vp, C.c_int, C.c_int64, C.c_int64] + [_dp] * 8 + [_u64p]
     L.orc_deposit.argtypes = [vp]
@@ -266,6 +268,12 @@ class Oracle:
 
     def step_index(self):
         return lib().orc_get_step(self.h)
+
+    def merge(self, s, frac, dv):
+        """Merge light particles of species s in pairs; (pairs, energy lost in J)."""
+        e = C.c_double(0)
+        n = lib().orc_merge(self.h, s, float(frac), float(dv), C.byref(e))
+        return int(n), e.value
 
     def ion_pass(self):
         """True when the next pass moves the ions (ion subcycling)."""

@@ -1256,6 +1256,115 @@ static void split(orc_state *st, int s, uint64_t id, orc_p *q) {
     for (int k = 0; k < N; ++k) newborn(st, s, s, id, 2 + k, copy);
 }
 
+/*
+ * Particle merging (Sec. 2.2 names the need to combine small particles
+ * and points to a reference; it gives no algorithm).  READING: particles of
+ * species s lighter than frac * w_r (w_r of their radial cell, as for the
+ * split) are grouped by cell of x~ and by velocity bin, the bin of each
+ * component being floor(v / dv) (clamped to +-2^20); inside a group they are
+ * taken in order of id and merged in pairs, the odd last one left alone.
+ * The pair (a, b), id a < id b, becomes one particle with id a and
+ *   w = w_a + w_b,  z = <z>,  r^2 = <r^2>,  v_r = <v_r>,  v_z = <v_z>,
+ *   a_r = <a_r>,  a_z = <a_z>,  v_theta = <r v_theta> / r  (and a_theta
+ *   likewise), <x> = (w_a x_a + w_b x_b) / w,
+ * which keeps the charge, the z and r^2 moments (so the cell, and the z-r^2
+ * deposit's totals and first moments), the radial and axial momentum, the
+ * angular momentum and the implicit current sum w a.  The kinetic energy
+ * the velocity spread held, (m/2) w_a w_b / w |v_a - v_b|^2 in the local
+ * components, is lost; *energy_J returns it.  Returns the pairs merged.
+ */
+typedef struct {
+    int64_t k;      /* index in the store */
+    int64_t cell;   /* j (nz-1) + i       */
+    uint64_t key;   /* velocity bin       */
+    uint64_t id;
+} orc_cand;
+
+static int cand_cmp(const void *pa, const void *pb) {
+    const orc_cand *a = pa, *b = pb;
+    if (a->cell != b->cell) return a->cell < b->cell ? -1 : 1;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    if (a->id != b->id) return a->id < b->id ? -1 : 1;
+    return 0;
+}
+
+static uint64_t vbin(double v, double dv) {
+    double b = floor(v / dv);
+    if (b < -1048576.0) b = -1048576.0;
+    if (b > 1048575.0) b = 1048575.0;
+    return (uint64_t)((int64_t)b + 1048576);
+}
+
+int64_t orc_merge(orc_state *st, int s, double frac, double dv, double *energy_J) {
+    orc_store *P = &st->p[s];
+    orc_cand *c = xmalloc((P->n > 0 ? P->n : 1) * sizeof(orc_cand));
+    int64_t nc = 0;
+    for (int64_t k = 0; k < P->n; ++k) {
+        int i = cell_z(st, P->z[k]), j = cell_r(st, P->r[k]);
+        if (!(P->w[k] < frac * orc_w_ref(st, s, j))) continue;
+        c[nc].k = k;
+        c[nc].cell = (int64_t)j * (st->c.nz - 1) + i;
+        c[nc].key = (vbin(P->vr[k], dv) << 42) | (vbin(P->vt[k], dv) << 21) | vbin(P->vz[k], dv);
+        c[nc].id = P->id[k];
+        ++nc;
+    }
+    qsort(c, nc, sizeof(orc_cand), cand_cmp);
+    char *gone = calloc(P->n > 0 ? P->n : 1, 1);
+    int64_t pairs = 0;
+    double lost = 0.0;
+    for (int64_t q = 0; q < nc;) {
+        int64_t e = q + 1;
+        while (e < nc && c[e].cell == c[q].cell && c[e].key == c[q].key) ++e;
+        for (int64_t u = q; u + 1 < e; u += 2) {
+            int64_t a = c[u].k, b = c[u + 1].k;
+            double wa = P->w[a], wb = P->w[b], W = wa + wb;
+            double ra = P->r[a], rb = P->r[b];
+            double r = sqrt((wa * ra * ra + wb * rb * rb) / W);
+            double vr = (wa * P->vr[a] + wb * P->vr[b]) / W;
+            double vz = (wa * P->vz[a] + wb * P->vz[b]) / W;
+            double Lt = wa * ra * P->vt[a] + wb * rb * P->vt[b];
+            double Lat = wa * ra * P->at[a] + wb * rb * P->at[b];
+            double vt = r > 0.0 ? Lt / (W * r) : (wa * P->vt[a] + wb * P->vt[b]) / W;
+            double at = r > 0.0 ? Lat / (W * r) : (wa * P->at[a] + wb * P->at[b]) / W;
+            double e0 = wa * (P->vr[a] * P->vr[a] + P->vt[a] * P->vt[a] + P->vz[a] * P->vz[a]) +
+                        wb * (P->vr[b] * P->vr[b] + P->vt[b] * P->vt[b] + P->vz[b] * P->vz[b]);
+            lost += 0.5 * st->c.m[s] * (e0 - W * (vr * vr + vt * vt + vz * vz));
+            P->z[a] = (wa * P->z[a] + wb * P->z[b]) / W;
+            P->r[a] = r;
+            P->vr[a] = vr;
+            P->vt[a] = vt;
+            P->vz[a] = vz;
+            P->ar[a] = (wa * P->ar[a] + wb * P->ar[b]) / W;
+            P->az[a] = (wa * P->az[a] + wb * P->az[b]) / W;
+            P->at[a] = at;
+            P->w[a] = W;
+            gone[b] = 1;
+            ++pairs;
+        }
+        q = e;
+    }
+    int64_t out = 0;
+    for (int64_t k = 0; k < P->n; ++k) {
+        if (gone[k]) continue;
+        P->r[out] = P->r[k];
+        P->z[out] = P->z[k];
+        P->vr[out] = P->vr[k];
+        P->vt[out] = P->vt[k];
+        P->vz[out] = P->vz[k];
+        P->ar[out] = P->ar[k];
+        P->az[out] = P->az[k];
+        P->at[out] = P->at[k];
+        P->w[out] = P->w[k];
+        P->id[out] = P->id[k];
+        ++out;
+    }
+    P->n = out;
+    free(gone);
+    free(c);
+    if (energy_J) *energy_J = lost;
+    return pairs;
+}
+
 static int eedf_bin(const orc_state *st, double E) {
     if (st->c.eedf_bins <= 0 || !(E >= 0.0)) return -1;
     double x = E / st->c.eedf_emax * st->c.eedf_bins;

@@ -121,6 +121,9 @@ void orc_set_step(orc_state *st, int64_t step);
 int64_t orc_get_step(const orc_state *st);
 /* 1 when the next pass moves the ions (always without subcycling) */
 int orc_ion_pass(const orc_state *st);
+/* merge light particles of species s in pairs (see oracle.c); returns the
+ * pairs merged, *energy_J the kinetic energy their velocity spread held */
+int64_t orc_merge(orc_state *st, int s, double frac, double dv, double *energy_J);
 
 /* external circuit state: out[0] electrode voltage V, out[1] electrode
  * charge Q, out[2] capacitor charge Q_c (C, after the last step) */
