@@ -348,6 +348,25 @@ pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64
 pic_status pic_get_circuit(pic_handle *h, double *out);
 
 /*
+ * pic_merge -- combine light particles of species s in pairs (Sec. 2.2 says
+ * small particles sometimes need combining and gives no algorithm; this is
+ * the library's reading).  Particles lighter than frac times the split's
+ * reference weight of their radial cell are grouped by cell and by velocity
+ * bin (each component's floor(v / dv), dv in m/s), taken in order of id
+ * within a group, and merged in pairs into the lower id: weight summed; z,
+ * r^2, v_r, v_z, a_r, a_z as weight-means; v_theta (and a_theta) so that the
+ * angular momentum is kept at the merged radius.  Charge, the z and r^2
+ * moments (hence the cell and the deposit's totals and first moments),
+ * radial and axial momentum, angular momentum and sum w a are kept; the
+ * kinetic energy of the pairs' velocity spread is lost and returned in
+ * *energy_J (nullable), the pairs in *pairs (nullable).  The deposit is
+ * redone.  Errors: PIC_ERR_ARG (s, frac or dv), PIC_ERR_CAPACITY (a cell
+ * with more than 1024 light particles of s: that cell is left as it was),
+ * PIC_ERR_CUDA.
+ */
+pic_status pic_merge(pic_handle *h, int32_t s, double frac, double dv, int64_t *pairs, double *energy_J);
+
+/*
  * pic_window -- a collisionless window of the timestep and the gradient of a
  * time-averaged ion-density functional by a hand-written adjoint (the
  * paper's timestep, Sec. 2.1 merged cycle, with the Monte Carlo step of

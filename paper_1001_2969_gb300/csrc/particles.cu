@@ -6,6 +6,8 @@
 // in [0, 1), so single precision keeps its resolution at large radius.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pmath.cuh"
 
 namespace pic {
@@ -794,8 +796,194 @@ void launch_to_abs(PBuf<T> sm, PBuf<T> sb, const int32_t *n_main_src, const int3
                                                               dr);
 }
 
+// ---------------------------------------------------------------------------
+// merging of light particles in pairs (Sec. 2.2 names the need, no
+// algorithm): one block per cell of the sorted store.  The cell's particles
+// lighter than frac * w_r(j) are collected in shared memory, sorted by
+// (velocity bin, id), and consecutive ones of a bin are merged in pairs
+// into the lower id: w, z, r^2, v_r, v_z, a_r, a_z as weighted means,
+// v_theta (and a_theta) from the angular momentum at the merged radius.
+// The other one of a pair is left as a dead record (cell -1), which the
+// re-sort that follows drops.
+// ---------------------------------------------------------------------------
+constexpr int kMergeCap = 1024;  // light particles of one cell a block can take
+constexpr int kMergeThreads = 256;
+
+__device__ __forceinline__ uint64_t vbin_of(double v, double dv) {
+    double b = floor(v / dv);
+    b = fmin(fmax(b, -1048576.0), 1048575.0);
+    return (uint64_t)((int64_t)b + 1048576);
+}
+
+__device__ __forceinline__ bool key_less(uint64_t ka, uint64_t ia, uint64_t kb, uint64_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMergeThreads)
+    k_merge(PBuf<T> mainb, PBuf<T> births, const int32_t *nmain_dev, const int32_t *perm, const int32_t *cursor,
+            int ncell, int ncz, double dz, double dr, const T *w_ref, double frac, double dv, double mass, int xyz,
+            unsigned long long *pairs_out, double *energy_out, int *overflow) {
+    __shared__ uint64_t s_key[kMergeCap], s_id[kMergeCap];
+    __shared__ int32_t s_loc[kMergeCap], s_first[kMergeCap / 2];
+    __shared__ int s_n, s_np;
+    __shared__ double s_red[kMergeThreads / 32];
+    __shared__ unsigned long long s_cnt[kMergeThreads / 32];
+    const int tid = threadIdx.x;
+    const int nmain = *nmain_dev;
+    double e_mine = 0.0;
+    unsigned long long p_mine = 0;
+    for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+        // cursor holds each cell's end in the permutation (after the rank)
+        const int start = c > 0 ? cursor[c - 1] : 0, end = cursor[c];
+        if (end - start >= 2) {
+            const int i = c % ncz, j = c / ncz;
+            const double thr = frac * (double)w_ref[j];
+            if (tid == 0) s_n = 0;
+            __syncthreads();
+            for (int q = start + tid; q < end; q += blockDim.x) {
+                const int loc = perm[q];
+                const bool in_main = loc < nmain;
+                const PBuf<T> &b = in_main ? mainb : births;
+                const int k = in_main ? loc : loc - nmain;
+                const PS<T> p = load_p(b, k, ncz);
+                if ((double)p.w < thr) {
+                    const int slot = atomicAdd(&s_n, 1);
+                    if (slot < kMergeCap) {
+                        s_key[slot] = (vbin_of((double)p.vr, dv) << 42) | (vbin_of((double)p.vt, dv) << 21) |
+                                      vbin_of((double)p.vz, dv);
+                        s_id[slot] = b.id[k];
+                        s_loc[slot] = loc;
+                    }
+                }
+            }
+            __syncthreads();
+            const int n = s_n;
+            if (n > kMergeCap) {
+                if (tid == 0) atomicExch(overflow, 1);
+            } else if (n >= 2) {
+                int P = 2;
+                while (P < n) P <<= 1;
+                for (int t = n + tid; t < P; t += blockDim.x) {
+                    s_key[t] = ~0ull;
+                    s_id[t] = ~0ull;
+                    s_loc[t] = -1;
+                }
+                __syncthreads();
+                // bitonic sort by (bin, id)
+                for (int kk = 2; kk <= P; kk <<= 1)
+                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                        for (int t = tid; t < P; t += blockDim.x) {
+                            const int u = t ^ jj;
+                            if (u > t) {
+                                const bool up = (t & kk) == 0;
+                                const bool gt = key_less(s_key[u], s_id[u], s_key[t], s_id[t]);
+                                if (up == gt) {
+                                    const uint64_t k0 = s_key[t], i0 = s_id[t];
+                                    const int32_t l0 = s_loc[t];
+                                    s_key[t] = s_key[u];
+                                    s_id[t] = s_id[u];
+                                    s_loc[t] = s_loc[u];
+                                    s_key[u] = k0;
+                                    s_id[u] = i0;
+                                    s_loc[u] = l0;
+                                }
+                            }
+                        }
+                        __syncthreads();
+                    }
+                // pairs: consecutive entries of one bin, from the bin's first
+                if (tid == 0) {
+                    int np = 0;
+                    for (int u = 0; u < n;) {
+                        int e = u + 1;
+                        while (e < n && s_key[e] == s_key[u]) ++e;
+                        for (int v = u; v + 1 < e; v += 2) s_first[np++] = v;
+                        u = e;
+                    }
+                    s_np = np;
+                }
+                __syncthreads();
+                for (int q = tid; q < s_np; q += blockDim.x) {
+                    const int u = s_first[q];
+                    const int la = s_loc[u], lb = s_loc[u + 1];
+                    const PBuf<T> &ba = la < nmain ? mainb : births;
+                    const PBuf<T> &bb = lb < nmain ? mainb : births;
+                    const int ka = la < nmain ? la : la - nmain, kb = lb < nmain ? lb : lb - nmain;
+                    const PS<T> a = load_p(ba, ka, ncz), b = load_p(bb, kb, ncz);
+                    const double wa = a.w, wb = b.w, W = wa + wb;
+                    const double za = (i + (double)a.oz) * dz, zb = (i + (double)b.oz) * dz;
+                    const double ra = (j + (double)a.orr) * dr, rb = (j + (double)b.orr) * dr;
+                    const double r = sqrt((wa * ra * ra + wb * rb * rb) / W);
+                    const double vr = (wa * a.vr + wb * b.vr) / W, vz = (wa * a.vz + wb * b.vz) / W;
+                    const double vt = r > 0.0 ? (wa * ra * a.vt + wb * rb * b.vt) / (W * r) : (wa * a.vt + wb * b.vt) / W;
+                    const double e0 = wa * ((double)a.vr * a.vr + (double)a.vt * a.vt + (double)a.vz * a.vz) +
+                                      wb * ((double)b.vr * b.vr + (double)b.vt * b.vt + (double)b.vz * b.vz);
+                    e_mine += 0.5 * mass * (e0 - W * (vr * vr + vt * vt + vz * vz));
+                    double oz = ((wa * za + wb * zb) / W) / dz - i, orr = r / dr - j;
+                    oz = fmin(fmax(oz, 0.0), (double)below_one<T>());
+                    orr = fmin(fmax(orr, 0.0), (double)below_one<T>());
+                    PS<T> m = a;
+                    m.oz = (T)oz;
+                    m.orr = (T)orr;
+                    m.vr = (T)vr;
+                    m.vt = (T)vt;
+                    m.vz = (T)vz;
+                    m.ar = (T)((wa * a.ar + wb * b.ar) / W);
+                    m.az = (T)((wa * a.az + wb * b.az) / W);
+                    m.w = (T)W;
+                    store_p(ba, ka, m, c, s_id[u]);
+                    if (xyz) {
+                        const double ata = ba.at[ka], atb = bb.at[kb];
+                        ba.at[ka] = (T)(r > 0.0 ? (wa * ra * ata + wb * rb * atb) / (W * r) : (wa * ata + wb * atb) / W);
+                    }
+                    bb.cell[kb] = -1;
+                    ++p_mine;
+                }
+            }
+        }
+        __syncthreads();  // the cell's shared arrays are free again
+    }
+    // block sums of the energy lost and the pairs merged
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        e_mine += __shfl_down_sync(0xffffffffu, e_mine, o);
+        p_mine += __shfl_down_sync(0xffffffffu, p_mine, o);
+    }
+    if (lane == 0) {
+        s_red[warp] = e_mine;
+        s_cnt[warp] = p_mine;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double e = 0.0;
+        unsigned long long p = 0;
+        for (int w = 0; w < kMergeThreads / 32; ++w) {
+            e += s_red[w];
+            p += s_cnt[w];
+        }
+        if (p) {
+            atomicAdd(energy_out, e);
+            atomicAdd(pairs_out, p);
+        }
+    }
+}
+
+template <typename T>
+void launch_merge(PBuf<T> mainb, PBuf<T> births, const int32_t *nmain_dev, const int32_t *perm,
+                  const int32_t *cursor, int ncell, int ncz, double dz, double dr, const T *w_ref, double frac,
+                  double dv, double mass, int xyz, unsigned long long *pairs, double *energy, int *overflow,
+                  cudaStream_t st) {
+    const int grid = std::max(1, std::min(ncell, 152 * 4));
+    k_merge<T><<<grid, kMergeThreads, 0, st>>>(mainb, births, nmain_dev, perm, cursor, ncell, ncz, dz, dr, w_ref,
+                                                frac, dv, mass, xyz, pairs, energy, overflow);
+}
+
 #define PIC_INST(T)                                                                              \
     template void launch_step<T>(const StepArgs<T> &, int, int, cudaStream_t);                   \
+    template void launch_merge<T>(PBuf<T>, PBuf<T>, const int32_t *, const int32_t *, const int32_t *, int, \
+                                  int, double, double, const T *, double, double, double, int,             \
+                                  unsigned long long *, double *, int *, cudaStream_t);                    \
     template void launch_load<T>(PBuf<T>, int64_t, int, int, int, double, double, double, double, \
                                  double, uint32_t, uint32_t, int64_t, cudaStream_t);              \
     template void launch_deposit<T>(PBuf<T>, const int32_t *, int, int, int, double *,           \

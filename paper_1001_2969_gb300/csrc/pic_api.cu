@@ -1850,6 +1850,64 @@ pic_status pic_window(pic_handle *h, int32_t nsteps, int32_t ckpt, const double 
                     : window_t<double>(h, nsteps, ckpt, w, amp0, phi_zL, grad != 0, J, dJ_damp, dJ_dphi_zL);
 }
 
+pic_status pic_merge(pic_handle *h, int32_t s, double frac, double dv, int64_t *pairs, double *energy_J) {
+    if (!h || s < 0 || s > 1 || !(frac > 0.0) || !std::isfinite(frac) || !(dv > 0.0) || !std::isfinite(dv))
+        return fail(h, PIC_ERR_ARG, "merge: species 0 or 1, frac and dv positive");
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
+    SpecDev &d = h->sp[s];
+    const int c = par_of(h, s);
+    struct Out {
+        unsigned long long pairs;
+        double energy;
+        int overflow;
+    };
+    Out *o = nullptr;
+    try {
+        o = (Out *)dalloc(h, sizeof(Out));
+    } catch (const std::bad_alloc &) {
+        return fail(h, PIC_ERR_CUDA, "merge: allocation failed");
+    }
+    cudaMemsetAsync(o, 0, sizeof(Out), h->st);
+    // the cells' ends in the permutation of the sorted store: recount, scan
+    // and rank (the same order the store already has)
+    auto resort = [&](auto tag) {
+        using T = decltype(tag);
+        cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), h->st);
+        launch_hist<T>(view<T>(d.main[c]), d.d_nmain[c], d.counts, h->st);
+        launch_hist<T>(view<T>(d.births[c]), d.d_nbirths[c], d.counts, h->st);
+        launch_scan(d.counts, d.cursor, h->ncell, d.block_sums, d.d_ntotal, d.cap, h->ds, nullptr, h->st);
+        launch_rank<T>(view<T>(d.main[c]), d.d_nmain[c], view<T>(d.births[c]), d.d_nbirths[c], d.cursor, d.perm,
+                       d.d_ntotal, d.cap, &h->ds->status, nullptr, h->ncell, h->st);
+        cudaMemcpyAsync(d.d_nalive, d.d_ntotal, sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
+        h->launches += 6;
+    };
+    auto run = [&](auto tag) {
+        using T = decltype(tag);
+        resort(tag);
+        launch_merge<T>(view<T>(d.main[c]), view<T>(d.births[c]), d.d_nmain[c], d.perm, d.cursor, h->ncell, h->ncz,
+                        h->dz, h->dr, (const T *)d.w_ref, frac, dv, h->cfg.sp[s].m,
+                        h->cfg.pusher == PIC_PUSH_XYZ ? 1 : 0, &o->pairs, &o->energy, &o->overflow, h->st);
+        h->launches += 1;
+        resort(tag);  // drops the merged-away records
+        deposit_current<T>(h);
+    };
+    if (h->mixed)
+        run(0.0f);
+    else
+        run(0.0);
+    Out out;
+    cudaMemcpyAsync(&out, o, sizeof(Out), cudaMemcpyDeviceToHost, h->st);
+    cudaStreamSynchronize(h->st);
+    release(h, o);
+    if (pairs) *pairs = (int64_t)out.pairs;
+    if (energy_J) *energy_J = out.energy;
+    const pic_status ce = cuda_check(h, "merge");
+    if (ce != PIC_OK) return ce;
+    if (out.overflow) return fail(h, PIC_ERR_CAPACITY, "merge: a cell held more light particles than one block takes");
+    return PIC_OK;
+}
+
 static const uint64_t kCkptMagic = 0x50494352475a3031ull;  // "PICRGZ01"
 
 pic_status pic_save(pic_handle *h, const char *path) {

@@ -241,6 +241,13 @@ template <typename T>
 void launch_load(PBuf<T> dst, int64_t n, int s, int nz, int nr, double dz, double dr,
                  double n0, double T_eV, double m, uint32_t key0, uint32_t key1,
                  int64_t ncell_pop, cudaStream_t st);
+// merges the light particles of each cell in pairs (k_merge in particles.cu);
+// cursor: each cell's end in the permutation
+template <typename T>
+void launch_merge(PBuf<T> mainb, PBuf<T> births, const int32_t *nmain_dev, const int32_t *perm,
+                  const int32_t *cursor, int ncell, int ncz, double dz, double dr, const T *w_ref, double frac,
+                  double dv, double mass, int xyz, unsigned long long *pairs, double *energy, int *overflow,
+                  cudaStream_t st);
 template <typename T>
 void launch_deposit(PBuf<T> src, const int32_t *n_dev, int nz, int nr, int weighting,
                     double *N, cudaStream_t st);
