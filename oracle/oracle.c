@@ -1271,7 +1271,8 @@ static void split(orc_state *st, int s, uint64_t id, orc_p *q) {
  * deposit's totals and first moments), the radial and axial momentum, the
  * angular momentum and the implicit current sum w a.  The kinetic energy
  * the velocity spread held, (m/2) w_a w_b / w |v_a - v_b|^2 in the local
- * components, is lost; *energy_J returns it.  Returns the pairs merged.
+ * components, is lost; *energy_J returns it.  The deposit of the stored
+ * state is redone (the next solve takes it).  Returns the pairs merged.
  */
 typedef struct {
     int64_t k;      /* index in the store */
@@ -1362,6 +1363,8 @@ int64_t orc_merge(orc_state *st, int s, double frac, double dv, double *energy_J
     free(gone);
     free(c);
     if (energy_J) *energy_J = lost;
+    /* the stored state's deposit follows the merged positions */
+    orc_deposit(st);
     return pairs;
 }
 

@@ -125,3 +125,39 @@ def test_a_cell_too_full_is_reported_and_left_alone(pic):
         pic.pic_merge(h, 0, 0.5, 1e9)
     assert err.value.status == pic.PIC_ERR_CAPACITY
     assert pic.pic_get_counts(h)["n_alive"][0] == n
+
+
+def test_merge_with_the_xyz_pusher_and_held_ions(pic):
+    """a_theta merges like v_theta (X-Y-Z pusher); ions merged while a
+    subcycled run holds them, then two steps (a holding and a moving pass):
+    the same as the oracle in FP64."""
+    cfg = dict(_cfg("fp64"), pusher="xyz", ion_subcycle=2, split_every=0)
+    rng = np.random.default_rng(12)
+    e = W.random_particles(cfg, 0, 30_000, seed=21, hot=3.0, accel=2e14, wscale=1.5e6)
+    i = W.random_particles(cfg, 1, 30_000, seed=22, hot=30.0, accel=5e9, wscale=1.5e6)
+    e["at"] = rng.normal(0.0, 2e14, 30_000)
+    i["at"] = rng.normal(0.0, 5e9, 30_000)
+    h = pic.pic_init(cfg, load=False)
+    o = Oracle(cfg)
+    for s, p in ((0, e), (1, i)):
+        pic.pic_set_particles(h, s, p)
+        o.set_particles(s, p)
+        o.set_at(s, p["at"])
+    pic.pic_set_step(h, 0)
+    o.set_step(0)
+    assert pic.pic_step(h, 1) == 0  # pass 0 holds the ions; newborn ions wait in their births
+    o.step(1)
+    for s in (0, 1):
+        n_g, _ = pic.pic_merge(h, s, 0.5, DV[s])
+        n_o, _ = o.merge(s, 0.5, DV[s])
+        assert n_g == n_o and n_o > 100, (s, n_g, n_o)
+    assert pic.pic_step(h, 2) == 0
+    o.step(2)
+    for s in (0, 1):
+        g = by_id(pic.pic_get_particles(h, s))
+        ref = o.get_particles(s)
+        ref["at"] = o.get_at(s)
+        ref = by_id(ref)
+        assert np.array_equal(g["id"], ref["id"])
+        for k in FIELDS + ("at",):
+            assert nerr(g[k], ref[k]) <= 1e-11, (s, k, nerr(g[k], ref[k]))
