@@ -798,7 +798,10 @@ void sort_finish(pic_handle *h, int par_e, int par_i, cudaStream_t st) {
     for (int s = 0; s < 2; ++s) {
         SpecDev &d = h->sp[s];
         const int par = s == 1 ? par_i : par_e;
-        launch_birth_ids(d.bkey[par], d.births[par].id, d.d_nbirths[par], d.d_nb0, h->sctl, s, h->rtmp, st);
+        // in a batch: at most 8 blocks (a step's births are few; the numbering
+        // is a cooperative launch, and a wide one waits for free SMs)
+        launch_birth_ids(d.bkey[par], d.births[par].id, d.d_nbirths[par], d.d_nb0, h->sctl, s, h->rtmp, st,
+                         h->in_batch ? 8 : 1 << 30);
     }
     k_sort_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nalive, h->sp[0].d_ntotal, h->sp[1].d_nalive,
                                  h->sp[1].d_ntotal);

@@ -284,9 +284,10 @@ struct RadixTmp {
     int *flag;
     int max_n;
 };
-// numbers the births key/id[*nb0 .. *nb) (nb0 nullable: from 0)
+// numbers the births key/id[*nb0 .. *nb) (nb0 nullable: from 0), on at
+// most max_grid blocks
 void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, const int32_t *nb0, StepCtl *ctl,
-                      int s, RadixTmp tmp, cudaStream_t st);
+                      int s, RadixTmp tmp, cudaStream_t st, int max_grid = 1 << 30);
 
 // ---- multigrid (field.cu) ----
 struct MGLevel {

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kRadixThreads)
 }
 
 void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, const int32_t *nb0, StepCtl *ctl,
-                      int s, RadixTmp tmp, cudaStream_t st) {
+                      int s, RadixTmp tmp, cudaStream_t st, int max_grid) {
     // one block per SM (the launch needs them co-resident), per device
     static int grids[64] = {0};
     int dev = 0;
@@ -355,7 +355,9 @@ void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, cons
     void *args[] = {(void *)&key, (void *)&id, (void *)&nb, (void *)&nb0, (void *)&ctl, (void *)&s, (void *)&tmp};
     // no more blocks than tiles of the largest batch of births (a small
     // reactor's numbering does not hold the whole GPU)
-    const int g = std::max(1, std::min(grid, (tmp.max_n + kRadixTile - 1) / kRadixTile));
+    // (max_grid: a reactor of a batch, whose numbering must not wait for
+    // many co-resident blocks while the other reactors' kernels hold SMs)
+    const int g = std::max(1, std::min(std::min(grid, max_grid), (tmp.max_n + kRadixTile - 1) / kRadixTile));
     cudaLaunchCooperativeKernel((void *)k_birth_ids, g, kRadixThreads, args, 0, st);
 }
 
