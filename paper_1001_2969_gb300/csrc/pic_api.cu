@@ -97,6 +97,7 @@ struct pic_handle {
     double *m_acc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     double *eedf = nullptr;
     double *tmp_grid[3] = {nullptr, nullptr, nullptr};
+    double *mom_stage = nullptr;  // the scaled time averages on their way to host buffers
     MGFast mgf;
     RadixTmp rtmp;
     int64_t step = 0;  // host copy of the device's step number (exact after each call)
@@ -1698,26 +1699,29 @@ pic_status pic_moments(pic_handle *h, pic_moments_out *out, int32_t reset) {
     const size_t gb = (size_t)h->ng * sizeof(double);
     const double f = h->nsamples > 0 ? 1.0 / (double)h->nsamples : 0.0;
     double *dst[5] = {out->ne, out->ni, out->phi, out->Ez, out->Er};
-    for (int k = 0; k < 5; ++k) {
-        if (!dst[k]) continue;
-        if (out->on_device) {
-            k_scale<<<(h->ng + 255) / 256, 256, 0, h->st>>>(h->m_acc[k], dst[k], h->ng, f);
-        } else {
-            std::vector<double> tmp((size_t)h->ng);
-            cudaMemcpyAsync(tmp.data(), h->m_acc[k], gb, cudaMemcpyDeviceToHost, h->st);
-            cudaStreamSynchronize(h->st);
-            for (int q = 0; q < h->ng; ++q) dst[k][q] = tmp[q] * f;
+    // host buffers: scaled on the device into a staging area, then one
+    // copy per output and one synchronisation for all
+    const int nb = std::max(1, h->cfg.eedf_bins);
+    if (!out->on_device && !h->mom_stage) {
+        try {
+            h->mom_stage = (double *)dalloc(h, (5 * (size_t)h->ng + (size_t)nb) * sizeof(double));
+        } catch (const std::bad_alloc &) {
+            return fail(h, PIC_ERR_CUDA, "moments: staging allocation failed");
         }
     }
+    for (int k = 0; k < 5; ++k) {
+        if (!dst[k]) continue;
+        double *to = out->on_device ? dst[k] : h->mom_stage + (size_t)k * h->ng;
+        k_scale<<<(h->ng + 255) / 256, 256, 0, h->st>>>(h->m_acc[k], to, h->ng, f);
+        if (!out->on_device) cudaMemcpyAsync(dst[k], to, gb, cudaMemcpyDeviceToHost, h->st);
+        h->launches += 1;
+    }
     if (out->eedf && h->cfg.eedf_bins > 0) {
-        if (out->on_device) {
-            k_scale<<<(h->cfg.eedf_bins + 255) / 256, 256, 0, h->st>>>(h->eedf, out->eedf, h->cfg.eedf_bins, f);
-        } else {
-            std::vector<double> tmp((size_t)h->cfg.eedf_bins);
-            cudaMemcpyAsync(tmp.data(), h->eedf, tmp.size() * 8, cudaMemcpyDeviceToHost, h->st);
-            cudaStreamSynchronize(h->st);
-            for (int q = 0; q < h->cfg.eedf_bins; ++q) out->eedf[q] = tmp[q] * f;
-        }
+        double *to = out->on_device ? out->eedf : h->mom_stage + 5 * (size_t)h->ng;
+        k_scale<<<(h->cfg.eedf_bins + 255) / 256, 256, 0, h->st>>>(h->eedf, to, h->cfg.eedf_bins, f);
+        if (!out->on_device)
+            cudaMemcpyAsync(out->eedf, to, (size_t)h->cfg.eedf_bins * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+        h->launches += 1;
     }
     DevScalars ds;
     cudaMemcpyAsync(&ds, h->ds, sizeof(ds), cudaMemcpyDeviceToHost, h->st);
