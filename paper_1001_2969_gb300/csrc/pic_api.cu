@@ -98,6 +98,11 @@ struct pic_handle {
     double *eedf = nullptr;
     double *tmp_grid[3] = {nullptr, nullptr, nullptr};
     double *mom_stage = nullptr;  // the scaled time averages on their way to host buffers
+    // pinned host copy of the step control and the status word, read once per call
+    struct HostCtl {
+        StepCtl c;
+        int32_t status;
+    } *host_ctl = nullptr;
     MGFast mgf;
     RadixTmp rtmp;
     int64_t step = 0;  // host copy of the device's step number (exact after each call)
@@ -1266,11 +1271,20 @@ void resync_ions(pic_handle *h, bool cut_births) {
 }
 
 pic_status finish_call(pic_handle *h, int64_t step0, int cur0, int cur_i0, int32_t nsteps) {
-    StepCtl c;
-    int32_t status = 0;
-    cudaMemcpyAsync(&c, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
-    cudaMemcpyAsync(&status, &h->ds->status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    // the one synchronisation of a call: both words into pinned memory
+    if (!h->host_ctl && cudaMallocHost((void **)&h->host_ctl, sizeof(*h->host_ctl)) != cudaSuccess) {
+        h->host_ctl = nullptr;
+        cudaGetLastError();
+    }
+    StepCtl local_c;
+    int32_t local_status = 0;
+    StepCtl *cp = h->host_ctl ? &h->host_ctl->c : &local_c;
+    int32_t *sp = h->host_ctl ? &h->host_ctl->status : &local_status;
+    cudaMemcpyAsync(cp, h->sctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(sp, &h->ds->status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
     cudaStreamSynchronize(h->st);
+    const StepCtl c = *cp;
+    const int32_t status = *sp;
     pic_status ce = cuda_check(h, "step");
     if (ce != PIC_OK) return ce;
     // a failed sort ends the call at the pass it sorts, before any later failure
@@ -2088,6 +2102,7 @@ void pic_destroy(pic_handle *h) {
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     destroy_streams(h);
     free_all(h);
+    if (h->host_ctl) cudaFreeHost(h->host_ctl);
     delete h;
 }
 
