@@ -407,6 +407,18 @@ pic_status pic_profile(pic_handle *h, int32_t on);
 pic_status pic_timings(pic_handle *h, double *ms, int64_t *particle_launches,
                        int64_t *all_launches, int32_t reset);
 
+/*
+ * pic_selftest_wait -- failure-detection self-test (no counterpart in the
+ * paper).  Every wait of the library's cooperative kernels (grid barriers,
+ * bulk-copy completions) gives up after a bounded number of polls and
+ * reports PIC_ERR_TIMEOUT instead of hanging.  This runs that barrier with
+ * one block waiting for a second participant that is never launched, with a
+ * limit of `polls` (256 to the library's own limit): *gave_up = 1 when the
+ * wait ran out and returned, as it must; the CUDA context stays usable.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA.
+ */
+pic_status pic_selftest_wait(int64_t polls, int32_t *gave_up);
+
 void pic_destroy(pic_handle *h);
 const char *pic_last_error(const pic_handle *h);
 const char *pic_status_string(pic_status s);

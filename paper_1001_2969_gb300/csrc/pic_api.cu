@@ -2094,6 +2094,17 @@ pic_status pic_timings(pic_handle *h, double *ms, int64_t *particle_launches, in
     return PIC_OK;
 }
 
+pic_status pic_selftest_wait(int64_t polls, int32_t *gave_up) {
+    if (!gave_up || polls < 256 || polls > kSpinLimit) return PIC_ERR_ARG;
+    int g = 0;
+    if (wait_selftest((long long)polls, &g) != 0) {
+        cudaGetLastError();
+        return PIC_ERR_CUDA;
+    }
+    *gave_up = g;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+}
+
 void pic_destroy(pic_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->st);

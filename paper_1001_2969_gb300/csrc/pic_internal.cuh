@@ -81,9 +81,10 @@ __device__ __forceinline__ void sort_failed(StepCtl *ctl, int status) {
 // acquire loads until the counter (which only grows) reaches `target`: the
 // participants times the barriers of this kind the block has passed.  The
 // block's writes before the barrier are visible to every participant after
-// it.  The poll is bounded: after kSpinLimit tries, or once another block
+// it.  The poll is bounded: after `limit` tries (kSpinLimit: a few seconds
+// at most, against microseconds for a wait that ends), or once another block
 // gave up, the block raises *timeout and the call returns false.
-constexpr long long kSpinLimit = 1LL << 26;
+constexpr long long kSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
@@ -95,7 +96,8 @@ __device__ __forceinline__ void atom_add_release(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool count_barrier(unsigned *count, unsigned target, int *timeout) {
+__device__ __forceinline__ bool count_barrier(unsigned *count, unsigned target, int *timeout,
+                                              long long limit = kSpinLimit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -103,7 +105,7 @@ __device__ __forceinline__ bool count_barrier(unsigned *count, unsigned target, 
         atom_add_release(count, 1u);
         long long it = 0;
         while ((int)(ld_acquire(count) - target) < 0) {
-            if ((++it & 255) == 0 && (it > kSpinLimit || *(volatile int *)timeout)) {
+            if ((++it & 255) == 0 && (it > limit || *(volatile int *)timeout)) {
                 atomicExch(timeout, 1);
                 ok = 0;
                 break;
@@ -284,6 +286,9 @@ struct RadixTmp {
     int *flag;
     int max_n;
 };
+// the bounded-wait self-test (sortk.cu): 0 when it ran, *gave_up = 1 when
+// the wait ran out as it must
+int wait_selftest(long long limit, int *gave_up);
 // numbers the births key/id[*nb0 .. *nb) (nb0 nullable: from 0), on at
 // most max_grid blocks
 void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, const int32_t *nb0, StepCtl *ctl,

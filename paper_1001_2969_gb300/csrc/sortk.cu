@@ -338,6 +338,26 @@ __global__ void __launch_bounds__(kRadixThreads)
     if (blockIdx.x == 0 && tid == 0) ctl->next_id[s] = base + (uint64_t)nb;
 }
 
+// failure-detection self-test: one block waits at the bounded grid barrier
+// for a second participant that is never launched; the wait must give up
+__global__ void k_wait_selftest(unsigned *count, int *timeout, long long limit, int *gave_up) {
+    const bool ok = count_barrier(count, 2u, timeout, limit);
+    if (threadIdx.x == 0) *gave_up = ok ? 0 : 1;
+}
+
+int wait_selftest(long long limit, int *gave_up) {
+    int *buf = nullptr;  // count, timeout, result
+    if (cudaMalloc(&buf, 3 * sizeof(int)) != cudaSuccess) return -1;
+    cudaMemset(buf, 0, 3 * sizeof(int));
+    k_wait_selftest<<<1, 32>>>(reinterpret_cast<unsigned *>(buf), buf + 1, limit, buf + 2);
+    int out[3] = {0, 0, 0};
+    const cudaError_t e = cudaMemcpy(out, buf, sizeof(out), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return -1;
+    *gave_up = out[2] && out[1];
+    return 0;
+}
+
 void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, const int32_t *nb0, StepCtl *ctl,
                       int s, RadixTmp tmp, cudaStream_t st, int max_grid) {
     // one block per SM (the launch needs them co-resident), per device

@@ -89,7 +89,7 @@ SYMBOLS = ("pic_init", "pic_step", "pic_field_solve", "pic_moments", "pic_get_pa
            "pic_get_counts", "pic_save", "pic_load", "pic_profile", "pic_timings", "pic_destroy",
            "pic_last_error", "pic_status_string", "pic_field_solve_noalloc", "pic_batch_init",
            "pic_batch_step", "pic_batch_destroy", "pic_tune", "pic_get_circuit", "pic_window",
-           "pic_merge")
+           "pic_merge", "pic_selftest_wait")
 
 
 class PicError(RuntimeError):
@@ -118,6 +118,7 @@ def lib():
         L.pic_tune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
         L.pic_get_circuit.argtypes = [vp, _dp]
         L.pic_merge.argtypes = [vp, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
+        L.pic_selftest_wait.argtypes = [C.c_int64, C.POINTER(C.c_int32)]
         L.pic_window.argtypes = [vp, C.c_int32, C.c_int32, _dp, C.c_double, _dp, C.c_int32, _dp, _dp, _dp]
         L.pic_field_solve.argtypes = [vp, vp, vp, C.c_double, vp, C.c_int32,
                                       C.POINTER(pic_solve_info)]
@@ -344,6 +345,15 @@ def pic_merge(h: Handle, s: int, frac: float, dv: float):
     e = C.c_double(0)
     _check(h, lib().pic_merge(h.ptr, int(s), float(frac), float(dv), C.byref(n), C.byref(e)))
     return int(n.value), float(e.value)
+
+
+def pic_selftest_wait(polls: int = 1 << 16) -> bool:
+    """Run the bounded-wait self-test; True when the wait gave up as it must."""
+    g = C.c_int32(0)
+    st = lib().pic_selftest_wait(int(polls), C.byref(g))
+    if st != PIC_OK:
+        raise PicError(st, "pic_selftest_wait failed")
+    return bool(g.value)
 
 
 def pic_tune(h: Handle, steps_per_variant: int = 2, variants=None):
