@@ -8,7 +8,9 @@ results, and the tuner must pick valid shapes.
 import numpy as np
 import pytest
 
+import parity as P
 import workloads as W
+from oracle import Oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +73,49 @@ def test_batch_matches_reactors_stepped_alone(pic, prec):
         ma, mb = pic.pic_moments(ha), pic.pic_moments(hb)
         if prec == "fp64":
             assert list(ma["counters"][:22]) == list(mb["counters"][:22])
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_reactors_match_the_oracle(pic, prec):
+    """Three reactors of an uneven draw (meshes, particle counts, pressures and
+    voltages differ), stepped together, each against the oracle stepped
+    alone: the first step element by element, two more steps (both buffer
+    parities) in the fields, ids and counters."""
+    cfgs = W.batch_configs(n=3, seed=11, n_lo=4_000, n_hi=30_000, precision=prec)
+    meshes = {(c["nz"], c["nr"]) for c in cfgs}
+    assert len(meshes) > 1
+    hs = [pic.pic_init(c) for c in cfgs]
+    b = pic.pic_batch_init(hs)
+    oracles = []
+    for c in cfgs:
+        o = Oracle(c)
+        o.load()
+        oracles.append((o, [o.get_particles(s) for s in (0, 1)]))
+    assert b.step(1) == [0] * len(cfgs)
+    ftol = 1e-12 if prec == "fp64" else 1e-6
+    for c, h, (o, loaded) in zip(cfgs, hs, oracles):
+        o.step(1)
+        grids = {k: o.grid(k) for k in ("phi", "Ez", "Er")}
+        f = pic.pic_get_fields(h)
+        for k in ("phi", "Ez", "Er"):
+            assert nerr(f[k], grids[k]) < ftol, (c["name"], k)
+        for s in (0, 1):
+            P.compare_species(c, s, pic.pic_get_particles(h, s), o.get_particles(s), prec,
+                              inputs=loaded[s], grids=grids, step=0)
+        if prec == "fp64":
+            oc, _ = o.counters()
+            assert list(pic.pic_moments(h)["counters"][:22]) == list(oc[:22]), c["name"]
+    assert b.step(2) == [0] * len(cfgs)
+    for c, h, (o, _) in zip(cfgs, hs, oracles):
+        o.step(2)
+        f = pic.pic_get_fields(h)
+        assert nerr(f["phi"], o.grid("phi")) < (1e-11 if prec == "fp64" else 1e-5), c["name"]
+        if prec == "fp64":
+            for s in (0, 1):
+                assert np.array_equal(by_id(pic.pic_get_particles(h, s))["id"], by_id(o.get_particles(s))["id"])
+            oc, _ = o.counters()
+            assert list(pic.pic_moments(h)["counters"][:22]) == list(oc[:22]), c["name"]
     b.close()
 
 

@@ -2,24 +2,39 @@
 
 After a few hundred steps two runs from the same start differ (deposit
 atomics add in any order, FP32 rounding in the mixed path, and the motion
-is chaotic), so time averages are compared: density and potential
-(volume-weighted over 2 x 4 regions of the mesh), the mean electron energy and
-the EEDF in energy bands.  Each statistic of the GPU run (seed 1) must lie
-within 1 % of the oracle's seed-1 value, or within 3 sigma, where sigma is
-the seed-to-seed spread of that statistic over K independent oracle runs
-(the difference of two runs carries sqrt(2) sigma).  Workload: the small
-reactor (33 x 65 nodes, 1e5 electrons + 1e5 ions), 200 steps, averages over
-the last 100.
+is chaotic), so time averages are compared as profiles:
+
+  - the axis column (r = 0 nodes) along z, 8 bins;
+  - the first interior row at each electrode (the sheaths) along r, 8 bins;
+  - 2 x 4 volume-weighted regions of the whole mesh;
+each for the electron density, the ion density and the potential; and the
+mean electron energy and the EEDF in five energy bands.
+
+Reference: the mean of K = 16 independent oracle runs (seeds 1..16); sigma
+per bin: their seed-to-seed spread.  A profile passes when the part of each
+bin's difference beyond 1 % of the profile's scale (the bulk ion density
+for densities, max |phi| for the potential, the value itself for the
+energy statistics) is consistent with noise: sum (excess / sigma')^2, with
+sigma' = sigma sqrt(1 + 1/K), stays below n F_{n, K-1} at the 3-sigma level
+(p = 0.0027) shared over the profiles.  Checked on 10 further oracle seeds:
+none fails; a 5 % error confined to the ion density of the axis column or
+of a sheath row fails, as does a 2 % error in the axis potential.
+
+Workload: the small reactor (33 x 65 nodes) with 1e6 electrons + 1e6 ions,
+200 steps, averages over the last 100.
 """
+import multiprocessing as mp
+import os
+
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle import Oracle
 
 pytestmark = pytest.mark.gpu
 
-STEPS, AVG, K = 200, 100, 6
+STEPS, AVG, K, NPART = 200, 100, 16, 1_000_000
+NBIN = 8
 
 
 @pytest.fixture(scope="module")
@@ -34,71 +49,87 @@ def pic():
     return P
 
 
-def _regions(a, w, nz, nr, bz=2, br=4):
-    """Weighted sums of a over blocks of nodes (bz rows x br columns), and the weights."""
-    iz = np.minimum(np.arange(nz) * bz // nz, bz - 1)
-    jr = np.minimum(np.arange(nr) * br // nr, br - 1)
-    s = np.zeros((bz, br))
-    ws = np.zeros((bz, br))
-    np.add.at(s, (iz[:, None], jr[None, :]), a * w)
-    np.add.at(ws, (iz[:, None], jr[None, :]), w)
-    return s, ws
+def _bins(n, b):
+    return np.minimum(np.arange(n) * b // n, b - 1)
+
+
+def _profile(a, w, idx, nb):
+    return np.bincount(idx, a * w, nb) / np.bincount(idx, w, nb)
 
 
 def stats(cfg, m, V):
-    """The compared statistics of one run, with the scale its 1 % refers to."""
+    """The compared profiles of one run's time averages."""
     nz, nr = cfg["nz"], cfg["nr"]
+    iz, jr = _bins(nz, NBIN), _bins(nr, NBIN)
+    reg = (_bins(nz, 2)[:, None] * 4 + _bins(nr, 4)[None, :]).ravel()
     out = {}
-    for key in ("ne", "ni"):
-        s, _ = _regions(m[key], V, nz, nr)  # charge carriers per region
-        big = s / s.sum() > 0.01
-        out[key] = (s[big], np.abs(s[big]))
-    s, ws = _regions(m["phi"], V, nz, nr)
-    phi = s / ws
-    out["phi"] = (phi.ravel(), np.full(phi.size, np.abs(m["phi"]).max()))
+    for key in ("ne", "ni", "phi"):
+        out[f"axis_{key}"] = _profile(m[key][:, 0], V[:, 0], iz, NBIN)
+        out[f"row1_{key}"] = _profile(m[key][1, :], V[1, :], jr, NBIN)
+        out[f"rowL_{key}"] = _profile(m[key][nz - 2, :], V[nz - 2, :], jr, NBIN)
+        out[f"regions_{key}"] = np.bincount(reg, (m[key] * V).ravel(), 8) / np.bincount(reg, V.ravel(), 8)
     e = (np.arange(cfg["eedf_bins"]) + 0.5) * cfg["eedf_emax"] / cfg["eedf_bins"]
     f = m["eedf"] / m["eedf"].sum()
-    mean = (e * f).sum()
-    out["mean_energy"] = (np.array([mean]), np.array([mean]))
+    out["mean_energy"] = np.array([(e * f).sum()])
     bands = [0, 2, 5, 10, 20, 100]
-    fr = np.array([f[(e >= a) & (e < b)].sum() for a, b in zip(bands[:-1], bands[1:])])
-    out["eedf_bands"] = (fr, fr)
+    out["eedf_bands"] = np.array([f[(e >= a) & (e < b)].sum() for a, b in zip(bands[:-1], bands[1:])])
     return out
 
 
-def _oracle(seed):
-    cfg = W.config("c1", seed=seed)
+def _oracle_run(seed):
+    from oracle import Oracle
+
+    cfg = W.scaled(W.config("c1", seed=seed), NPART)
     o = Oracle(cfg)
     o.load()
     o.step(STEPS - AVG)
     o.reset_moments()
     o.step(AVG)
     m = o.moments()
-    return cfg, m, o.node_volumes()
+    return {k: m[k] for k in ("ne", "ni", "phi", "eedf", "nsamples")}, o.node_volumes()
 
 
 @pytest.fixture(scope="module")
 def oracle_runs():
-    runs = [_oracle(1 + k) for k in range(K)]
-    cfg, m1, V = runs[0]
-    st = [stats(cfg, m, V) for _, m, _ in runs]
-    sigma = {key: np.std(np.array([s[key][0] for s in st]), axis=0, ddof=1) for key in st[0]}
-    return cfg, m1, V, st[0], sigma
+    # a spawned pool: the parent already holds a CUDA context
+    with mp.get_context("spawn").Pool(min(K, os.cpu_count() or 1)) as pool:
+        runs = pool.map(_oracle_run, range(1, K + 1))
+    cfg = W.scaled(W.config("c1"), NPART)
+    V = runs[0][1]
+    st = [stats(cfg, m, V) for m, _ in runs]
+    mean = {k: np.mean([s[k] for s in st], axis=0) for k in st[0]}
+    sigma = {k: np.std([s[k] for s in st], axis=0, ddof=1) for k in st[0]}
+    scale = {"ne": np.abs(runs[0][0]["ni"]).max(), "ni": np.abs(runs[0][0]["ni"]).max(),
+             "phi": np.abs(runs[0][0]["phi"]).max()}
+    return cfg, V, mean, sigma, scale, runs[0][0]["nsamples"]
+
+
+def profile_failures(g, mean, sigma, scale):
+    from scipy import stats as S
+
+    p = 0.0027 / len(mean)
+    fails = []
+    for k, ref in mean.items():
+        d = g[k] - ref
+        sc = scale.get(k.split("_")[-1], np.abs(ref))
+        excess = np.maximum(np.abs(d) - 0.01 * sc, 0.0)
+        s2 = sigma[k] ** 2 * (1.0 + 1.0 / K)
+        chi = float(np.sum(np.where(excess > 0, excess ** 2 / np.maximum(s2, 1e-300), 0.0)))
+        lim = d.size * S.f.ppf(1.0 - p, d.size, K - 1)
+        if chi > lim:
+            fails.append((k, chi, lim, g[k], ref))
+    return fails
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_time_averages_match_the_oracle(pic, oracle_runs, prec):
-    cfg, om, V, ost, sigma = oracle_runs
-    h = pic.pic_init(W.config("c1", precision=prec))
+    cfg, V, mean, sigma, scale, nsamples = oracle_runs
+    h = pic.pic_init(W.scaled(W.config("c1", precision=prec), NPART))
     assert pic.pic_step(h, STEPS - AVG) == 0
     pic.pic_moments(h, reset=True)
     assert pic.pic_step(h, AVG) == 0
     gm = pic.pic_moments(h)
-    assert gm["nsamples"] == om["nsamples"] == AVG
-    gst = stats(cfg, gm, V)
-    for key, (o, scale) in ost.items():
-        g = gst[key][0]
-        assert g.shape == o.shape, key
-        lim = np.maximum(0.01 * scale, 3.0 * np.sqrt(2.0) * sigma[key])
-        worst = np.max(np.abs(g - o) / lim)
-        assert worst <= 1.0, (key, worst, g, o)
+    assert gm["nsamples"] == nsamples == AVG
+    fails = profile_failures(stats(cfg, gm, V), mean, sigma, scale)
+    assert not fails, fails
+    pic.pic_destroy(h)

@@ -1,14 +1,20 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances: FP64 path 1e-12 relative per step (normalised by each output's
-largest magnitude), integer work bit-exact (cells, ids, collision and split
-counts, absorbed counts); mixed FP32/FP64 path 2e-5 relative, integer
-decisions equal except where FP32 rounding moves a value across a threshold
-(a handful, counted and bounded).
+Tolerances: FP64 path 1e-12 relative per step, mixed FP32/FP64 path 2e-5,
+for every particle and quantity element by element (tests/parity.py states
+the floors), and for rho and chi node by node (relative to the node's charge
+magnitude sum_s |q_s| N_s / V, resp. chi itself).  The potential and E are
+compared in the max norm, the norm the field solve's stopping rule and
+error bound are stated in.  Integer work is bit-exact in FP64 (cells, ids,
+the cell-sort permutation's order and coverage, collision and split counts,
+absorbed counts); in the mixed path an integer decision may differ only
+where FP32 rounding of the inputs crosses the threshold, which each such
+particle must show (parity.explain).
 """
 import numpy as np
 import pytest
 
+import parity as P
 import workloads as W
 from oracle import C_ABS, C_BIRTHS, C_CAND, C_COLL, C_SPLITS, Oracle
 
@@ -52,24 +58,12 @@ def cells_of(cfg, p):
     return j * (cfg["nz"] - 1) + i
 
 
-def compare_particles(cfg, g, o, prec, max_outliers=0):
-    g, o = by_id(g), by_id(o)
-    if prec == "fp64":
-        assert np.array_equal(g["id"], o["id"])
-        for k in FIELDS:
-            e = nerr(g[k], o[k])
-            assert e <= TOL[prec], (k, e)
-        assert np.array_equal(g["cell"], cells_of(cfg, o))
-        return 0
-    common, gi, oi = np.intersect1d(g["id"], o["id"], return_indices=True)
-    nd = len(g["id"]) + len(o["id"]) - 2 * len(common)
-    bad = np.zeros(len(common), bool)
-    for k in FIELDS:
-        s = np.abs(o[k][oi]).max() if len(oi) else 1.0
-        bad |= np.abs(g[k][gi] - o[k][oi]) > TOL[prec] * max(s, 1e-300)
-    nbad = int(bad.sum()) + nd
-    assert nbad <= max_outliers, (nbad, nd)
-    return nbad
+def grid_node_errors(g, o, floor):
+    """max over nodes of |g - o| / max(|o|, floor) (0 where both vanish)."""
+    den = np.maximum(np.abs(o), floor)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        e = np.where(den > 0, np.abs(g - o) / np.where(den > 0, den, 1.0), np.abs(g - o))
+    return float(e.max(initial=0.0))
 
 
 def make_pair(pic, cfg, load=True, capacity=None):
@@ -96,10 +90,14 @@ def test_load_parity(pic, prec):
         c = np.where(p < rem * (base + 1), p // (base + 1), rem + (p - rem * (base + 1)) // max(base, 1))
         gs = by_id(g)
         assert np.array_equal(gs["cell"], c)
-        compare_particles(cfg, g, ref, prec if prec == "fp64" else "mixed")
-        if prec == "mixed":
-            for k in FIELDS:
-                assert nerr(gs[k], by_id(ref)[k]) < 2e-7, k
+        P.check_sorted(g, (cfg["nz"] - 1) * (cfg["nr"] - 1))
+        rs = by_id(ref)
+        assert np.array_equal(gs["id"], rs["id"])
+        # the loaded state: FP64 to 1e-12 (a position stored as cell + offset
+        # is rounded to eps |x|, eps (nr - 1) of a cell width); mixed, one FP32
+        # rounding of the cell offset, the velocities and the weight
+        e = P.errors(cfg, s, gs, rs, 0.0, P.w_ref_table(cfg, s))
+        assert e.max() <= (1e-12 if prec == "fp64" else 2e-7), float(e.max())
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -196,7 +194,7 @@ def _counters_match(gc, oc, prec):
             assert abs(int(gc[k]) - int(oc[k])) <= max(3, 1e-4 * oc[k]), (k, gc[k], oc[k])
 
 
-def _one_step(pic, cfg, e, i, step_index, prec, max_outliers=0):
+def _one_step(pic, cfg, e, i, step_index, prec):
     h = pic.pic_init(cfg, load=False)
     o = Oracle(cfg)
     pic.pic_set_particles(h, 0, e)
@@ -209,17 +207,27 @@ def _one_step(pic, cfg, e, i, step_index, prec, max_outliers=0):
     o.step(1)
     assert st == 0
     f = pic.pic_get_fields(h)
+    grids = {k: o.grid(k) for k in ("phi", "Ez", "Er")}
     o.finalize()
     tol = TOL[prec]
     for name in ("phi", "Ez", "Er"):
-        assert nerr(f[name], o.grid(name)) < (tol if prec == "fp64" else 1e-6), name
-    for name in ("rho", "chi"):
-        assert nerr(f[name], o.grid(name)) < (tol if prec == "fp64" else 5e-5), name
-    nb = 0
-    for s in (0, 1):
+        assert nerr(f[name], grids[name]) < (tol if prec == "fp64" else 1e-6), name
+    # rho and chi node by node, relative to the node's charge magnitude
+    # (electron and ion charge cancel where the plasma is neutral) plus what
+    # one particle of the split's reference weight adds there (a node that a
+    # single particle barely reaches holds a tiny, rounding-sized value)
+    V = o.node_volumes()
+    q, m = abs(cfg["species"][0]["q"]), cfg["species"][0]["m"]
+    w1 = P.w_ref_table(cfg, 0)[np.minimum(np.arange(cfg["nr"]), cfg["nr"] - 2)][None, :] / V
+    qabs = q * ((o.grid("Ne") + o.grid("Ni")) / V + w1)
+    chi1 = q * q / m * w1 * cfg["dt"] ** 2 / (2.0 * 8.8541878128e-12)
+    assert grid_node_errors(f["rho"], o.grid("rho"), qabs) <= tol
+    assert grid_node_errors(f["chi"], o.grid("chi"), chi1) <= tol
+    explained = 0
+    for s, inp in ((0, e), (1, i)):
         g = pic.pic_get_particles(h, s)
         ref = o.get_particles(s)
-        nb += compare_particles(cfg, g, ref, prec, max_outliers)
+        explained += P.compare_species(cfg, s, g, ref, prec, inputs=inp, grids=grids, step=step_index)
     m = pic.pic_moments(h)
     oc, oq = o.counters()
     _counters_match(m["counters"], oc, prec)
@@ -234,7 +242,7 @@ def _one_step(pic, cfg, e, i, step_index, prec, max_outliers=0):
 def test_one_step_parity_with_collisions_and_births(pic, prec):
     cfg = _state_cfg(prec)
     e, i = _random_state(cfg, 60_001, 40_003, seed=5)
-    h, o, oc = _one_step(pic, cfg, e, i, 17, prec, max_outliers=40)
+    h, o, oc = _one_step(pic, cfg, e, i, 17, prec)
     assert oc[C_COLL + 2] > 50  # ionisations happened
     assert oc[C_COLL + 4] > 0  # charge exchange happened
     assert oc[C_ABS:C_ABS + 6].sum() > 0  # walls absorbed
@@ -251,7 +259,7 @@ def test_one_step_parity_with_splitting(pic, prec):
         j = np.minimum(np.floor(p["r"] / dr).astype(int), cfg["nr"] - 2)
         wr = np.array([o.w_ref(s, int(k)) for k in j])
         p["w"] = wr * rng.uniform(0.3, 12.0, len(j))
-    h, o2, oc = _one_step(pic, cfg, e, i, 0, prec, max_outliers=60)
+    h, o2, oc = _one_step(pic, cfg, e, i, 0, prec)
     assert oc[C_SPLITS] > 1000 and oc[C_SPLITS + 1] > 1000
 
 
@@ -261,7 +269,7 @@ def test_tiny_and_empty_inputs(pic, prec):
     rng = np.random.default_rng(0)
     e = W.random_particles(cfg, 0, 7, seed=1, hot=4.0)
     i = W.random_particles(cfg, 1, 0, seed=2)
-    _one_step(pic, cfg, e, i, 3, prec, max_outliers=2)
+    _one_step(pic, cfg, e, i, 3, prec)
     # both species empty: the field is the vacuum (Laplace) solution
     cfg2 = W.config("tiny", precision=prec)
     h = pic.pic_init(W.scaled(cfg2, 0), load=False)
