@@ -152,7 +152,7 @@ def run_gpu(args, rank, world):
         if args.particles:
             cfg = W.scaled(cfg, args.particles)
         h = pic.pic_init(cfg, stream=stream.cuda_stream)
-        pic.pic_step(h, args.warmup)
+        statuses = [pic.pic_step(h, args.warmup)]
         n0 = pic.pic_get_counts(h)["n_alive"].sum()
         if world > 1:
             torch.distributed.barrier()
@@ -166,6 +166,7 @@ def run_gpu(args, rank, world):
         ev0.record(stream)
         st = pic.pic_step(h, steps)  # each step one CUDA graph replay
         ev1.record(stream)
+        statuses.append(st)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -181,12 +182,12 @@ def run_gpu(args, rank, world):
         # phase breakdown and the particle kernel's own time: the same number of
         # steps again, launched one by one with CUDA events around each phase
         pic.pic_profile(h, True)
-        pic.pic_step(h, steps)
+        statuses.append(pic.pic_step(h, steps))
         pic.pic_profile(h, False)
         tm = pic.pic_timings(h, reset=True)
         prof_psteps = float(pic.pic_moments(h, reset=True)["counters"][pic.PIC_C_PSTEPS])
         res = dict(ms=ms, psteps=psteps, prof_psteps=prof_psteps, n0=int(n0), n1=int(n1), timings=tm,
-                   clocks=ck, status=st, mg_cycles=cycles / steps, launches=launches)
+                   clocks=ck, status=st, statuses=statuses, mg_cycles=cycles / steps, launches=launches)
         if prec == args.precision:
             # end to end through the public API with host buffers: per step the z = L
             # boundary row goes host -> device from pinned memory and the time-averaged
@@ -203,7 +204,7 @@ def run_gpu(args, rank, world):
             t0 = time.perf_counter()
             for _ in range(e_steps):
                 pic.lib().pic_set_boundary(h.ptr, phiL.data_ptr(), 0)
-                pic.pic_step(h, 1)
+                statuses.append(pic.pic_step(h, 1))
                 pic.pic_moments_into(h, mo)
             torch.cuda.synchronize()
             e2e_s = time.perf_counter() - t0
@@ -530,6 +531,9 @@ def main():
         "mg_cycles_per_step": main_r["mg_cycles"],
         "gpu_launches": main_r["launches"],
         "clocks": main_r["clocks"],
+        # pic_step's status over the warm-up, the timed steps, the phase pass and
+        # the end-to-end steps: anything but PIC_OK voids the line
+        "status": _status_name(pic_lib(), first_bad(main_r["statuses"])),
     }
     if "fp64" in res and args.precision != "fp64":
         r = res["fp64"]
@@ -551,7 +555,27 @@ def main():
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+    bad = [first_bad(r["statuses"]) for r in res.values()]
+    if any(b != 0 for b in bad):
+        print(f"bench: a timed call returned {line['status']} (fp64 leg: "
+              f"{_status_name(pic_lib(), bad[-1])}); the figures above are void", file=sys.stderr)
+        return 1
     return 0
+
+
+def first_bad(statuses):
+    """The first status other than PIC_OK (0), else 0."""
+    return next((int(s) for s in statuses if int(s) != 0), 0)
+
+
+def pic_lib():
+    from paper_1001_2969_gb300 import pic
+
+    return pic.lib()
+
+
+def _status_name(L, st):
+    return L.pic_status_string(int(st)).decode()
 
 
 if __name__ == "__main__":

@@ -265,23 +265,26 @@ pic_status pic_field_solve(pic_handle *h, const double *rho, const double *chi, 
  * pic_field_solve_noalloc -- the same FP64 multigrid solve as pic_field_solve,
  * without a handle and without allocating any device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot allocate
- * when they need a solve -- code running while a CUDA graph is captured,
- * hosts that give the library a fixed memory budget, real-time loops that
- * must not stall on an allocation.
+ * when they need a solve -- hosts that give the library a fixed memory budget
+ * at start-up and allow no growth afterwards, real-time loops that must not
+ * stall on an allocation.
  *
  * rho, chi (in) and phi (out) are caller-owned DEVICE arrays [nz][nr]; phi_zL
  * is a device array of nr potentials on z = L or NULL (grounded); z = 0 is
  * at V, r = R grounded.  Cold start, at most max_cycles V-cycles, tolerance
  * tol as mg_tol in pic_config.  Work is issued on `stream` (a cudaStream_t,
- * NULL for the legacy stream) and is finished when the call returns.  info
- * (host) may be NULL.
+ * NULL for the legacy stream); the residual is read back to the host after
+ * every V-cycle, so the call synchronises `stream` and the solve is finished
+ * when it returns.  info (host) may be NULL.
  *
  * Workspace: one fixed device array of 800,000 doubles (6.4 MB) compiled
  * into the library, held on every GPU that loads it until the process
  * exits; it fits meshes up to 129 x 513 nodes.  A larger mesh is rejected
  * with PIC_ERR_ARG and a message on stderr; bad arguments likewise.  The
- * first call on a device looks up the workspace's device address (with that
- * device current); make that first call outside any stream capture.  All
+ * first call on a device looks up the workspace's device address with that
+ * device current and keeps it for the process; make that first call before
+ * any stream capture begins.  The kept address does not survive a device
+ * reset (cudaDeviceReset): do not call this entry point after one.  All
  * calls share the one workspace, which keeps the last call's contents: calls
  * that overlap on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA,

@@ -279,12 +279,15 @@ static void line_rows(const Tc *cz, const Tc *cr, const Tu *f, Tu *u, int nz, in
     const size_t smem = 8 * (size_t)n * sizeof(Ts);
     int threads = 32;
     while (threads < n && threads < 1024) threads <<= 1;
-    static bool attr_set[2] = {false, false};
-    const int slot = sizeof(Ts) == 8 ? 1 : 0;
-    if (smem > 48 * 1024 && !attr_set[slot]) {
+    // the opt-in is a per-device attribute of the kernel: set it once for
+    // every device this process launches on
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || !attr_set[dev])) {
         cudaFuncSetAttribute(k_line<Tc, Tu, Ts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
-        attr_set[slot] = true;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     k_line<Tc, Tu, Ts><<<nrows, threads, smem, st>>>(cz, cr, f, u, nr, row0, 2);
     ++*launches;

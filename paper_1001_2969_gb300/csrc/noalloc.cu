@@ -1,15 +1,14 @@
 // noalloc.cu -- a field solve that allocates no device memory.
 //
 // Who needs it: callers that must not allocate at the moment they solve.
-// Examples are code running while a CUDA graph is being captured (an
-// allocation there either breaks the capture or bakes a pointer into the
-// graph), hosts that hand the library a fixed memory budget and forbid
+// Examples are hosts that hand the library a fixed memory budget and forbid
 // growth after start-up, and real-time loops where an allocation could stall
 // on a device-wide synchronisation.  pic_field_solve allocates its multigrid
 // workspace through a handle; pic_field_solve_noalloc runs the same FP64
 // multigrid solve on the caller's device arrays and takes its workspace from
 // one fixed array that lives in this file for as long as the library is
-// loaded on a device.
+// loaded on a device.  The solve reads its residual back to the host after
+// every V-cycle (the stopping rule), so the call synchronises `stream`.
 #include <stdio.h>
 
 #include <mutex>
@@ -38,7 +37,10 @@ std::mutex g_mu;
 DeviceSlots g_slots[kMaxDevices];
 
 // The symbols above are host-side stand-ins in host code; the device
-// addresses are looked up once per device, with that device current.
+// addresses are looked up once per device, with that device current, and
+// kept for the life of the process.  The cache does not survive a device
+// reset (cudaDeviceReset or any other teardown of the device's primary
+// context): after one, the addresses it holds are stale.
 pic_status device_addresses(double **scratch, pic::DevScalars **scalars) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PIC_ERR_CUDA;

@@ -1,9 +1,11 @@
 """The allocation-free field solve against the handle's field solve.
 
 pic_field_solve_noalloc serves callers that cannot allocate device memory
-when they solve (stream capture, fixed memory budgets, real-time loops): it
-must give the same potential as pic_field_solve, call after call, while
-using only its fixed workspace.  This file is collected last on purpose.
+when they solve (a host that fixed the library's memory budget at start-up,
+a real-time loop that must not stall on an allocation): it must give the
+same potential as pic_field_solve, call after call, while using only its
+fixed workspace -- the device's free memory does not change across a call.
+This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -29,30 +31,45 @@ def _nerr(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def test_noalloc_solve_matches_handle_solve_on_two_calls_in_a_row(env):
+@pytest.mark.parametrize("mesh", [(65, 257), (129, 513), (33, 1025)])
+def test_noalloc_solve_matches_handle_solve_on_two_calls_in_a_row(env, mesh):
+    """(129, 513) is the largest mesh the workspace holds; (33, 1025) is a wide,
+    short one whose line solves take more than 48 KB of shared memory."""
     torch, pic = env
-    nz, nr = 65, 257
-    cfg = W.scaled(W.config("c1", nz=nz, nr=nr, mg_tol=1e-12, mg_max_cycles=60), 0)
+    nz, nr = mesh
+    cfg = W.scaled(W.config("c1", nz=nz, nr=nr, R=0.05 * (nr - 1) / 64, mg_tol=1e-12, mg_max_cycles=60), 0)
     h = pic.pic_init(cfg, load=False)
     stream = torch.cuda.current_stream().cuda_stream
-    for call, (seed, V, with_zL) in enumerate(((11, 60.0, False), (12, -35.0, True))):
+    calls = []
+    for seed, V, with_zL in ((11, 60.0, False), (12, -35.0, True)):
         chi = W.random_grid(cfg, seed=seed, scale=2.0)
         rho = 1e-5 * (W.random_grid(cfg, seed=seed + 100, smooth=False) - 0.5)
         zL = np.linspace(5.0, 0.0, nr) if with_zL else None
         pic.pic_set_boundary(h, zL)
         ref, cyc_ref, _, st_ref = pic.pic_field_solve(h, rho, chi, V)
         assert st_ref == pic.PIC_OK
-        d_rho = torch.tensor(rho, dtype=torch.float64, device="cuda")
-        d_chi = torch.tensor(chi, dtype=torch.float64, device="cuda")
-        d_phi = torch.full((nz, nr), float("nan"), dtype=torch.float64, device="cuda")
-        d_zL = torch.tensor(zL, dtype=torch.float64, device="cuda") if with_zL else None
+        dev = dict(rho=torch.tensor(rho, dtype=torch.float64, device="cuda"),
+                   chi=torch.tensor(chi, dtype=torch.float64, device="cuda"),
+                   phi=torch.full((nz, nr), float("nan"), dtype=torch.float64, device="cuda"),
+                   zL=torch.tensor(zL, dtype=torch.float64, device="cuda") if with_zL else None)
+        calls.append((V, dev, ref, cyc_ref))
+    pic.pic_destroy(h)
+    torch.cuda.synchronize()
+    free = []
+    for V, dev, ref, cyc_ref in calls:
+        free.append(torch.cuda.mem_get_info()[0])
         st, cyc, res = pic.pic_field_solve_noalloc(
-            cfg["R"], cfg["L"], nz, nr, 0, d_rho.data_ptr(), d_chi.data_ptr(), V,
-            d_zL.data_ptr() if with_zL else None, d_phi.data_ptr(), 1e-12, 60, stream)
+            cfg["R"], cfg["L"], nz, nr, 0, dev["rho"].data_ptr(), dev["chi"].data_ptr(), V,
+            dev["zL"].data_ptr() if dev["zL"] is not None else None, dev["phi"].data_ptr(), 1e-12, 60,
+            stream)
         torch.cuda.synchronize()
-        assert st == pic.PIC_OK, (call, st)
+        assert st == pic.PIC_OK, st
         assert cyc == cyc_ref and res <= 1e-12
-        assert _nerr(d_phi.cpu().numpy(), ref) < 1e-12, call
+        assert _nerr(dev["phi"].cpu().numpy(), ref) < 1e-12
+    free.append(torch.cuda.mem_get_info()[0])
+    # the second call (the first may load the module's kernels) leaves the
+    # device's free memory as it found it
+    assert free[2] == free[1], free
 
 
 def test_noalloc_solve_rejects_a_mesh_beyond_its_workspace(env):
