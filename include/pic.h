@@ -422,6 +422,18 @@ pic_status pic_timings(pic_handle *h, double *ms, int64_t *particle_launches,
  */
 pic_status pic_selftest_wait(int64_t polls, int32_t *gave_up);
 
+/*
+ * pic_fp64_fma_rate -- measured FP64 rate of the current device (no
+ * counterpart in the paper): a plain kernel of independent fused
+ * multiply-add chains (8 per thread, `iters` FMAs each, 8 blocks of 256
+ * threads per SM), timed with CUDA events after one warm-up launch; *gflops
+ * = 2 x FMAs / time in GFLOP/s.  It is the peak the FP64 particle pass is
+ * compared with.  Allocates and frees a small device buffer; synchronises
+ * the device.  Errors: PIC_ERR_ARG (iters outside 16 .. 2^20, null
+ * gflops), PIC_ERR_CUDA.
+ */
+pic_status pic_fp64_fma_rate(int32_t iters, double *gflops);
+
 void pic_destroy(pic_handle *h);
 const char *pic_last_error(const pic_handle *h);
 const char *pic_status_string(pic_status s);

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
 
-SOURCES = ["pic_api.cu", "particles.cu", "sortk.cu", "field.cu", "mg.cu", "noalloc.cu", "window.cu"]
+SOURCES = ["pic_api.cu", "particles.cu", "sortk.cu", "field.cu", "mg.cu", "noalloc.cu", "window.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I", INCLUDE, "-I", CSRC]

@@ -4,12 +4,15 @@
 // Cell sort: counts per cell (made by the particle pass), an exclusive scan
 // into per-cell cursors, then a rank pass that writes the permutation the
 // next pass reads through.  Dead particles (cell -1) are left out, so the
-// sort also compacts.  Order inside a cell is not fixed.
+// sort also compacts.  Order inside a cell is not fixed (shared and global
+// atomics hand out the places).
 //
 // Newborns are numbered next_id + rank of their key (parent species, parent
 // id, birth slot): one block ranks small batches directly, larger batches
 // go through an LSD radix sort of (key, index) pairs, both in one
 // cooperative launch that reads the count on the device.
+#include <limits.h>
+
 #include <algorithm>
 
 #include "pic_internal.cuh"
@@ -135,38 +138,117 @@ void launch_step_check(const DevScalars *ds, StepCtl *ctl, cudaStream_t st) {
 }
 
 // ---- rank: perm[cursor[cell]++] = element (main first, then births) ----
+//
+// A block takes segments of kRankSeg consecutive elements.  The main set is
+// in (old) cell order and a particle moves at most a few cells per step, so
+// the new cells of a segment fall in a window of at most kRankWin cells above
+// the segment's smallest: the block counts its elements per window cell in
+// shared memory (the count a shared atomic returns is the element's rank in
+// the block), reserves each cell's places with one global atomic per
+// distinct cell, and writes the permutation.  A segment whose cells spread
+// wider (the births, which come in any order) ranks warp by warp: one
+// global atomic per distinct cell of a warp (__match_any_sync).
+constexpr int kRankThreads = 256;
+constexpr int kRankPer = 8;
+constexpr int kRankSeg = kRankThreads * kRankPer;
+constexpr int kRankWin = 2048;
+
 template <typename T>
-__global__ void k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births,
-                       const int32_t *n_births_dev, int32_t *cursor, int32_t *perm,
-                       const int32_t *n_alive, int64_t cap, const int32_t *status, const StepCtl *ctl,
-                       int ncell) {
+__global__ void __launch_bounds__(kRankThreads)
+    k_rank(PBuf<T> mainb, const int32_t *n_main_dev, PBuf<T> births, const int32_t *n_births_dev,
+           int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap, const int32_t *status,
+           const StepCtl *ctl, int ncell) {
+    __shared__ int s_hist[kRankWin];
+    __shared__ int s_lo, s_hi;
     // a failed step keeps the previous permutation
     if (sort_skip(ctl) || (int64_t)*n_alive > cap || (*status & (ST_CAPACITY | ST_BIRTH_OVERFLOW))) return;
     const int nm = *n_main_dev, nb = *n_births_dev;
     const int total = nm + nb;
-    const int lane = threadIdx.x & 31;
-    for (int base = blockIdx.x * blockDim.x; base < total; base += gridDim.x * blockDim.x) {
-        const int e = base + threadIdx.x;
-        int c = -1;
-        if (e < nm)
-            c = mainb.cell[e];
-        else if (e < total)
-            c = births.cell[e - nm];
-        if (c >= ncell) c = -1;  // never a cell of the mesh: no place is taken for it
-        // the input is in (old) cell order, so equal cells sit in runs of
-        // lanes: the first lane of a run reserves places for the whole run
-        const int cprev = __shfl_up_sync(0xffffffffu, c, 1);
-        const bool head = lane == 0 || cprev != c;
-        const unsigned heads = __ballot_sync(0xffffffffu, head);
-        const int first = 31 - __clz(heads & ((2u << lane) - 1u));  // head of this lane's run
-        const unsigned above = heads & ~((2u << lane) - 1u);
-        const int rend = above ? __ffs(above) - 1 : 32;               // one past the run's end
-        int pos = 0;
-        if (c >= 0 && head) pos = atomicAdd(cursor + c, rend - lane);
-        pos = __shfl_sync(0xffffffffu, pos, first);
-        // (cells and counts agree, so pos < *n_alive <= cap; the bound keeps
-        // an inconsistent pass from writing past the permutation)
-        if (c >= 0 && (int64_t)pos + (lane - first) < cap) perm[pos + (lane - first)] = e;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    // the cells of a segment; the next segment's are requested before the
+    // current one is ranked
+    auto load = [&](int base, int *c) {
+#pragma unroll
+        for (int u = 0; u < kRankPer; ++u) {
+            const int e = base + u * kRankThreads + tid;
+            int v = -1;
+            if (e < nm)
+                v = mainb.cell[e];
+            else if (e < total)
+                v = births.cell[e - nm];
+            c[u] = v < ncell ? v : -1;  // never a cell of the mesh: no place is taken for it
+        }
+    };
+    int c[kRankPer];
+    load(blockIdx.x * kRankSeg, c);
+    for (int seg = blockIdx.x; seg * kRankSeg < total; seg += gridDim.x) {
+        const int base = seg * kRankSeg;
+        int lo = INT_MAX, hi = -1;
+#pragma unroll
+        for (int u = 0; u < kRankPer; ++u)
+            if (c[u] >= 0) {
+                lo = min(lo, c[u]);
+                hi = max(hi, c[u]);
+            }
+        if (tid == 0) {
+            s_lo = INT_MAX;
+            s_hi = -1;
+        }
+        __syncthreads();
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (lane == 0) {
+            atomicMin(&s_lo, lo);
+            atomicMax(&s_hi, hi);
+        }
+        __syncthreads();
+        const int wlo = s_lo, whi = s_hi;
+        int cn[kRankPer];
+        load(base + gridDim.x * kRankSeg, cn);
+        if (whi >= 0 && whi - wlo < kRankWin) {
+            for (int w = tid; w <= whi - wlo; w += kRankThreads) s_hist[w] = 0;
+            __syncthreads();
+            // rank inside the block: lanes of a warp with one cell share one
+            // shared atomic (an ion warp is mostly a single cell)
+            int r[kRankPer];
+#pragma unroll
+            for (int u = 0; u < kRankPer; ++u) {
+                const unsigned peers = __match_any_sync(0xffffffffu, c[u]);
+                const int first = __ffs(peers) - 1;
+                int b = 0;
+                if (c[u] >= 0 && lane == first) b = atomicAdd(&s_hist[c[u] - wlo], __popc(peers));
+                r[u] = __shfl_sync(0xffffffffu, b, first) + __popc(peers & lt);
+            }
+            __syncthreads();
+            // each cell's places: one global atomic per distinct cell
+            for (int w = tid; w <= whi - wlo; w += kRankThreads) {
+                const int k = s_hist[w];
+                if (k > 0) s_hist[w] = atomicAdd(cursor + wlo + w, k);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kRankPer; ++u) {
+                if (c[u] < 0) continue;
+                const int pos = s_hist[c[u] - wlo] + r[u];
+                // (cells and counts agree, so pos < *n_alive <= cap; the bound
+                // keeps an inconsistent pass from writing past the permutation)
+                if ((int64_t)pos < cap) perm[pos] = base + u * kRankThreads + tid;
+            }
+        } else if (whi >= 0) {
+#pragma unroll
+            for (int u = 0; u < kRankPer; ++u) {
+                const unsigned peers = __match_any_sync(0xffffffffu, c[u]);
+                const int first = __ffs(peers) - 1;
+                int pos = 0;
+                if (c[u] >= 0 && lane == first) pos = atomicAdd(cursor + c[u], __popc(peers));
+                pos = __shfl_sync(0xffffffffu, pos, first) + __popc(peers & lt);
+                if (c[u] >= 0 && (int64_t)pos < cap) perm[pos] = base + u * kRankThreads + tid;
+            }
+        }
+        __syncthreads();  // s_lo, s_hi and s_hist are reused by the next segment
+#pragma unroll
+        for (int u = 0; u < kRankPer; ++u) c[u] = cn[u];
     }
 }
 
@@ -174,12 +256,12 @@ template <typename T>
 void launch_rank(PBuf<T> mainb, const int32_t *n_main, PBuf<T> births, const int32_t *n_births,
                  int32_t *cursor, int32_t *perm, const int32_t *n_alive, int64_t cap,
                  const int32_t *status, const StepCtl *ctl, int ncell, cudaStream_t st) {
-    // short-lived blocks (a few tiles each): beside the field solve they
-    // retire often, so the solve's blocks find SMs early; a small store
-    // takes no more blocks than its capacity fills (blocks stride on)
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(152 * 32, (cap + 255) / 256));
-    k_rank<T><<<grid, 256, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap, status,
-                                     ctl, ncell);
+    // a few segments per block: beside the field solve the blocks retire
+    // often, so the solve's blocks find SMs early; a small store takes no
+    // more blocks than its capacity fills (blocks stride on)
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(152 * 8, (cap + kRankSeg - 1) / kRankSeg));
+    k_rank<T><<<grid, kRankThreads, 0, st>>>(mainb, n_main, births, n_births, cursor, perm, n_alive, cap, status,
+                                             ctl, ncell);
 }
 
 // ---- newborn numbering ----

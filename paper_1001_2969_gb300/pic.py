@@ -89,7 +89,7 @@ SYMBOLS = ("pic_init", "pic_step", "pic_field_solve", "pic_moments", "pic_get_pa
            "pic_get_counts", "pic_save", "pic_load", "pic_profile", "pic_timings", "pic_destroy",
            "pic_last_error", "pic_status_string", "pic_field_solve_noalloc", "pic_batch_init",
            "pic_batch_step", "pic_batch_destroy", "pic_tune", "pic_get_circuit", "pic_window",
-           "pic_merge", "pic_selftest_wait")
+           "pic_merge", "pic_selftest_wait", "pic_fp64_fma_rate")
 
 
 class PicError(RuntimeError):
@@ -119,6 +119,7 @@ def lib():
         L.pic_get_circuit.argtypes = [vp, _dp]
         L.pic_merge.argtypes = [vp, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
         L.pic_selftest_wait.argtypes = [C.c_int64, C.POINTER(C.c_int32)]
+        L.pic_fp64_fma_rate.argtypes = [C.c_int32, _dp]
         L.pic_window.argtypes = [vp, C.c_int32, C.c_int32, _dp, C.c_double, _dp, C.c_int32, _dp, _dp, _dp]
         L.pic_field_solve.argtypes = [vp, vp, vp, C.c_double, vp, C.c_int32,
                                       C.POINTER(pic_solve_info)]
@@ -354,6 +355,15 @@ def pic_selftest_wait(polls: int = 1 << 16) -> bool:
     if st != PIC_OK:
         raise PicError(st, "pic_selftest_wait failed")
     return bool(g.value)
+
+
+def pic_fp64_fma_rate(iters: int = 4096) -> float:
+    """Measured FP64 fused multiply-add rate of the current device, GFLOP/s."""
+    g = C.c_double(0.0)
+    st = lib().pic_fp64_fma_rate(int(iters), C.byref(g))
+    if st != PIC_OK:
+        raise PicError(st, "pic_fp64_fma_rate failed")
+    return g.value
 
 
 def pic_tune(h: Handle, steps_per_variant: int = 2, variants=None):
