@@ -42,6 +42,10 @@ WORKLOAD = WORKLOADS["c2"]
 # algorithmic bytes of the particle pass per particle: the state read once and
 # written once (mixed: cell 4 + offsets 8 + v 12 + a 8 + w 4 + id 8 = 44 B)
 BYTES_PER_PARTICLE = {"mixed": 88, "fp64": 152}
+# FP64 floating-point operations of the FP64 particle pass per particle-step
+# (2 DFMA + DADD + DMUL thread instructions; ncu on the c2 mesh, 1M + 1M
+# particles: electrons 256, ions 225; profiles/k_step_fp64_c2.md)
+FP64_FLOPS_PER_PARTICLE = 240
 
 
 def whole_job(ms, psteps, e2e_seconds, e2e_psteps, world, device="cuda"):
@@ -433,7 +437,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--cpu-steps", type=int, default=3)
@@ -539,11 +543,22 @@ def main():
         r = res["fp64"]
         t64 = r["timings"]
         k64 = t64["particle_e_ms"] + t64["particle_i_ms"]
+        # the FP64 pass is bound by GB300's FP64 pipe: its FP64 arithmetic
+        # against the FP64 FMA rate a plain kernel reaches on this GPU
+        fma = pic_lib_rate()
+        flops = FP64_FLOPS_PER_PARTICLE * r["prof_psteps"] / (k64 * 1e-3) / 1e9 if k64 > 0 else None
         line["fp64"] = {"value": r["psteps"] / (r["ms"] * 1e-3), "unit": UNIT,
                         "ms_per_step": r["ms"] / args.fp64_steps, "steps": args.fp64_steps,
                         "particle_pass_ms_per_step": k64 / args.fp64_steps,
                         "solve_ms_per_step": t64["solve_ms"] / args.fp64_steps,
-                        "mg_cycles_per_step": r["mg_cycles"]}
+                        "mg_cycles_per_step": r["mg_cycles"],
+                        "roofline": {"bound": "alu", "kernel": "k_step<double> (both species)",
+                                     "achieved": flops, "peak": fma, "unit": "GFLOP/s",
+                                     "frac": flops / fma if flops and fma else None,
+                                     "peak_source": "measured: pic_fp64_fma_rate (FP64 FMA chains)",
+                                     "flops_per_particle": FP64_FLOPS_PER_PARTICLE,
+                                     "note": "DFMA, DADD and DMUL only; FP64 conversions and compares "
+                                             "issue on the same pipe (profiles/k_step_fp64_c2.md)"}}
     e = main_r["e2e"]
     line["e2e"] = {"value": e2e_n / e2e_s, "unit": UNIT,
                    "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"],
@@ -561,6 +576,13 @@ def main():
               f"{_status_name(pic_lib(), bad[-1])}); the figures above are void", file=sys.stderr)
         return 1
     return 0
+
+
+def pic_lib_rate():
+    """The GPU's FP64 FMA rate in GFLOP/s (pic_fp64_fma_rate)."""
+    from paper_1001_2969_gb300 import pic
+
+    return pic.pic_fp64_fma_rate(16384)
 
 
 def first_bad(statuses):
