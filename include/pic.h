@@ -337,6 +337,41 @@ pic_status pic_set_boundary(pic_handle *h, const double *phi_zL, int32_t on_devi
 pic_status pic_get_fields(pic_handle *h, double *rho, double *chi, double *phi, double *Ez,
                           double *Er, int32_t on_device);
 
+/*
+ * pic_get_deposit / pic_set_deposit -- the particle deposit the next step's
+ * field solve takes, for a reactor whose particles are shared among
+ * processes (Sec. 2.7: each process deposits its own particles, the sums are
+ * all-reduced, and every process then solves the same field, as the paper's
+ * MPI version does).  Ne, Ni: the electron and ion deposits, [nz][nr] FP64,
+ * the sums over particles of weight x shape factor at each node (Eq. (10)
+ * before the division by the node volume); q: 3 doubles, the charge
+ * absorbed at z = 0, z = L and r = R since the last external-circuit solve
+ * (the whole run without a circuit), which the circuit's electrode charge
+ * takes.  Valid between calls that step: after pic_step returns they hold
+ * this handle's deposit of its last pass; what pic_set_deposit writes is
+ * what the next step solves with.  The time averages of pic_moments are
+ * taken before any exchange, from this handle's own deposit, and add up
+ * across processes.  NULL members are skipped; pointers are host memory
+ * unless on_device (then device memory, ordered on the handle's stream).
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA.
+ */
+pic_status pic_get_deposit(pic_handle *h, double *Ne, double *Ni, double *q, int32_t on_device);
+pic_status pic_set_deposit(pic_handle *h, const double *Ne, const double *Ni, const double *q,
+                           int32_t on_device);
+
+/*
+ * pic_set_id_stride -- number this handle's newborns next_id[s] + stride x
+ * (rank of their key) for species s, next_id advancing by stride x births
+ * (no counterpart in the paper; the default is the stride 1 of the
+ * canonical numbering).  With the particles of one reactor shared among P
+ * processes, process r sets stride P and next_id[s] = N_s + r (N_s above
+ * every id in use) so that newborn ids stay unique across the processes;
+ * since every draw is keyed by the particle id, a newborn's history then
+ * differs from the one-process run's, which is statistically the same.
+ * next_id: 2 values, host.  Errors: PIC_ERR_ARG (stride 0, null).
+ */
+pic_status pic_set_id_stride(pic_handle *h, const uint64_t *next_id, uint64_t stride);
+
 /* pic_get_counts -- particles alive per species, steps taken, next ids. */
 pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64_t *next_id);
 

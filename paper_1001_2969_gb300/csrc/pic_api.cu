@@ -1812,6 +1812,45 @@ pic_status pic_set_boundary(pic_handle *h, const double *phi_zL, int32_t on_devi
     return cuda_check(h, "set_boundary");
 }
 
+// The deposit the next step's solve takes (Sec. 2.7: with the particles
+// shared among processes each deposits its own and the sums are
+// all-reduced, then every process solves the same field).
+pic_status pic_get_deposit(pic_handle *h, double *Ne, double *Ni, double *q, int32_t on_device) {
+    if (!h) return PIC_ERR_ARG;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t gb = (size_t)h->ng * sizeof(double);
+    if (Ne) cudaMemcpyAsync(Ne, h->N[0], gb, k, h->st);
+    if (Ni) cudaMemcpyAsync(Ni, h->N[1], gb, k, h->st);
+    if (q) cudaMemcpyAsync(q, h->ds->qstep, 3 * sizeof(double), k, h->st);
+    if (!on_device) cudaStreamSynchronize(h->st);
+    return cuda_check(h, "get_deposit");
+}
+
+pic_status pic_set_deposit(pic_handle *h, const double *Ne, const double *Ni, const double *q,
+                           int32_t on_device) {
+    if (!h) return PIC_ERR_ARG;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t gb = (size_t)h->ng * sizeof(double);
+    if (Ne) cudaMemcpyAsync(h->N[0], Ne, gb, k, h->st);
+    if (Ni) cudaMemcpyAsync(h->N[1], Ni, gb, k, h->st);
+    if (q) cudaMemcpyAsync(h->ds->qstep, q, 3 * sizeof(double), k, h->st);
+    // host sources are the caller's: they are read before the call returns
+    if (!on_device) cudaStreamSynchronize(h->st);
+    return cuda_check(h, "set_deposit");
+}
+
+pic_status pic_set_id_stride(pic_handle *h, const uint64_t *next_id, uint64_t stride) {
+    if (!h || !next_id || stride < 1) return fail(h, PIC_ERR_ARG, "bad id stride");
+    const pic_status cs = complete_sort(h);
+    if (cs != PIC_OK) return cs;
+    h->sp[0].next_id = next_id[0];
+    h->sp[1].next_id = next_id[1];
+    push_ctl(h);
+    cudaMemcpyAsync(&h->sctl->id_stride, &stride, sizeof(stride), cudaMemcpyHostToDevice, h->st);
+    cudaStreamSynchronize(h->st);
+    return cuda_check(h, "set_id_stride");
+}
+
 pic_status pic_get_fields(pic_handle *h, double *rho, double *chi, double *phi, double *Ez,
                           double *Er, int32_t on_device) {
     if (!h) return PIC_ERR_ARG;

@@ -58,6 +58,10 @@ struct StepCtl {
     int32_t sort_fail_status;  // ST_* bits of the failure
     int32_t pad2;
     int64_t sort_fail_step;    // number of the step whose sort failed
+    // newborns of one pass get ids next_id + id_stride * rank (0 means 1): a
+    // reactor whose particles are shared among processes numbers each
+    // process's newborns in its own residue class
+    uint64_t id_stride;
 };
 
 // a sort kernel has nothing to do: no pass waits for it, or the sort failed

@@ -7,8 +7,9 @@
 // sort also compacts.  Order inside a cell is not fixed (shared and global
 // atomics hand out the places).
 //
-// Newborns are numbered next_id + rank of their key (parent species, parent
-// id, birth slot): one block ranks small batches directly, larger batches
+// Newborns are numbered next_id + stride x rank of their key (parent
+// species, parent id, birth slot; the stride is 1 unless the reactor's
+// particles are shared among processes): one block ranks small batches directly, larger batches
 // go through an LSD radix sort of (key, index) pairs, both in one
 // cooperative launch that reads the count on the device.
 #include <limits.h>
@@ -299,20 +300,22 @@ __global__ void __launch_bounds__(kRadixThreads)
     if (nb <= kSmallBirths) {
         if (blockIdx.x != 0) return;
         const uint64_t base = ctl->next_id[s];
+        const uint64_t stride = ctl->id_stride ? ctl->id_stride : 1ull;
         for (int k = tid; k < nb; k += blockDim.x) s_key[k] = key[k];
         __syncthreads();
         for (int k = tid; k < nb; k += blockDim.x) {
             const uint64_t mine = s_key[k];
             int rank = 0;
             for (int q = 0; q < nb; ++q) rank += s_key[q] < mine;
-            id[k] = base + (uint64_t)rank;
+            id[k] = base + stride * (uint64_t)rank;
         }
         __syncthreads();
-        if (tid == 0) ctl->next_id[s] = base + (uint64_t)nb;
+        if (tid == 0) ctl->next_id[s] = base + stride * (uint64_t)nb;
         return;
     }
     // every block reads the base before the first barrier; block 0 moves it on at the end
     const uint64_t base = ctl->next_id[s];
+    const uint64_t stride = ctl->id_stride ? ctl->id_stride : 1ull;
     const int ntiles = (nb + kRadixTile - 1) / kRadixTile;
     unsigned nbar = 0;
     // a wait that gives up fails the sort (its ids would be wrong)
@@ -416,8 +419,8 @@ __global__ void __launch_bounds__(kRadixThreads)
         va = vb;
         vb = tv;
     }
-    for (int r = blockIdx.x * blockDim.x + tid; r < nb; r += gridDim.x * blockDim.x) id[va[r]] = base + (uint64_t)r;
-    if (blockIdx.x == 0 && tid == 0) ctl->next_id[s] = base + (uint64_t)nb;
+    for (int r = blockIdx.x * blockDim.x + tid; r < nb; r += gridDim.x * blockDim.x) id[va[r]] = base + stride * (uint64_t)r;
+    if (blockIdx.x == 0 && tid == 0) ctl->next_id[s] = base + stride * (uint64_t)nb;
 }
 
 // failure-detection self-test: one block waits at the bounded grid barrier

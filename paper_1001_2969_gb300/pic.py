@@ -89,7 +89,8 @@ SYMBOLS = ("pic_init", "pic_step", "pic_field_solve", "pic_moments", "pic_get_pa
            "pic_get_counts", "pic_save", "pic_load", "pic_profile", "pic_timings", "pic_destroy",
            "pic_last_error", "pic_status_string", "pic_field_solve_noalloc", "pic_batch_init",
            "pic_batch_step", "pic_batch_destroy", "pic_tune", "pic_get_circuit", "pic_window",
-           "pic_merge", "pic_selftest_wait", "pic_fp64_fma_rate")
+           "pic_merge", "pic_selftest_wait", "pic_fp64_fma_rate", "pic_get_deposit",
+           "pic_set_deposit", "pic_set_id_stride")
 
 
 class PicError(RuntimeError):
@@ -120,6 +121,9 @@ def lib():
         L.pic_merge.argtypes = [vp, C.c_int32, C.c_double, C.c_double, _i64p, _dp]
         L.pic_selftest_wait.argtypes = [C.c_int64, C.POINTER(C.c_int32)]
         L.pic_fp64_fma_rate.argtypes = [C.c_int32, _dp]
+        L.pic_get_deposit.argtypes = [vp, vp, vp, vp, C.c_int32]
+        L.pic_set_deposit.argtypes = [vp, vp, vp, vp, C.c_int32]
+        L.pic_set_id_stride.argtypes = [vp, _u64p, C.c_uint64]
         L.pic_window.argtypes = [vp, C.c_int32, C.c_int32, _dp, C.c_double, _dp, C.c_int32, _dp, _dp, _dp]
         L.pic_field_solve.argtypes = [vp, vp, vp, C.c_double, vp, C.c_int32,
                                       C.POINTER(pic_solve_info)]
@@ -355,6 +359,30 @@ def pic_selftest_wait(polls: int = 1 << 16) -> bool:
     if st != PIC_OK:
         raise PicError(st, "pic_selftest_wait failed")
     return bool(g.value)
+
+
+def pic_get_deposit(h: Handle):
+    """The deposit the next solve takes: {"Ne", "Ni": [nz][nr], "q": [3]} (host)."""
+    nz, nr = h.nz, h.nr
+    Ne, Ni, q = np.zeros((nz, nr)), np.zeros((nz, nr)), np.zeros(3)
+    _check(h, lib().pic_get_deposit(h.ptr, Ne.ctypes.data, Ni.ctypes.data, q.ctypes.data, 0))
+    return {"Ne": Ne, "Ni": Ni, "q": q}
+
+
+def pic_set_deposit(h: Handle, Ne, Ni, q=None) -> None:
+    """Replace the deposit the next solve takes (host arrays)."""
+    Ne = np.ascontiguousarray(Ne, dtype=np.float64)
+    Ni = np.ascontiguousarray(Ni, dtype=np.float64)
+    assert Ne.size == h.nz * h.nr and Ni.size == h.nz * h.nr
+    qa = np.ascontiguousarray(q, dtype=np.float64) if q is not None else None
+    _check(h, lib().pic_set_deposit(h.ptr, Ne.ctypes.data, Ni.ctypes.data,
+                                    qa.ctypes.data if qa is not None else None, 0))
+
+
+def pic_set_id_stride(h: Handle, next_id, stride: int) -> None:
+    """Newborns of species s get ids next_id[s] + stride x rank (shared reactors)."""
+    ids = (C.c_uint64 * 2)(*[int(x) for x in next_id])
+    _check(h, lib().pic_set_id_stride(h.ptr, ids, int(stride)))
 
 
 def pic_fp64_fma_rate(iters: int = 4096) -> float:

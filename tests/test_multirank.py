@@ -63,3 +63,67 @@ def test_one_rank_is_its_own_whole_job():
     import bench
 
     assert bench.whole_job(3.0, 10.0, 0.5, 4.0, 1) == (3.0, 10.0, 0.5, 4.0)
+
+
+def _shard_worker(rank, world, port, root, q):
+    """The deposit exchange of a shared reactor on a fake handle (no GPU)."""
+    import numpy as np
+    import torch.distributed as dist
+
+    sys.path.insert(0, root)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1001_2969_gb300 import pic, shard
+
+    class Fake:
+        nz, nr = 3, 4
+
+    h = Fake()
+    state = {"Ne": np.full((3, 4), 1.0 + rank), "Ni": np.arange(12.0).reshape(3, 4) * (rank + 1),
+             "q": np.array([1.0, 2.0, 3.0]) * (10 ** rank), "steps": 0}
+    pic.pic_get_deposit = lambda hh: {k: state[k].copy() for k in ("Ne", "Ni", "q")}
+
+    def setd(hh, Ne, Ni, q=None):
+        state["Ne"], state["Ni"], state["q"] = (np.asarray(Ne).reshape(3, 4), np.asarray(Ni).reshape(3, 4),
+                                                np.asarray(q))
+
+    def stepf(hh, n):
+        state["steps"] += n
+        return pic.PIC_OK
+
+    pic.pic_set_deposit = setd
+    pic.pic_step = stepf
+    st = shard.step(h, 2, None)
+    q.put((rank, st, state["steps"], state["Ne"].tolist(), state["Ni"].tolist(), state["q"].tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shared_reactor_deposit_exchange_over_two_gloo_ranks():
+    """Each rank's deposit (electrons, ions, wall charges) is replaced by the sum
+    over the ranks after every step (Sec. 2.7's all-reduce before the solve)."""
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, root, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = {}
+    for _ in range(2):
+        r, *rest = q.get(timeout=180)
+        got[r] = rest
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # two steps: the first exchange sums (1 + 2), the second sums the sums
+    for r in (0, 1):
+        st, steps, Ne, Ni, qq = got[r]
+        assert st == 0 and steps == 2
+        np.testing.assert_array_equal(np.array(Ne), np.full((3, 4), 2.0 * 3.0))
+        np.testing.assert_array_equal(np.array(Ni), 2.0 * 3.0 * np.arange(12.0).reshape(3, 4))
+        np.testing.assert_array_equal(np.array(qq), 2.0 * 11.0 * np.array([1.0, 2.0, 3.0]))
