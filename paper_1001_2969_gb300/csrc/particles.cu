@@ -343,8 +343,8 @@ constexpr int kThreads = 256;
 // shared-memory atomics of a warp are serialised
 constexpr int kEedfCopies = 8;
 
-// The fused particle pass (Sec. 2.1 merged cycle).  Each block walks chunks
-// of kChunk particles of the cell-sorted input.  Lanes of a warp hold
+// The fused particle pass (Sec. 2.1 merged cycle).  Each block works on
+// chunks of kChunk particles of the cell-sorted input, claimed from a counter.  Lanes of a warp hold
 // consecutive particles, so their output cells come in runs; each run's
 // deposit is summed across its lanes and its first lane adds it to the four
 // nodes with global reductions (fire-and-forget, resolved in L2).  A
@@ -381,18 +381,29 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     const int n = *a.n_alive;
     const int nmain = *a.n_main_src;
     const int nchunks = (n + kChunk - 1) / kChunk;
+    // chunks are claimed one at a time from a counter, the next one while
+    // the current one is worked on: blocks that meet costly chunks (many
+    // collisions) take fewer, and the pass ends within one chunk's time
+    __shared__ int s_claim;
+    if (tid == 0) s_claim = atomicAdd(a.chunk_next, 1);
+    __syncthreads();
+    int ck = s_claim;
     // this thread's perm entries of its next chunk, read a chunk ahead
     int pn[kPPT];
     if (PF) {
 #pragma unroll
         for (int m = 0; m < kPPT; ++m) {
-            const int k = blockIdx.x * kChunk + m * kThreads + tid;
+            const int k = ck * kChunk + m * kThreads + tid;
             pn[m] = k < n ? a.perm[k] : 0;
         }
     }
-    for (int ck = blockIdx.x; ck < nchunks; ck += gridDim.x) {
+    while (ck < nchunks) {
         const int base = ck * kChunk;
         const int end = min(base + kChunk, n);
+        __syncthreads();  // every thread has read s_claim
+        if (tid == 0) s_claim = atomicAdd(a.chunk_next, 1);
+        __syncthreads();
+        const int ck_next = s_claim;
         // request the chunk's particles, then read the next chunk's perm
         // entries; a thread fills and reads only its own slots, so chunks
         // need no barrier
@@ -423,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                 }
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
-            const int nb = (ck + gridDim.x) * kChunk;
+            const int nb = ck_next * kChunk;
 #pragma unroll
             for (int m = 0; m < kPPT; ++m) {
                 const int k = nb + m * kThreads + tid;
@@ -598,6 +609,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                 atomicAdd(g + a.nr + 1, (double)c11);
             }
         }
+        ck = ck_next;
     }
     __syncthreads();
     for (int k = tid; k < PIC_NCOUNT; k += blockDim.x)
@@ -626,6 +638,12 @@ void launch_shape(const StepArgs<T> &a, int grid, cudaStream_t st) {
     // it for every size (the static tallies come on top of `smem`)
     if (smem > 0)
         cudaFuncSetAttribute(k_step<T, PF, PPT, XYZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // blocks claim chunks until none is left: as many as are resident at once
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<T, PF, PPT, XYZ>, kThreads, smem);
+    if (per_sm > 0 && nsm > 0) grid = std::min(grid, per_sm * nsm);
     k_step<T, PF, PPT, XYZ><<<grid, kThreads, smem, st>>>(a);
 }
 

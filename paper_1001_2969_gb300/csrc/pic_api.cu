@@ -764,6 +764,7 @@ void fill_step_args(pic_handle *h, StepArgs<T> &a, int s, int src_set, int dst_s
     }
     a.bcap = (int)std::min(h->sp[0].bcap, h->sp[1].bcap);
     a.ds = h->ds;
+    a.chunk_next = &h->ds->chunk_next[s];
     a.eedf = (s == 0 && h->cfg.eedf_bins > 0) ? h->eedf : nullptr;
     a.eedf_bins = h->cfg.eedf_bins;
     a.eedf_scale = h->cfg.eedf_bins > 0 ? (T)(h->cfg.eedf_bins / h->cfg.eedf_emax_eV) : (T)0;
@@ -906,7 +907,9 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv) {
         // blocks walk the chunks of the count on the device; a small store
         // takes no more blocks than its capacity has chunks
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->step_grid, (h->sp[s].cap + 1023) / 1024));
-        launch_step<T>(a, grid, h->variant[s], (fork2 && s == 1) ? sb : st);
+        cudaStream_t ps = (fork2 && s == 1) ? sb : st;
+        cudaMemsetAsync(a.chunk_next, 0, sizeof(int32_t), ps);
+        launch_step<T>(a, grid, h->variant[s], ps);
         h->launches += 1;
         h->particle_launches += 1;
     }

@@ -172,6 +172,7 @@ struct DevScalars {
     double qstep[3];  // absorbed charge per wall since the circuit last took it
     unsigned long long mg_res_bits;  // max |residual| of the last residual kernel
     unsigned long long mg_aux_bits;
+    int32_t chunk_next[2];  // the particle pass's next unclaimed chunk, per species
 };
 
 template <typename T>
@@ -231,6 +232,7 @@ struct StepArgs {
     double *N[2];
     int32_t *counts[2];
     DevScalars *ds;
+    int32_t *chunk_next;  // zero before the launch; blocks claim chunks from it
     double *eedf;
     int eedf_bins;
     T eedf_scale;  // bins per eV
