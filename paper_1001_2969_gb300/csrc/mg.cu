@@ -436,6 +436,12 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
     while (lb > 0 && units_of(m.nz[lb - 1]) <= G) --lb;
     const bool in_group = (int)blockIdx.x < G;
     __shared__ unsigned long long s_r[32], s_b[32];
+    __shared__ double s_dot[4][32];
+    // the mixed path accelerates its refinement by flexible GCR(1) (the
+    // Krylov vectors are allocated for it); the FP64 path runs the paper's
+    // plain V(0,1) iteration
+    const bool kry = mixed && m.kr != nullptr && L > 0;
+    double kc = 0.0;  // |w|^2 of the previous direction's A-image
     __shared__ __align__(8) unsigned long long s_mbar[3];
     __shared__ int s_decide;
     if (tid == 0) {
@@ -497,6 +503,159 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
             Tv *T1 = T0 + (size_t)tw * nz0;
             Tv *f0v = mixed ? (Tv *)m.f32[0] : (Tv *)m.f64[0];
             const int ntile = (n + tw - 1) / tw;
+            // the restriction chain of the residual tile T0 (columns j0 ..)
+            // down to the coarsest level, in the V-cycle's type
+            auto chain = [&](int j0) {
+        Tv *src = T0, *dst = T1;
+        int nzp = nz0;
+        for (int l = 1; l <= L; ++l) {
+            const int nzc = m.nz[l];
+            Tv *fl = mixed ? (Tv *)m.f32[l] : (Tv *)m.f64[l];
+            for (int e = tid; e < tw * (nzc - 2); e += nt) {
+                const int c = e % tw, I = 1 + e / tw, j = j0 + c;
+                const Tv *s = src + (size_t)c * nzp;
+                const Tv v = (Tv)0.5 * s[2 * I - 1] + s[2 * I] + (Tv)0.5 * s[2 * I + 1];
+                dst[(size_t)c * nzc + I] = v;
+                if (j < n) {
+                    const size_t k = (size_t)I * nr + j;
+                    if (l == L)
+                        m.fc64[k] = (double)v;
+                    else
+                        fl[k] = v;
+                }
+            }
+            __syncthreads();
+            Tv *tmp = src;
+            src = dst;
+            dst = tmp;
+            nzp = nzc;
+        }
+            };
+            if (kry && cyc > 0) {
+                // ---- flexible GCR(1) step (mixed path) ----
+                // z: the V-cycle's correction of the last cycle; w = A z;
+                // the direction is z less its projection on the previous
+                // one (in the A-image), the step length minimises |r|_2
+                double a[4] = {0.0, 0.0, 0.0, 0.0};  // r.w, w.w, w.wp, r.wp
+                for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+                    const int j0 = t * tw;
+                    for (int e = tid; e < sw * nz0; e += nt) {
+                        const int c = e % sw - 1, i = e / sw, j = j0 + c;
+                        S[(size_t)(c + 1) * nz0 + i] = (j >= 0 && j < nr) ? (double)delta[(size_t)i * nr + j] : 0.0;
+                    }
+                    __syncthreads();
+                    // batches of kU nodes per thread, loads first
+                    for (int e0 = tid; e0 < tw * (nz0 - 2); e0 += kU * nt) {
+                        double ca[kU], cb[kU], ce[kU], cd[kU], dgv[kU], rv[kU], wpv[kU];
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int e = e0 + u * nt, c = e % tw, i = 1 + e / tw, j = j0 + c;
+                            ca[u] = cb[u] = ce[u] = cd[u] = dgv[u] = rv[u] = wpv[u] = 0.0;
+                            if (e < tw * (nz0 - 2) && j < n) {
+                                const size_t k = (size_t)i * nr + j;
+                                ca[u] = cz[k - nr];
+                                cb[u] = cz[k];
+                                ce[u] = cr[k];
+                                cd[u] = j > 0 ? cr[k - 1] : 0.0;
+                                dgv[u] = m.dg0[k];
+                                rv[u] = m.kr[k];
+                                wpv[u] = m.kwp[k];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int e = e0 + u * nt, c = e % tw, i = 1 + e / tw, j = j0 + c;
+                            if (e >= tw * (nz0 - 2) || j >= n) continue;
+                            const size_t k = (size_t)i * nr + j;
+                            const double *Sc = S + (size_t)(c + 1) * nz0 + i;
+                            const double w = dgv[u] * Sc[0] - ca[u] * Sc[-1] - cb[u] * Sc[1] - ce[u] * Sc[nz0] -
+                                             cd[u] * Sc[-nz0];
+                            m.kw[k] = w;
+                            a[0] += rv[u] * w;
+                            a[1] += w * w;
+                            a[2] += w * wpv[u];
+                            a[3] += rv[u] * wpv[u];
+                        }
+                    }
+                    __syncthreads();  // S is reused by the next tile
+                }
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    for (int o = 16; o > 0; o >>= 1) a[d] += __shfl_xor_sync(0xffffffffu, a[d], o);
+                    if (lane == 0) s_dot[d][warp] = a[d];
+                }
+                __syncthreads();
+                if (tid < 4) {
+                    double v = 0.0;
+                    for (int q = 0; q < (nt >> 5); ++q) v += s_dot[tid][q];
+                    m.kpart[(size_t)blockIdx.x * 4 + tid] = v;
+                }
+                if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
+                    leave(false);
+                    return;
+                }
+                // every block sums the partial products in block order: the
+                // same step length everywhere
+                if (warp == 0) {
+                    double v[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int b = lane; b < (int)gridDim.x; b += 32)
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) v[d] += m.kpart[(size_t)b * 4 + d];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        for (int o = 16; o > 0; o >>= 1) v[d] += __shfl_xor_sync(0xffffffffu, v[d], o);
+                        if (lane == 0) s_dot[d][0] = v[d];
+                    }
+                }
+                __syncthreads();
+                const double beta = kc > 0.0 ? s_dot[2][0] / kc : 0.0;
+                const double den = s_dot[1][0] - beta * s_dot[2][0];
+                const double alpha = den > 0.0 ? (s_dot[0][0] - beta * s_dot[3][0]) / den : 1.0;
+                kc = den > 0.0 ? den : 0.0;
+                __syncthreads();  // s_dot is rewritten by the next cycle
+                for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+                    const int j0 = t * tw;
+                    for (int e0 = tid; e0 < tw * (nz0 - 2); e0 += kU * nt) {
+                        double pz[kU], qw[kU], zp[kU], wpv[kU], xv[kU], rv[kU];
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int e = e0 + u * nt, c = e % tw, i = 1 + e / tw, j = j0 + c;
+                            pz[u] = qw[u] = zp[u] = wpv[u] = xv[u] = rv[u] = 0.0;
+                            if (e < tw * (nz0 - 2) && j < n) {
+                                const size_t k = (size_t)i * nr + j;
+                                pz[u] = (double)delta[k];
+                                qw[u] = m.kw[k];
+                                if (beta != 0.0) {
+                                    zp[u] = m.kzp[k];
+                                    wpv[u] = m.kwp[k];
+                                }
+                                xv[u] = cur[k];
+                                rv[u] = m.kr[k];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int e = e0 + u * nt, c = e % tw, i = 1 + e / tw, j = j0 + c;
+                            if (e >= tw * (nz0 - 2)) break;
+                            double rn = 0.0;
+                            if (j < n) {
+                                const size_t k = (size_t)i * nr + j;
+                                const double p = pz[u] - beta * zp[u], q = qw[u] - beta * wpv[u];
+                                nxt[k] = xv[u] + alpha * p;
+                                rn = rv[u] - alpha * q;
+                                m.kr[k] = rn;
+                                m.kzp[k] = p;
+                                m.kwp[k] = q;
+                                rmax = max(rmax, abs_bits(rn));
+                                f0v[k] = (Tv)rn;
+                            }
+                            T0[(size_t)c * nz0 + i] = (Tv)rn;
+                        }
+                    }
+                    __syncthreads();
+                    chain(j0);
+                }
+            } else
             for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
                 const int j0 = t * tw;
                 // batches of kU elements per thread: all loads first (stores to
@@ -564,35 +723,13 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                             bmax = max(bmax, abs_bits(bb));
                         }
                         if (L > 0) f0v[k] = (Tv)r;
+                        if (kry) m.kr[k] = r;
                     }
                     T0[(size_t)c * nz0 + i] = (Tv)r;
                     }
                 }
                 __syncthreads();
-                Tv *src = T0, *dst = T1;
-                int nzp = nz0;
-                for (int l = 1; l <= L; ++l) {
-                    const int nzc = m.nz[l];
-                    Tv *fl = mixed ? (Tv *)m.f32[l] : (Tv *)m.f64[l];
-                    for (int e = tid; e < tw * (nzc - 2); e += nt) {
-                        const int c = e % tw, I = 1 + e / tw, j = j0 + c;
-                        const Tv *s = src + (size_t)c * nzp;
-                        const Tv v = (Tv)0.5 * s[2 * I - 1] + s[2 * I] + (Tv)0.5 * s[2 * I + 1];
-                        dst[(size_t)c * nzc + I] = v;
-                        if (j < n) {
-                            const size_t k = (size_t)I * nr + j;
-                            if (l == L)
-                                m.fc64[k] = (double)v;
-                            else
-                                fl[k] = v;
-                        }
-                    }
-                    __syncthreads();
-                    Tv *tmp = src;
-                    src = dst;
-                    dst = tmp;
-                    nzp = nzc;
-                }
+                chain(j0);
             }
             for (int o = 16; o > 0; o >>= 1) {
                 rmax = max(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));

@@ -54,6 +54,10 @@ struct MGFast {
     double *f0;                                 // fine right-hand side
     double *dg0;                                // fine operator's diagonal
     double *phi2;                               // second copy of phi (the solve alternates)
+    // flexible GCR(1) of the mixed path (null on the FP64 path): the FP64
+    // residual, A z of the last correction z, the previous direction and
+    // its A-image, and per-block partial dot products (4 per block)
+    double *kr, *kw, *kzp, *kwp, *kpart;
     MGCtl *ctl;
     MGFast *self;  // device copy of this struct (kernels read it through a pointer)
 };

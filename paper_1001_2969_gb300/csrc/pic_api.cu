@@ -636,6 +636,14 @@ void setup_device(pic_handle *h) {
     m.f0 = (double *)dalloc(h, gb);
     m.dg0 = (double *)dalloc(h, gb);
     m.phi2 = (double *)dalloc(h, gb);
+    if (h->mixed) {
+        m.kr = (double *)dalloc(h, gb);
+        m.kw = (double *)dalloc(h, gb);
+        m.kzp = (double *)dalloc(h, gb);
+        m.kwp = (double *)dalloc(h, gb);
+        m.kpart = (double *)dalloc(h, (size_t)4 * 1024 * sizeof(double));
+        for (double *z : {m.kr, m.kw, m.kzp, m.kwp}) cudaMemsetAsync(z, 0, gb, h->st);
+    }
     m.ctl = (MGCtl *)dalloc(h, sizeof(MGCtl));
     m.self = (MGFast *)dalloc(h, sizeof(MGFast));
     mg_fast_upload(m, h->st);

@@ -115,7 +115,10 @@ def test_deposit_parity_after_load(pic, prec):
 @pytest.mark.parametrize("mesh", [(33, 65), (65, 257), (129, 513)])
 def test_field_solve_parity(pic, prec, mesh):
     nz, nr = mesh
-    cfg = W.config("c1", nz=nz, nr=nr, precision=prec, mg_tol=1e-13 if prec == "fp64" else 1e-10,
+    # the mixed path (FP32 V-cycles in FP64 refinement, GCR-accelerated) to a
+    # relative residual of 1e-12, the oracle's plain V(0,1) to 1e-13: both
+    # are then within ~cond(A) 1e-12 of the same discrete solution
+    cfg = W.config("c1", nz=nz, nr=nr, precision=prec, mg_tol=1e-13 if prec == "fp64" else 1e-12,
                    mg_max_cycles=100)
     cfg = W.scaled(cfg, 0)
     h = pic.pic_init(cfg, load=False)
@@ -126,7 +129,7 @@ def test_field_solve_parity(pic, prec, mesh):
     o.set_grid("chi", chi)
     o.set_grid("rho", rho)
     o.set_grid("phi", np.zeros((nz, nr)))
-    ost, ocyc, ores = o.solve(80.0)
+    ost, ocyc, ores = o.solve(80.0, tol=1e-13)
     assert st == 0 and ost == 0
     assert nerr(phi, o.grid("phi")) < (1e-12 if prec == "fp64" else 1e-9)
     if prec == "fp64":
