@@ -10,7 +10,8 @@ through zero:
   (vr, vt, vz)  the velocity vector, relative to max(|v|, v_th), v_th the
                 species' thermal speed sqrt(e T/m) (a rotation error of the
                 scattering spreads over the components);
-  (ar, az)      the acceleration vector, relative to max(|a|, |q/m| E_max),
+  (ar, az[, at]) the acceleration vector (with a_theta under the X-Y-Z
+                pusher), relative to max(|a|, |q/m| E_max),
                 E_max the largest field of the step (a_bar carries the gathered
                 field, whose error the field solve bounds in the max norm);
   w             relative to max(w, w_r), w_r the split's reference weight of
@@ -72,8 +73,12 @@ def errors(cfg, s, g, o, emax, wref):
     dv = np.sqrt((g["vr"] - o["vr"]) ** 2 + (g["vt"] - o["vt"]) ** 2 + (g["vz"] - o["vz"]) ** 2)
     v = np.sqrt(o["vr"] ** 2 + o["vt"] ** 2 + o["vz"] ** 2)
     e = np.maximum(e, dv / np.maximum(v, vth))
-    da = np.hypot(g["ar"] - o["ar"], g["az"] - o["az"])
-    e = np.maximum(e, da / np.maximum(np.hypot(o["ar"], o["az"]), afl))
+    da2 = (g["ar"] - o["ar"]) ** 2 + (g["az"] - o["az"]) ** 2
+    a2 = o["ar"] ** 2 + o["az"] ** 2
+    if "at" in g and "at" in o:  # a_theta, carried by the X-Y-Z pusher
+        da2 = da2 + (g["at"] - o["at"]) ** 2
+        a2 = a2 + o["at"] ** 2
+    e = np.maximum(e, np.sqrt(da2) / np.maximum(np.sqrt(a2), afl))
     j = np.clip(np.floor(o["r"] / dr).astype(np.int64), 0, cfg["nr"] - 2)
     e = np.maximum(e, np.abs(g["w"] - o["w"]) / np.maximum(np.abs(o["w"]), wref[j]))
     return e
@@ -122,11 +127,15 @@ def explain(cfg, s, pid, inputs, grids, step, gpu_state, prec, tries=48, rel=4.0
         o.set_grid("Er", grids["Er"] * fr)
         o.set_step(step)
         o.set_particles(s, p)
+        if "at" in p:
+            o.set_at(s, p["at"])
         o.set_particles(1 - s, empty)
         o.set_next_id(0, 1 << 40)
         o.set_next_id(1, 1 << 40)
         o.particle_pass()
         out = o.get_particles(s)
+        if "at" in base:
+            out["at"] = o.get_at(s)
         hit = np.nonzero(out["id"] == pid)[0]
         if gpu_state is None:
             if len(hit) == 0:
@@ -174,7 +183,8 @@ def compare_species(cfg, s, g_raw, o_raw, prec, inputs=None, grids=None, step=No
         idx = np.arange(len(o["id"]))
         if sample is not None and sample < len(idx):
             idx = np.sort(rng.choice(len(idx), sample, replace=False))
-        e = errors(cfg, s, {f: g[f][idx] for f in FIELDS}, {f: o[f][idx] for f in FIELDS}, emax, wref)
+        F = FIELDS + (("at",) if "at" in g and "at" in o else ())
+        e = errors(cfg, s, {f: g[f][idx] for f in F}, {f: o[f][idx] for f in F}, emax, wref)
         assert e.max(initial=0.0) <= tol, (s, float(e.max()), o["id"][idx][np.argmax(e)])
         return 0
     in_ids = np.unique(np.asarray(inputs["id"], dtype=np.uint64))
@@ -185,8 +195,8 @@ def compare_species(cfg, s, g_raw, o_raw, prec, inputs=None, grids=None, step=No
     pick = np.arange(len(common))
     if sample is not None and sample < len(pick):
         pick = np.sort(rng.choice(len(pick), sample, replace=False))
-    e = errors(cfg, s, {f: g[f][gi[pick]] for f in FIELDS}, {f: o[f][oi[pick]] for f in FIELDS},
-               emax, wref)
+    F = FIELDS + (("at",) if "at" in g and "at" in o else ())
+    e = errors(cfg, s, {f: g[f][gi[pick]] for f in F}, {f: o[f][oi[pick]] for f in F}, emax, wref)
     suspects = common[pick][e > tol].tolist()
     suspects += np.setdiff1d(o["id"][o_par], g["id"][g_par]).tolist()  # absorbed by the GPU only
     unexplained = []
