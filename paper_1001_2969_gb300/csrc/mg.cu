@@ -394,15 +394,6 @@ __device__ __forceinline__ bool ld_wait(Loader &q) {
     return ok;
 }
 
-// Shared-memory layout of the one-launch solve (byte offsets), set on the host.
-struct SolveLayout {
-    int offBuf;  // three line buffers (right-hand side in, solution out), M * 33 values of 8 bytes each
-    int offW;    // the black line's two coupling coefficients, 32 M values of 8 bytes each
-    int offF;    // factors of the two red lines and the black line; the residual tile lies over them
-    int offC;    // factors of the coarsest row (FP64)
-    int tw;      // columns per residual tile
-};
-
 // black lines of a level with nz rows (at least one unit of work: nz = 3 has
 // a red line only)
 __device__ __forceinline__ int units_of(int nz) { return max((nz - 3) / 2, 1); }
@@ -415,10 +406,11 @@ constexpr int kUL = 4;  // unknowns per thread and batch of a level's right-hand
 // takes ~200 registers) is a little faster for a reactor's solve alone; two
 // (127 registers, no spills) lets the solves of a batch of reactors share
 // SMs, and the batch step runs ~28 % faster with it.
-template <typename Tv, int M, int MINB>
-__global__ void __launch_bounds__(kSolveThreads, MINB)
-    k_solve_persistent(const MGFast *__restrict__ mp, double *phi, int nr, int first_cycle, SolveLayout lay,
-                       double tol, int max_cycles, const StepCtl *sctl) {
+// One reactor's solve on nbk blocks (bid: this block's index among them).
+template <typename Tv, int M>
+__device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double *phi, int nr, int first_cycle,
+                                           const SolveLayout &lay, double tol, int max_cycles,
+                                           const StepCtl *sctl, const int bid, const int nbk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const MGFast &m = *mp;
     MGCtl *ctl = m.ctl;
@@ -431,10 +423,10 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
     constexpr int LFE = line_factor_elems(M);
     const unsigned FBv = (unsigned)(LFE * sizeof(Tv)), FBd = (unsigned)(LFE * sizeof(double));
     // levels whose work fits in G blocks are swept by the first G blocks only
-    const int G = min(kBarGroup, (int)gridDim.x);
+    const int G = min(kBarGroup, nbk);
     int lb = L;
     while (lb > 0 && units_of(m.nz[lb - 1]) <= G) --lb;
-    const bool in_group = (int)blockIdx.x < G;
+    const bool in_group = bid < G;
     __shared__ unsigned long long s_r[32], s_b[32];
     __shared__ double s_dot[4][32];
     // the mixed path accelerates its refinement by flexible GCR(1) (the
@@ -486,7 +478,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
     auto at = [](int j) { return (j % M) * kRow + j / M; };
     for (int cyc = 0;; ++cyc) {
         // ---- residual of phi + delta, its norms, and the restriction chain ----
-        if (blockIdx.x == 0 && L > 0) {
+        if (bid == 0 && L > 0) {
             ld_begin(qC, FBc);
             ld_copy(qC, FC, facc_v, FBc);
         }
@@ -537,7 +529,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                 // the direction is z less its projection on the previous
                 // one (in the A-image), the step length minimises |r|_2
                 double a[4] = {0.0, 0.0, 0.0, 0.0};  // r.w, w.w, w.wp, r.wp
-                for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+                for (int t = bid; t < ntile; t += nbk) {
                     const int j0 = t * tw;
                     for (int e = tid; e < sw * nz0; e += nt) {
                         const int c = e % sw - 1, i = e / sw, j = j0 + c;
@@ -588,9 +580,9 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                 if (tid < 4) {
                     double v = 0.0;
                     for (int q = 0; q < (nt >> 5); ++q) v += s_dot[tid][q];
-                    m.kpart[(size_t)blockIdx.x * 4 + tid] = v;
+                    m.kpart[(size_t)bid * 4 + tid] = v;
                 }
-                if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
+                if (!count_barrier(&ctl->bar_count.v, (++ngrid) * nbk, &ctl->timeout)) {
                     leave(false);
                     return;
                 }
@@ -598,7 +590,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                 // same step length everywhere
                 if (warp == 0) {
                     double v[4] = {0.0, 0.0, 0.0, 0.0};
-                    for (int b = lane; b < (int)gridDim.x; b += 32)
+                    for (int b = lane; b < nbk; b += 32)
 #pragma unroll
                         for (int d = 0; d < 4; ++d) v[d] += m.kpart[(size_t)b * 4 + d];
 #pragma unroll
@@ -613,7 +605,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                 const double alpha = den > 0.0 ? (s_dot[0][0] - beta * s_dot[3][0]) / den : 1.0;
                 kc = den > 0.0 ? den : 0.0;
                 __syncthreads();  // s_dot is rewritten by the next cycle
-                for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+                for (int t = bid; t < ntile; t += nbk) {
                     const int j0 = t * tw;
                     for (int e0 = tid; e0 < tw * (nz0 - 2); e0 += kU * nt) {
                         double pz[kU], qw[kU], zp[kU], wpv[kU], xv[kU], rv[kU];
@@ -656,7 +648,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                     chain(j0);
                 }
             } else
-            for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+            for (int t = bid; t < ntile; t += nbk) {
                 const int j0 = t * tw;
                 // batches of kU elements per thread: all loads first (stores to
                 // global memory would otherwise hold back the next loads)
@@ -753,7 +745,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                 }
             }
         }
-        if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
+        if (!count_barrier(&ctl->bar_count.v, (++ngrid) * nbk, &ctl->timeout)) {
             leave(false);
             return;
         }
@@ -769,7 +761,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
             else if (cyc >= max_cycles)
                 d = tol > 0.0 ? 2 : 1;
             s_decide = d;
-            if (blockIdx.x == 0) {
+            if (bid == 0) {
                 ctl->last_res = rn;
                 ctl->bnorm = bn;
                 ctl->cycles = cyc;
@@ -782,7 +774,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         const int decide = s_decide;
         first = 0;
         if (decide == 3) {
-            for (int k = blockIdx.x * nt + tid; k < ng; k += gridDim.x * nt) {
+            for (int k = bid * nt + tid; k < ng; k += nbk * nt) {
                 const int i = k / nr, j = k % nr;
                 if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] = 0.0;
             }
@@ -792,7 +784,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         if (decide != 0) {
             // the answer is the iterate the residual phase just stored
             if (dbuf && nxt != phi)
-                for (int k = blockIdx.x * nt + tid; k < ng; k += gridDim.x * nt) {
+                for (int k = bid * nt + tid; k < ng; k += nbk * nt) {
                     const int i = k / nr, j = k % nr;
                     if (i > 0 && i < nz0 - 1 && j < nr - 1) phi[k] = nxt[k];
                 }
@@ -806,7 +798,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         }
         if (L == 0) {
             // nz = 3: the single interior row of phi, exactly
-            if (blockIdx.x == 0) {
+            if (bid == 0) {
                 ld_begin(qC, FBd);
                 ld_copy(qC, FC64, m.facc, FBd);
                 const double *cz = m.cz[0], *cr = m.cr[0];
@@ -828,7 +820,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                 __syncthreads();
                 for (int j = tid; j < n; j += nt) phi[(size_t)nr + j] = BC[at(j)];
             }
-            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
+            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * nbk, &ctl->timeout)) {
                 leave(false);
                 return;
             }
@@ -837,7 +829,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         // level 0's sweeps rewrite delta: when they run in the group alone,
         // every block's update of phi has to be in first
         if (lb == 0)
-            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout)) {
+            if (!count_barrier(&ctl->bar_count.v, (++ngrid) * nbk, &ctl->timeout)) {
                 leave(false);
                 return;
             }
@@ -845,7 +837,7 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
         bool have = false;  // this block's first red factors of the level are requested
         for (int l = L - 1; l >= 0; --l) {
             const bool grp = l >= lb;
-            const int P = grp ? G : (int)gridDim.x;
+            const int P = grp ? G : nbk;
             const int nzl = m.nz[l], nzc = m.nz[l + 1];
             const int NB = (nzl - 3) / 2;  // black lines (>= 1: nzl >= 5 here)
             Tv *u = mixed ? (Tv *)m.u32[l] : (Tv *)m.u64[l];
@@ -854,8 +846,8 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
             const Tv *cz = mixed ? (const Tv *)m.cz32[l] : (const Tv *)m.cz[l];
             const Tv *fac = mixed ? (const Tv *)m.fac32[l] : (const Tv *)m.fac64[l];
             bool fail = false;
-            if ((int)blockIdx.x < P) {
-                if (l == L - 1 && blockIdx.x == 0) {
+            if (bid < P) {
+                if (l == L - 1 && bid == 0) {
                     // the coarsest row (FP64 factors, requested with the residual),
                     // then level L-1 in this block alone
                     for (int j = tid; j < NW; j += nt) Bf0[at(j)] = j < n ? (Tv)m.fc64[(size_t)nr + j] : (Tv)0;
@@ -871,10 +863,10 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                     __syncthreads();
                     have = false;
                 }
-                for (int q = blockIdx.x; q < NB; q += P) {
+                for (int q = bid; q < NB; q += P) {
                     const int ra = 2 * q + 1, rb = 2 * q + 3, ib = 2 * q + 2;
                     // factor requests: the reds (unless already in), then the black
-                    if (!(have && q == (int)blockIdx.x)) {
+                    if (!(have && q == bid)) {
                         ld_begin(qR, 2 * FBv);
                         ld_copy(qR, R0, fac + (size_t)(ra - 1) * LFE, FBv);
                         ld_copy(qR, R1, fac + (size_t)(rb - 1) * LFE, FBv);
@@ -954,11 +946,11 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
                 // request the next level's first red factors of this block
                 if (!fail && l > 0) {
                     const int ln = l - 1;
-                    const int Pn = ln >= lb ? G : (int)gridDim.x;
+                    const int Pn = ln >= lb ? G : nbk;
                     const int nbn = (m.nz[ln] - 3) / 2;
-                    if ((int)blockIdx.x < Pn && (int)blockIdx.x < nbn) {
+                    if (bid < Pn && bid < nbn) {
                         const Tv *facn = mixed ? (const Tv *)m.fac32[ln] : (const Tv *)m.fac64[ln];
-                        const int q = blockIdx.x;
+                        const int q = bid;
                         ld_begin(qR, 2 * FBv);
                         ld_copy(qR, R0, facn + (size_t)(2 * q) * LFE, FBv);
                         ld_copy(qR, R1, facn + (size_t)(2 * q + 2) * LFE, FBv);
@@ -976,13 +968,39 @@ __global__ void __launch_bounds__(kSolveThreads, MINB)
             if (l > 0 && grp && l - 1 >= lb)
                 ok = in_group ? count_barrier(&ctl->gbar_count.v, (++ngroup) * G, &ctl->timeout) : true;
             else
-                ok = count_barrier(&ctl->bar_count.v, (++ngrid) * gridDim.x, &ctl->timeout);
+                ok = count_barrier(&ctl->bar_count.v, (++ngrid) * nbk, &ctl->timeout);
             if (!ok) {
                 leave(false);
                 return;
             }
         }
     }
+}
+
+template <typename Tv, int M, int MINB>
+__global__ void __launch_bounds__(kSolveThreads, MINB)
+    k_solve_persistent(const MGFast *__restrict__ mp, double *phi, int nr, int first_cycle, SolveLayout lay,
+                       double tol, int max_cycles, const StepCtl *sctl) {
+    solve_body<Tv, M>(mp, phi, nr, first_cycle, lay, tol, max_cycles, sctl, blockIdx.x, gridDim.x);
+}
+
+// The solves of several reactors (one line chunk M, one precision) in one
+// cooperative launch: job k takes blocks [block0, block0 + nblocks) and its
+// barriers count its own blocks only, so the reactors proceed side by side.
+template <typename Tv, int M, int MINB>
+__global__ void __launch_bounds__(kSolveThreads, MINB) k_solve_multi(const SolveJob *__restrict__ jobs, int njobs) {
+    int lo = 0, hi = njobs - 1;  // the job whose block range holds this block
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block0 <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const SolveJob &j = jobs[lo];
+    const int bid = (int)blockIdx.x - j.block0;
+    if (bid >= j.nblocks) return;
+    solve_body<Tv, M>(j.mp, j.phi, j.nr, j.first_cycle, j.lay, j.tol, j.max_cycles, j.sctl, bid, j.nblocks);
 }
 
 }  // namespace
@@ -996,6 +1014,23 @@ namespace {
 template <typename Tv, int M>
 void *solve_fn(int minb) {
     return minb == 2 ? (void *)k_solve_persistent<Tv, M, 2> : (void *)k_solve_persistent<Tv, M, 1>;
+}
+
+template <typename Tv, int M>
+void *multi_fn(int minb) {
+    return minb == 2 ? (void *)k_solve_multi<Tv, M, 2> : (void *)k_solve_multi<Tv, M, 1>;
+}
+
+template <typename Tv>
+void *multi_kernel(int M, int minb) {
+    switch (M) {
+        case 1: return multi_fn<Tv, 1>(minb);
+        case 2: return multi_fn<Tv, 2>(minb);
+        case 4: return multi_fn<Tv, 4>(minb);
+        case 8: return multi_fn<Tv, 8>(minb);
+        case 16: return multi_fn<Tv, 16>(minb);
+        default: return multi_fn<Tv, 32>(minb);
+    }
 }
 
 template <typename Tv>
@@ -1022,6 +1057,8 @@ void raise_smem_limits() {
         for (int minb = 1; minb <= 2; ++minb) {
             cudaFuncSetAttribute(solve_kernel<float>(M, minb), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
             cudaFuncSetAttribute(solve_kernel<double>(M, minb), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+            cudaFuncSetAttribute(multi_kernel<float>(M, minb), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+            cudaFuncSetAttribute(multi_kernel<double>(M, minb), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         }
     }
     done = true;
@@ -1085,10 +1122,72 @@ void mg_fast_upload(MGFast &m, cudaStream_t st) {
     cudaStreamSynchronize(st);
 }
 
+// The launch shape of one reactor's one-launch solve (shared-memory layout,
+// blocks, kernel); false when it cannot be launched.
+bool solve_job(const FieldDims &fd, MGFast &m, double *phi, bool mixed, double tol, int max_cycles,
+               const StepCtl *sctl, bool wide, SolveJob &job) {
+    const int nz = fd.nz, nr = fd.nr, n = nr - 1;
+    const int M = line_chunk(n);
+    raise_smem_limits();
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    const size_t LFE = (size_t)line_factor_elems(M);
+    SolveLayout lay{};
+    // wide: residual tiles of 4 columns over two blocks per black line: the
+    // residual phase (FP64 stencil, restriction chain) runs on twice the SMs
+    // the line phases need; the remaining SMs stay free for the cell sort
+    // that runs beside the solve in a timestep (measured on c2: 0.551 ->
+    // 0.518 ms per solve; three blocks per line leave the sort too few SMs).
+    // Narrow (one block per black line, tiles of 8): many reactors solving
+    // side by side each take fewer SMs.
+    lay.tw = wide ? 4 : 8;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off += (b + 127) & ~(size_t)127;
+        return (int)o;
+    };
+    // line buffers and couplings; during the residual phase the same space
+    // holds phi + delta of a tile of columns with its two neighbours
+    const size_t bufw = (size_t)3 * M * kRow * sizeof(double) + (size_t)2 * kLine * M * sizeof(double);
+    const size_t stage = (size_t)(lay.tw + 2) * nz * sizeof(double);
+    lay.offBuf = take(std::max(bufw, stage) - (size_t)2 * kLine * M * sizeof(double));
+    lay.offW = take((size_t)2 * kLine * M * sizeof(double));
+    lay.offF = take(std::max((size_t)3 * LFE * es, (size_t)2 * lay.tw * nz * es));
+    lay.offC = take(LFE * sizeof(double));
+    const size_t sp = off;
+    // a wide solve (one reactor alone) takes the one-block-per-SM build; a
+    // narrow one (a reactor of a batch) the two-block build
+    const int minb = wide ? 1 : 2;
+    void *fn = mixed ? solve_kernel<float>(M, minb) : solve_kernel<double>(M, minb);
+    int per_sm = 0;
+    if (sp <= kSolveSmemLimit) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSolveThreads, sp);
+    if (per_sm < 1) return false;
+    const int grid = std::max(1, std::min(nsm * per_sm, std::min(nsm, (wide ? 2 : 1) * ((nz - 1) / 2))));
+    job.mp = m.self;
+    job.phi = phi;
+    job.nr = nr;
+    job.first_cycle = 1;
+    job.lay = lay;
+    job.tol = tol;
+    job.max_cycles = max_cycles;
+    job.sctl = sctl;
+    job.block0 = 0;
+    job.nblocks = grid;
+    job.M = M;
+    job.mixed = mixed ? 1 : 0;
+    job.minb = minb;
+    job.smem = sp;
+    job.fn = fn;
+    return true;
+}
+
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
-                  bool v_from_ctl, bool setup, cudaEvent_t at_solve, bool wide) {
+                  bool v_from_ctl, bool setup, cudaEvent_t at_solve, bool wide, SolveJob *defer) {
     const int nz = fd.nz, nr = fd.nr, n = nr - 1, ng = nz * nr;
     const int M = line_chunk(n);
     const int nlev = m.nlev;
@@ -1137,47 +1236,22 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
         cudaMemsetAsync(m.u64[0], 0, sizeof(double) * ng, st);
     cudaMemsetAsync(m.ctl, 0, sizeof(MGCtl), st);
     // all cycles in one cooperative launch
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const size_t es = mixed ? sizeof(float) : sizeof(double);
-    const size_t LFE = (size_t)line_factor_elems(M);
-    SolveLayout lay{};
-    // wide: residual tiles of 4 columns over two blocks per black line: the
-    // residual phase (FP64 stencil, restriction chain) runs on twice the SMs
-    // the line phases need; the remaining SMs stay free for the cell sort
-    // that runs beside the solve in a timestep (measured on c2: 0.551 ->
-    // 0.518 ms per solve; three blocks per line leave the sort too few SMs).
-    // Narrow (one block per black line, tiles of 8): many reactors solving
-    // side by side each take fewer SMs.
-    lay.tw = wide ? 4 : 8;
-    size_t off = 0;
-    auto take = [&](size_t b) {
-        const size_t o = off;
-        off += (b + 127) & ~(size_t)127;
-        return (int)o;
-    };
-    // line buffers and couplings; during the residual phase the same space
-    // holds phi + delta of a tile of columns with its two neighbours
-    const size_t bufw = (size_t)3 * M * kRow * sizeof(double) + (size_t)2 * kLine * M * sizeof(double);
-    const size_t stage = (size_t)(lay.tw + 2) * nz * sizeof(double);
-    lay.offBuf = take(std::max(bufw, stage) - (size_t)2 * kLine * M * sizeof(double));
-    lay.offW = take((size_t)2 * kLine * M * sizeof(double));
-    lay.offF = take(std::max((size_t)3 * LFE * es, (size_t)2 * lay.tw * nz * es));
-    lay.offC = take(LFE * sizeof(double));
-    const size_t sp = off;
-    // a wide solve (one reactor alone) takes the one-block-per-SM build; a
-    // narrow one (a reactor of a batch) the two-block build
-    const int minb = wide ? 1 : 2;
-    void *fn = mixed ? solve_kernel<float>(M, minb) : solve_kernel<double>(M, minb);
-    int per_sm = 0;
-    if (sp <= kSolveSmemLimit) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSolveThreads, sp);
-    if (per_sm < 1) {
+    SolveJob job;
+    if (!solve_job(fd, m, phi, mixed, tol, max_cycles, sctl, wide, job)) {
         if (at_solve) cudaEventRecord(at_solve, st);
         if (launches) *launches += L;
         return kSolveNoLaunch;
     }
-    const int grid = std::max(1, std::min(nsm * per_sm, std::min(nsm, (wide ? 2 : 1) * ((nz - 1) / 2))));
+    if (defer) {
+        // the caller launches it with other reactors' solves (mg_multi_launch)
+        *defer = job;
+        if (launches) *launches += L;
+        return 0;
+    }
+    const SolveLayout lay = job.lay;
+    const size_t sp = job.smem;
+    void *fn = job.fn;
+    const int grid = job.nblocks;
     int first_cycle = 1, nrv = nr, mc = max_cycles;
     double tv = tol;
     const StepCtl *sc = sctl;
@@ -1231,6 +1305,83 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     }
     if (rel_res) *rel_res = ch.bnorm > 0 ? ch.last_res / ch.bnorm : 0.0;
     return ch.converged ? ch.cycles : -ch.cycles - 1;
+}
+
+std::vector<std::pair<int, int>> mg_multi_plan(std::vector<SolveJob> &jobs) {
+    std::stable_sort(jobs.begin(), jobs.end(), [](const SolveJob &a, const SolveJob &b) {
+        return a.mixed != b.mixed ? a.mixed < b.mixed : a.M < b.M;
+    });
+    std::vector<std::pair<int, int>> out;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    for (size_t a = 0; a < jobs.size();) {
+        size_t b = a;
+        size_t smem = 0;
+        while (b < jobs.size() && jobs[b].mixed == jobs[a].mixed && jobs[b].M == jobs[a].M) {
+            smem = std::max(smem, jobs[b].smem);
+            ++b;
+        }
+        void *fn = jobs[a].mixed ? multi_kernel<float>(jobs[a].M, 2) : multi_kernel<double>(jobs[a].M, 2);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSolveThreads, smem);
+        const int cap = std::max(1, per_sm * nsm);
+        // launches of at most `cap` blocks and one block per job at least
+        while (a < b) {
+            size_t e = std::min(b, a + (size_t)cap);
+            int want = 0;
+            for (size_t k = a; k < e; ++k) want += jobs[k].nblocks;
+            const double scale = want > cap ? (double)cap / want : 1.0;
+            int used = 0;
+            for (size_t k = a; k < e; ++k) {
+                jobs[k].nblocks = std::max(1, (int)(jobs[k].nblocks * scale));
+                used += jobs[k].nblocks;
+            }
+            while (used > cap) {  // the one-block floors overshot: trim the largest
+                size_t big = a;
+                for (size_t k = a; k < e; ++k)
+                    if (jobs[k].nblocks > jobs[big].nblocks) big = k;
+                if (jobs[big].nblocks <= 1) break;
+                --jobs[big].nblocks;
+                --used;
+            }
+            used = 0;
+            for (size_t k = a; k < e; ++k) {
+                jobs[k].block0 = used;
+                jobs[k].fn = fn;
+                jobs[k].smem = smem;
+                used += jobs[k].nblocks;
+            }
+            out.push_back({(int)a, (int)e});
+            a = e;
+        }
+    }
+    return out;
+}
+
+int mg_multi_launch(const std::vector<SolveJob> &jobs, int j0, int j1, const SolveJob *jobs_dev,
+                    cudaStream_t st) {
+    if (j1 <= j0) return 0;
+    int blocks = 0;
+    for (int k = j0; k < j1; ++k) blocks = std::max(blocks, jobs[k].block0 + jobs[k].nblocks);
+    const SolveJob *tab = jobs_dev + j0;
+    int nj = j1 - j0;
+    void *args[] = {(void *)&tab, (void *)&nj};
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(blocks);
+    lc.blockDim = dim3(kSolveThreads);
+    lc.dynamicSmemBytes = jobs[j0].smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelExC(&lc, jobs[j0].fn, args) == cudaSuccess ? 0 : kSolveNoLaunch;
+}
+
+void mg_solve_done(MGFast &m, StepCtl *sctl, bool first_of_step, cudaStream_t st) {
+    k_solve_done<<<1, 1, 0, st>>>(m.ctl, sctl, first_of_step ? 0 : 1);
 }
 
 }  // namespace pic

@@ -62,6 +62,33 @@ struct MGFast {
     MGFast *self;  // device copy of this struct (kernels read it through a pointer)
 };
 
+// Shared-memory layout of the one-launch solve (byte offsets), set on the host.
+struct SolveLayout {
+    int offBuf;  // three line buffers (right-hand side in, solution out), M * 33 values of 8 bytes each
+    int offW;    // the black line's two coupling coefficients, 32 M values of 8 bytes each
+    int offF;    // factors of the two red lines and the black line; the residual tile lies over them
+    int offC;    // factors of the coarsest row (FP64)
+    int tw;      // columns per residual tile
+};
+
+// One reactor's one-launch solve, as the kernel takes it (a table of these
+// drives the solves of several reactors in one cooperative launch), with its
+// launch shape on the host.
+struct SolveJob {
+    const MGFast *mp;
+    double *phi;
+    int nr, first_cycle;
+    SolveLayout lay;
+    double tol;
+    int max_cycles;
+    const StepCtl *sctl;
+    int block0, nblocks;  // this job's blocks in the launch
+    // host side
+    int M, mixed, minb;
+    size_t smem;
+    void *fn;
+};
+
 // line-factor elements of one r-line of a mesh with nr nodes per row
 // (the same count in FP32 and FP64)
 size_t mg_line_factor_elems(int nr);
@@ -80,10 +107,29 @@ void mg_fast_geometry(const MGFast &m, int nr, double dr, std::vector<double> &o
 // before the one-launch solve, after the set-up: work that waits for it runs
 // beside the solve.  wide: two blocks per black line (a reactor alone on the
 // GPU); else one (many reactors solving side by side).
+// defer (narrow solves of a batch): the set-up is enqueued, the solve itself
+// is described in *defer and left to mg_multi_launch; its end (the report to
+// sctl) is then mg_solve_done's.
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
                   bool v_from_ctl = true, bool setup = true, cudaEvent_t at_solve = nullptr,
-                  bool wide = true);
+                  bool wide = true, SolveJob *defer = nullptr);
+
+// the launch shape of one reactor's solve (host only); false: not launchable
+bool solve_job(const FieldDims &fd, MGFast &m, double *phi, bool mixed, double tol, int max_cycles,
+               const StepCtl *sctl, bool wide, SolveJob &job);
+
+// Plan deferred solves for shared cooperative launches: jobs of one (precision,
+// line chunk) kind share a launch; each job's blocks are cut, in proportion,
+// so that the launch fits the GPU at once (at least one block per job).
+// Returns the launches as [first job, end job) ranges of `jobs`, which it
+// reorders by kind and fills with block0 / nblocks.  Host only.
+std::vector<std::pair<int, int>> mg_multi_plan(std::vector<SolveJob> &jobs);
+// launch the planned range [j0, j1) of the device copy of the table
+int mg_multi_launch(const std::vector<SolveJob> &jobs, int j0, int j1, const SolveJob *jobs_dev,
+                    cudaStream_t st);
+// a deferred solve's report to its step control (k_solve_done)
+void mg_solve_done(MGFast &m, StepCtl *sctl, bool first_of_step, cudaStream_t st);
 
 }  // namespace pic

@@ -145,7 +145,9 @@ struct pic_batch {
         cudaGraphExec_t exec = nullptr;
         std::vector<int64_t> launches;  // kernels per reactor in the graph
         bool failed = false;
+        pic::SolveJob *jobs_d = nullptr;  // the shared solve launches' job table (device)
     };
+    cudaEvent_t ev_fork2 = nullptr;
     std::map<std::vector<char>, Graph> graphs;
 };
 
@@ -816,7 +818,7 @@ void sort_finish(pic_handle *h, int par_e, int par_i, cudaStream_t st) {
         // in a batch: at most 8 blocks (a step's births are few; the numbering
         // is a cooperative launch, and a wide one waits for free SMs)
         launch_birth_ids(d.bkey[par], d.births[par].id, d.d_nbirths[par], d.d_nb0, h->sctl, s, h->rtmp, st,
-                         h->in_batch ? 8 : 1 << 30);
+                         h->in_batch ? 1 : 1 << 30);
     }
     k_sort_end<<<1, 1, 0, st>>>(h->sctl, h->sp[0].d_nalive, h->sp[0].d_ntotal, h->sp[1].d_nalive,
                                  h->sp[1].d_ntotal);
@@ -830,11 +832,20 @@ void sort_finish(pic_handle *h, int par_e, int par_i, cudaStream_t st) {
 // sort is left pending for the next step or the end of the call.  mv: the
 // pass moves the ions (always without subcycling); otherwise they stay in
 // their buffer set with their deposit, and newborn ions join their births.
+// part 0: the whole step; a batch whose reactors solve in shared launches
+// splits it: part 1 ends after the solve's set-up (its solve described in
+// *job), part 2 starts after the shared solve launch.
 template <typename T>
-void one_step(pic_handle *h, cudaStream_t sb, bool mv) {
+void one_step(pic_handle *h, cudaStream_t sb, bool mv, int part = 0, SolveJob *job = nullptr) {
     cudaStream_t st = h->st;
     const int src = h->cur, dst = 1 - h->cur;
     const int isrc = h->cur_i, idst = mv ? 1 - h->cur_i : h->cur_i;
+    if (part == 2) {
+        mg_solve_done(h->mgf, h->sctl, true, st);
+        launch_efield<T>(h->phi, h->Ez, h->Er, (typename V2<T>::type *)h->E2, h->nz, h->nr, h->dz,
+                         h->dr, h->sctl, st);
+        h->launches += 3;  // the shared solve's share, its report, E
+    } else {
     k_step_begin<<<1, 1, 0, st>>>(h->sctl, h->rf_d, h->cfg.rf.n, h->cfg.dt, h->cfg.split_every);
     h->launches += 1;
     if (!sb) {
@@ -867,7 +878,11 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv) {
         } else {
             mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi,
                           true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, true,
-                          true, fork, !h->in_batch);
+                          true, fork, !h->in_batch, part == 1 ? job : nullptr);
+            if (part == 1) {
+                h->launches += L;
+                return;
+            }
         }
         if (sb) {
             cudaStreamWaitEvent(sb, h->ev_fork, 0);
@@ -879,6 +894,7 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv) {
         h->launches += L + 2;
     }
     if (sb) cudaStreamWaitEvent(st, h->ev_join, 0);
+    }
     {
         PhaseTimer t(h, 3);
         sort_finish(h, src, isrc, st);
@@ -1068,36 +1084,90 @@ void enqueue_sort_tail(pic_handle *h, cudaStream_t on, bool check_only = false) 
 }
 
 // capture one step of every reactor of the batch as one fork-join graph
+// One batch step as one graph.  Reactors without an external circuit share
+// their field solves: each branch runs its step up to the solve's set-up, the
+// branches join, the solves of all of them run in a few cooperative launches
+// (one per precision and line chunk; every reactor's blocks synchronise among
+// themselves only), and the branches fork again for the rest of the step.
+// Reactors with a circuit (two solves per step) run their whole step in one
+// branch.  Without the shared launches (they cannot be planned), every
+// reactor's step runs in its own branch.
 void capture_batch(pic_batch *b, pic_batch::Graph &g) {
     const size_t nh = b->hs.size();
     g.launches.assign(nh, 0);
+    std::vector<SolveJob> jobs;
+    std::vector<char> shared(nh, 0);
+    for (size_t k = 0; k < nh; ++k) {
+        pic_handle *h = b->hs[k];
+        if (h->cfg.circuit_C > 0.0) continue;
+        FieldDims fd{h->nz, h->nr, h->dz, h->dr, h->cfg.mesh.L, h->cfg.chi_face};
+        SolveJob j;
+        if (!solve_job(fd, h->mgf, h->phi, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, h->sctl, false, j))
+            continue;
+        jobs.push_back(j);
+        shared[k] = 1;
+    }
+    std::vector<std::pair<int, int>> plan;
+    if (!jobs.empty()) {
+        plan = mg_multi_plan(jobs);
+        if (!g.jobs_d && cudaMalloc(&g.jobs_d, jobs.size() * sizeof(SolveJob)) != cudaSuccess) g.jobs_d = nullptr;
+        if (!g.jobs_d ||
+            cudaMemcpy(g.jobs_d, jobs.data(), jobs.size() * sizeof(SolveJob), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            std::fill(shared.begin(), shared.end(), 0);
+            plan.clear();
+        }
+    }
+    if (!b->ev_fork2) cudaEventCreateWithFlags(&b->ev_fork2, cudaEventDisableTiming);
+    // one part of reactor k's step, on its branch
+    auto run = [&](size_t k, int part) {
+        pic_handle *h = b->hs[k];
+        const int64_t L0 = h->launches, P0 = h->particle_launches;
+        cudaStream_t keep = h->st;
+        h->st = h->gst;
+        h->in_batch = true;
+        SolveJob unused;
+        if (h->mixed)
+            one_step<float>(h, nullptr, true, part, &unused);
+        else
+            one_step<double>(h, nullptr, true, part, &unused);
+        h->in_batch = false;
+        h->st = keep;
+        g.launches[k] += h->launches - L0;
+        h->launches = L0;
+        h->particle_launches = P0;
+    };
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
+        std::vector<int> cur(nh), cur_i(nh);
+        for (size_t k = 0; k < nh; ++k) {
+            cur[k] = b->hs[k]->cur;
+            cur_i[k] = b->hs[k]->cur_i;
+        }
         cudaEventRecord(b->ev_fork, b->origin);
         for (size_t k = 0; k < nh; ++k) {
-            pic_handle *h = b->hs[k];
-            const int cur = h->cur, cur_i = h->cur_i;
-            const int64_t L0 = h->launches, P0 = h->particle_launches;
-            cudaStreamWaitEvent(h->gst, b->ev_fork, 0);
-            cudaStream_t keep = h->st;
-            h->st = h->gst;
+            cudaStreamWaitEvent(b->hs[k]->gst, b->ev_fork, 0);
             // the reactors' branches run side by side; inside a branch the
             // step stays in order (its own second branch adds nodes, not speed)
-            h->in_batch = true;
-            if (h->mixed)
-                one_step<float>(h, nullptr, true);
-            else
-                one_step<double>(h, nullptr, true);
-            h->in_batch = false;
-            h->st = keep;
-            h->cur = cur;  // the replays flip them
-            h->cur_i = cur_i;
-            g.launches[k] = h->launches - L0;
-            h->launches = L0;
-            h->particle_launches = P0;
-            cudaEventRecord(b->ev_join[k], h->gst);
+            run(k, shared[k] ? 1 : 0);
+            cudaEventRecord(b->ev_join[k], b->hs[k]->gst);
             cudaStreamWaitEvent(b->origin, b->ev_join[k], 0);
+        }
+        if (!plan.empty()) {
+            for (const auto &r : plan) mg_multi_launch(jobs, r.first, r.second, g.jobs_d, b->origin);
+            cudaEventRecord(b->ev_fork2, b->origin);
+            for (size_t k = 0; k < nh; ++k) {
+                if (!shared[k]) continue;
+                cudaStreamWaitEvent(b->hs[k]->gst, b->ev_fork2, 0);
+                run(k, 2);
+                cudaEventRecord(b->ev_join[k], b->hs[k]->gst);
+                cudaStreamWaitEvent(b->origin, b->ev_join[k], 0);
+            }
+        }
+        for (size_t k = 0; k < nh; ++k) {  // the replays flip them
+            b->hs[k]->cur = cur[k];
+            b->hs[k]->cur_i = cur_i[k];
         }
         e = cudaStreamEndCapture(b->origin, &graph);
     }
@@ -1681,8 +1751,11 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps, pic_status *statuses) {
 void pic_batch_destroy(pic_batch *b) {
     if (!b) return;
     if (b->origin) cudaStreamSynchronize(b->origin);
-    for (auto &kv : b->graphs)
+    for (auto &kv : b->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.jobs_d) cudaFree(kv.second.jobs_d);
+    }
+    if (b->ev_fork2) cudaEventDestroy(b->ev_fork2);
     for (cudaEvent_t e : b->ev_join)
         if (e) cudaEventDestroy(e);
     if (b->ev_in) cudaEventDestroy(b->ev_in);

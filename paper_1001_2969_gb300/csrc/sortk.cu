@@ -463,7 +463,10 @@ void launch_birth_ids(const uint64_t *key, uint64_t *id, const int32_t *nb, cons
     // (max_grid: a reactor of a batch, whose numbering must not wait for
     // many co-resident blocks while the other reactors' kernels hold SMs)
     const int g = std::max(1, std::min(std::min(grid, max_grid), (tmp.max_n + kRadixTile - 1) / kRadixTile));
-    cudaLaunchCooperativeKernel((void *)k_birth_ids, g, kRadixThreads, args, 0, st);
+    if (g == 1)  // one block: its barriers wait for itself alone, no co-residency to ask for
+        k_birth_ids<<<1, kRadixThreads, 0, st>>>(key, id, nb, nb0, ctl, s, tmp);
+    else
+        cudaLaunchCooperativeKernel((void *)k_birth_ids, g, kRadixThreads, args, 0, st);
 }
 
 template void launch_hist<float>(PBuf<float>, const int32_t *, int32_t *, cudaStream_t);
