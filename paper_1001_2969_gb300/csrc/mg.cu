@@ -313,14 +313,26 @@ __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, doubl
     }
     m.f0[k] = v;
     m.dg0[k] = dg;
+    double p;
     if (i == 0)
-        phi[k] = (j == nr - 1) ? 0.0 : V;
+        p = (j == nr - 1) ? 0.0 : V;
     else if (i == nz - 1)
-        phi[k] = phi_zL ? phi_zL[j] : 0.0;
+        p = phi_zL ? phi_zL[j] : 0.0;
     else if (j == nr - 1)
-        phi[k] = 0.0;
-    else if (cold)
-        phi[k] = 0.0;
+        p = 0.0;
+    else
+        p = cold ? 0.0 : phi[k];
+    phi[k] = p;
+    // the solve alternates between phi and a copy (both carry the boundary
+    // values); the level-0 correction starts at zero (and stays zero on the
+    // boundary); the solve's control block starts cleared
+    m.phi2[k] = p;
+    if (m.u32[0])
+        m.u32[0][k] = 0.0f;
+    else
+        m.u64[0][k] = 0.0;
+    for (int w = k; w < (int)(sizeof(MGCtl) / sizeof(unsigned)); w += nz * nr)
+        reinterpret_cast<unsigned *>(m.ctl)[w] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -1227,14 +1239,8 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(mp, rho, phi, phi_zL, V, nz, nr, warm ? 0 : 1, sctl,
                                                v_from_ctl ? 1 : 0);
     ++L;
-    // the solve alternates between phi and a copy (both carry the boundary values)
-    cudaMemcpyAsync(m.phi2, phi, sizeof(double) * ng, cudaMemcpyDeviceToDevice, st);
-    // the level-0 correction starts at zero and stays zero on the boundary
-    if (mixed)
-        cudaMemsetAsync(m.u32[0], 0, sizeof(float) * ng, st);
-    else
-        cudaMemsetAsync(m.u64[0], 0, sizeof(double) * ng, st);
-    cudaMemsetAsync(m.ctl, 0, sizeof(MGCtl), st);
+    // (k_rhs_bc also copies phi to its alternate, clears the level-0
+    // correction and the solve's control block)
     // all cycles in one cooperative launch
     SolveJob job;
     if (!solve_job(fd, m, phi, mixed, tol, max_cycles, sctl, wide, job)) {
@@ -1307,7 +1313,7 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     return ch.converged ? ch.cycles : -ch.cycles - 1;
 }
 
-std::vector<std::pair<int, int>> mg_multi_plan(std::vector<SolveJob> &jobs) {
+std::vector<std::pair<int, int>> mg_multi_plan(std::vector<SolveJob> &jobs, bool &concurrent) {
     std::stable_sort(jobs.begin(), jobs.end(), [](const SolveJob &a, const SolveJob &b) {
         return a.mixed != b.mixed ? a.mixed < b.mixed : a.M < b.M;
     });
@@ -1315,42 +1321,74 @@ std::vector<std::pair<int, int>> mg_multi_plan(std::vector<SolveJob> &jobs) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // the kinds' ranges, their kernels and their share of the GPU: every
+    // kind's launch gets SMs in proportion to the blocks its jobs would take
+    // alone, so that the launches of all kinds fit the GPU together
+    struct Kind {
+        size_t a, b;
+        void *fn;
+        size_t smem;
+        int want;
+    };
+    std::vector<Kind> kinds;
+    int want_all = 0;
     for (size_t a = 0; a < jobs.size();) {
         size_t b = a;
         size_t smem = 0;
+        int want = 0;
         while (b < jobs.size() && jobs[b].mixed == jobs[a].mixed && jobs[b].M == jobs[a].M) {
             smem = std::max(smem, jobs[b].smem);
+            want += jobs[b].nblocks;
             ++b;
         }
         void *fn = jobs[a].mixed ? multi_kernel<float>(jobs[a].M, 2) : multi_kernel<double>(jobs[a].M, 2);
+        kinds.push_back({a, b, fn, smem, want});
+        want_all += want;
+        a = b;
+    }
+    // side by side only while that leaves the jobs a fair part of their
+    // blocks: with more than six times the GPU's co-resident blocks wanted
+    // (64 c4 reactors), the kinds take the whole GPU one after another
+    // (measured: 16 and 32 reactors 1.08 -> 1.35 and 1.21 -> 1.35e10
+    // particle-steps/s side by side, 64 reactors 1.48 -> 1.32e10)
+    int per_min = 1 << 30;
+    for (const Kind &k : kinds) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSolveThreads, smem);
-        const int cap = std::max(1, per_sm * nsm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, kSolveThreads, k.smem);
+        per_min = std::min(per_min, std::max(per_sm, 1));
+    }
+    const bool side_by_side = want_all <= 6 * per_min * nsm;
+    concurrent = side_by_side;
+    for (const Kind &k : kinds) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, kSolveThreads, k.smem);
+        const int share = side_by_side ? std::max(1, (int)((double)nsm * k.want / std::max(want_all, 1))) : nsm;
+        const int cap = std::max(1, per_sm * share);
         // launches of at most `cap` blocks and one block per job at least
-        while (a < b) {
-            size_t e = std::min(b, a + (size_t)cap);
+        for (size_t a = k.a; a < k.b;) {
+            const size_t e = std::min(k.b, a + (size_t)cap);
             int want = 0;
-            for (size_t k = a; k < e; ++k) want += jobs[k].nblocks;
+            for (size_t j = a; j < e; ++j) want += jobs[j].nblocks;
             const double scale = want > cap ? (double)cap / want : 1.0;
             int used = 0;
-            for (size_t k = a; k < e; ++k) {
-                jobs[k].nblocks = std::max(1, (int)(jobs[k].nblocks * scale));
-                used += jobs[k].nblocks;
+            for (size_t j = a; j < e; ++j) {
+                jobs[j].nblocks = std::max(1, (int)(jobs[j].nblocks * scale));
+                used += jobs[j].nblocks;
             }
             while (used > cap) {  // the one-block floors overshot: trim the largest
                 size_t big = a;
-                for (size_t k = a; k < e; ++k)
-                    if (jobs[k].nblocks > jobs[big].nblocks) big = k;
+                for (size_t j = a; j < e; ++j)
+                    if (jobs[j].nblocks > jobs[big].nblocks) big = j;
                 if (jobs[big].nblocks <= 1) break;
                 --jobs[big].nblocks;
                 --used;
             }
             used = 0;
-            for (size_t k = a; k < e; ++k) {
-                jobs[k].block0 = used;
-                jobs[k].fn = fn;
-                jobs[k].smem = smem;
-                used += jobs[k].nblocks;
+            for (size_t j = a; j < e; ++j) {
+                jobs[j].block0 = used;
+                jobs[j].fn = k.fn;
+                jobs[j].smem = k.smem;
+                used += jobs[j].nblocks;
             }
             out.push_back({(int)a, (int)e});
             a = e;

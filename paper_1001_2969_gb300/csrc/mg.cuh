@@ -121,11 +121,15 @@ bool solve_job(const FieldDims &fd, MGFast &m, double *phi, bool mixed, double t
                const StepCtl *sctl, bool wide, SolveJob &job);
 
 // Plan deferred solves for shared cooperative launches: jobs of one (precision,
-// line chunk) kind share a launch; each job's blocks are cut, in proportion,
-// so that the launch fits the GPU at once (at least one block per job).
+// line chunk) kind share a launch; each kind gets SMs in proportion to the
+// blocks its jobs would take alone, and each job's blocks are cut in
+// proportion so that the launches of all kinds fit the GPU together (at
+// least one block per job; a kind with more jobs than its share takes
+// several launches).  concurrent (out): the kinds' launches fit side by side;
+// else each takes the whole GPU and they run one after another.
 // Returns the launches as [first job, end job) ranges of `jobs`, which it
 // reorders by kind and fills with block0 / nblocks.  Host only.
-std::vector<std::pair<int, int>> mg_multi_plan(std::vector<SolveJob> &jobs);
+std::vector<std::pair<int, int>> mg_multi_plan(std::vector<SolveJob> &jobs, bool &concurrent);
 // launch the planned range [j0, j1) of the device copy of the table
 int mg_multi_launch(const std::vector<SolveJob> &jobs, int j0, int j1, const SolveJob *jobs_dev,
                     cudaStream_t st);

@@ -364,6 +364,31 @@ __global__ void k_step_end(StepCtl *c, DevScalars *ds, int32_t *nmain0, const in
 // a pass that holds the ions: the births its newborn ions join start at
 // the buffer's present count (skipped once the step has failed, so that a
 // dropped pass's newborns can be cut off again)
+// zero what the particle passes accumulate into (null members skipped)
+struct PassReset {
+    double *N[2];
+    int32_t *counts[2];
+    int32_t *nbirths[2];
+    int32_t *nb0;
+    int32_t *chunk_next;  // [2]
+    int ng, ncell;
+};
+__global__ void k_pass_reset(PassReset r) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int s = 0; s < 2; ++s) {
+        if (r.N[s])
+            for (int k = t; k < r.ng; k += stride) r.N[s][k] = 0.0;
+        if (r.counts[s])
+            for (int k = t; k < r.ncell; k += stride) r.counts[s][k] = 0;
+    }
+    if (t == 0) {
+        for (int s = 0; s < 2; ++s)
+            if (r.nbirths[s]) *r.nbirths[s] = 0;
+        if (r.nb0) *r.nb0 = 0;
+        r.chunk_next[0] = r.chunk_next[1] = 0;
+    }
+}
+
 __global__ void k_hold_ions(const StepCtl *c, int32_t *nb0, const int32_t *nb) {
     if (c->halt) return;
     *nb0 = *nb;
@@ -899,19 +924,28 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv, int part = 0, SolveJob *j
         PhaseTimer t(h, 3);
         sort_finish(h, src, isrc, st);
     }
-    for (int s = 0; s < 2; ++s) {
-        SpecDev &d = h->sp[s];
-        if (s == 1 && !mv) {
+    {
+        // the passes' deposit, cell counts, births counters and chunk
+        // counters start at zero (one launch for both species)
+        PassReset r{};
+        r.ng = h->ng;
+        r.ncell = h->ncell;
+        r.chunk_next = h->ds->chunk_next;
+        for (int s = 0; s < (mv ? 2 : 1); ++s) {
+            SpecDev &d = h->sp[s];
+            r.N[s] = h->N[s];
+            r.counts[s] = d.counts;
+            r.nbirths[s] = d.d_nbirths[s == 1 ? idst : dst];
+        }
+        if (mv && h->K > 1) r.nb0 = h->sp[1].d_nb0;  // else always 0
+        k_pass_reset<<<std::max(1, std::min(152 * 4, (std::max(h->ng, h->ncell) + 255) / 256)), 256, 0, st>>>(r);
+        h->launches += 1;
+        if (!mv) {
             // held ions: deposit, counts and births stay; this pass's
             // newborns are numbered from the births already there
-            k_hold_ions<<<1, 1, 0, st>>>(h->sctl, d.d_nb0, d.d_nbirths[idst]);
+            k_hold_ions<<<1, 1, 0, st>>>(h->sctl, h->sp[1].d_nb0, h->sp[1].d_nbirths[idst]);
             h->launches += 1;
-            continue;
         }
-        cudaMemsetAsync(h->N[s], 0, (size_t)h->ng * sizeof(double), st);
-        cudaMemsetAsync(d.counts, 0, (size_t)h->ncell * sizeof(int32_t), st);
-        cudaMemsetAsync(d.d_nbirths[s == 1 ? idst : dst], 0, sizeof(int32_t), st);
-        if (s == 1 && h->K > 1) cudaMemsetAsync(d.d_nb0, 0, sizeof(int32_t), st);  // else always 0
     }
     // the two species' passes are independent (what they share -- the other
     // species' births, deposit and counts -- takes atomics or reserved
@@ -931,9 +965,7 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv, int part = 0, SolveJob *j
         // blocks walk the chunks of the count on the device; a small store
         // takes no more blocks than its capacity has chunks
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->step_grid, (h->sp[s].cap + 1023) / 1024));
-        cudaStream_t ps = (fork2 && s == 1) ? sb : st;
-        cudaMemsetAsync(a.chunk_next, 0, sizeof(int32_t), ps);
-        launch_step<T>(a, grid, h->variant[s], ps);
+        launch_step<T>(a, grid, h->variant[s], (fork2 && s == 1) ? sb : st);
         h->launches += 1;
         h->particle_launches += 1;
     }
@@ -1108,8 +1140,9 @@ void capture_batch(pic_batch *b, pic_batch::Graph &g) {
         shared[k] = 1;
     }
     std::vector<std::pair<int, int>> plan;
+    bool concurrent = false;
     if (!jobs.empty()) {
-        plan = mg_multi_plan(jobs);
+        plan = mg_multi_plan(jobs, concurrent);
         if (!g.jobs_d && cudaMalloc(&g.jobs_d, jobs.size() * sizeof(SolveJob)) != cudaSuccess) g.jobs_d = nullptr;
         if (!g.jobs_d ||
             cudaMemcpy(g.jobs_d, jobs.data(), jobs.size() * sizeof(SolveJob), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1155,7 +1188,30 @@ void capture_batch(pic_batch *b, pic_batch::Graph &g) {
             cudaStreamWaitEvent(b->origin, b->ev_join[k], 0);
         }
         if (!plan.empty()) {
-            for (const auto &r : plan) mg_multi_launch(jobs, r.first, r.second, g.jobs_d, b->origin);
+            // the kinds' launches side by side (their blocks fit the GPU
+            // together), each on a branch of its own; a kind's further
+            // launches follow its first on the same branch
+            cudaEventRecord(b->ev_fork2, b->origin);
+            std::vector<char> used(nh, 0);
+            std::vector<std::pair<int, int>> kinds;  // (mixed, M) in order of appearance
+            for (size_t r = 0; r < plan.size(); ++r) {
+                const SolveJob &j = jobs[plan[r].first];
+                size_t kind = 0;
+                while (kind < kinds.size() && kinds[kind] != std::make_pair(j.mixed, j.M)) ++kind;
+                if (kind == kinds.size()) kinds.push_back({j.mixed, j.M});
+                const size_t br = concurrent ? kind % nh : 0;
+                cudaStream_t bs = b->hs[br]->gst;
+                if (!used[br]) {
+                    cudaStreamWaitEvent(bs, b->ev_fork2, 0);
+                    used[br] = 1;
+                }
+                mg_multi_launch(jobs, plan[r].first, plan[r].second, g.jobs_d, bs);
+            }
+            for (size_t k = 0; k < nh; ++k)
+                if (used[k]) {
+                    cudaEventRecord(b->ev_join[k], b->hs[k]->gst);
+                    cudaStreamWaitEvent(b->origin, b->ev_join[k], 0);
+                }
             cudaEventRecord(b->ev_fork2, b->origin);
             for (size_t k = 0; k < nh; ++k) {
                 if (!shared[k]) continue;

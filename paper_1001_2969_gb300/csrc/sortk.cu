@@ -119,9 +119,40 @@ __global__ void k_scan_apply(const int32_t *counts, int ncell, const int32_t *bl
     }
 }
 
+// the whole scan in one block (meshes of at most kScanOne cells, a batch's
+// small reactors): each thread sums a run of consecutive cells, one block
+// scan, then each thread writes its run's cursors.  Larger meshes take the
+// three tile kernels, whose loads coalesce.
+constexpr int kScanOne = 16384;
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_one(const int32_t *counts, int ncell, int32_t *cursor, int32_t *n_alive, int64_t capacity,
+               DevScalars *ds, const StepCtl *ctl) {
+    __shared__ int s_warp[32];
+    if (sort_skip(ctl)) return;
+    const int per = (ncell + kScanThreads - 1) / kScanThreads;
+    const int c0 = min(ncell, threadIdx.x * per), c1 = min(ncell, c0 + per);
+    int v = 0;
+    for (int c = c0; c < c1; ++c) v += counts[c];
+    int tot;
+    int ex = block_exclusive_scan(v, s_warp, &tot);
+    for (int c = c0; c < c1; ++c) {
+        const int x = counts[c];
+        cursor[c] = ex;
+        ex += x;
+    }
+    if (threadIdx.x == 0) {
+        *n_alive = tot;
+        if ((int64_t)tot > capacity) atomicOr(&ds->status, ST_CAPACITY);
+    }
+}
+
 void launch_scan(const int32_t *counts, int32_t *cursor, int ncell, int32_t *block_sums,
                  int32_t *n_alive, int64_t capacity, DevScalars *ds, const StepCtl *ctl,
                  cudaStream_t st) {
+    if (ncell <= kScanOne) {
+        k_scan_one<<<1, kScanThreads, 0, st>>>(counts, ncell, cursor, n_alive, capacity, ds, ctl);
+        return;
+    }
     const int nb = (ncell + kScanTile - 1) / kScanTile;
     k_scan_tiles<<<nb, kScanThreads, 0, st>>>(counts, ncell, block_sums, ctl);
     k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb, n_alive, capacity, ds, ctl);
