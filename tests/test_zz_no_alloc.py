@@ -5,12 +5,14 @@ when they solve (a host that fixed the library's memory budget at start-up,
 a real-time loop that must not stall on an allocation): it must give the
 same potential as pic_field_solve, call after call, while using only its
 fixed workspace -- the device's free memory does not change across a call.
+On one mesh the reference is also checked against the FP64 oracle's solve.
 This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import Oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -48,6 +50,14 @@ def test_noalloc_solve_matches_handle_solve_on_two_calls_in_a_row(env, mesh):
         pic.pic_set_boundary(h, zL)
         ref, cyc_ref, _, st_ref = pic.pic_field_solve(h, rho, chi, V)
         assert st_ref == pic.PIC_OK
+        if mesh == (65, 257):
+            # the handle's solve is the oracle's: the same V(0,1) iterates
+            o = Oracle(dict(cfg, phi_zL=zL))
+            o.set_grid("chi", chi)
+            o.set_grid("rho", rho)
+            o.set_grid("phi", np.zeros((nz, nr)))
+            assert o.solve(V, tol=1e-12, max_cycles=60)[0] == 0
+            assert _nerr(ref, o.grid("phi")) < 1e-12
         dev = dict(rho=torch.tensor(rho, dtype=torch.float64, device="cuda"),
                    chi=torch.tensor(chi, dtype=torch.float64, device="cuda"),
                    phi=torch.full((nz, nr), float("nan"), dtype=torch.float64, device="cuda"),
