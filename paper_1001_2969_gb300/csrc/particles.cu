@@ -381,29 +381,43 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     const int n = *a.n_alive;
     const int nmain = *a.n_main_src;
     const int nchunks = (n + kChunk - 1) / kChunk;
-    // chunks are claimed one at a time from a counter, the next one while
-    // the current one is worked on: blocks that meet costly chunks (many
-    // collisions) take fewer, and the pass ends within one chunk's time
-    __shared__ int s_claim;
-    if (tid == 0) s_claim = atomicAdd(a.chunk_next, 1);
+    // work is claimed from a counter, the next claim made while the current
+    // one is worked on: blocks that meet costly chunks (many collisions)
+    // take fewer.  The prefetching shapes claim chunks of kChunk particles;
+    // the direct-load shapes claim slots of kThreads particles, kPPT at a
+    // time until the last 2 x (blocks x kPPT) slots, then one at a time, so
+    // the pass ends within about one slot's time
+    const int nunits = PF ? nchunks : (n + kThreads - 1) / kThreads;
+    const int tail = PF ? nunits : nunits - 2 * (int)gridDim.x * kPPT;
+    __shared__ int s_claim, s_want;
+    if (tid == 0) {
+        const int w = PF ? 1 : (tail > 0 ? kPPT : 1);
+        s_claim = atomicAdd(a.chunk_next, w);
+        s_want = w;
+    }
     __syncthreads();
-    int ck = s_claim;
+    int cl = s_claim, cw = s_want;
     // this thread's perm entries of its next chunk, read a chunk ahead
     int pn[kPPT];
     if (PF) {
 #pragma unroll
         for (int m = 0; m < kPPT; ++m) {
-            const int k = ck * kChunk + m * kThreads + tid;
+            const int k = cl * kChunk + m * kThreads + tid;
             pn[m] = k < n ? a.perm[k] : 0;
         }
     }
-    while (ck < nchunks) {
-        const int base = ck * kChunk;
-        const int end = min(base + kChunk, n);
+    while (cl < nunits) {
+        const int base = PF ? cl * kChunk : cl * kThreads;
+        const int nslot = PF ? kPPT : min(cw, nunits - cl);
+        const int end = min(base + nslot * kThreads, n);
         __syncthreads();  // every thread has read s_claim
-        if (tid == 0) s_claim = atomicAdd(a.chunk_next, 1);
+        if (tid == 0) {
+            const int w = PF ? 1 : (cl + cw >= tail ? 1 : kPPT);
+            s_claim = atomicAdd(a.chunk_next, w);
+            s_want = w;
+        }
         __syncthreads();
-        const int ck_next = s_claim;
+        const int ck_next = s_claim, cw_next = s_want;
         // request the chunk's particles, then read the next chunk's perm
         // entries; a thread fills and reads only its own slots, so chunks
         // need no barrier
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
         // each thread reads back only the slots it requested itself
         if (PF) asm volatile("cp.async.wait_group 0;" ::: "memory");
 #pragma unroll 1
-        for (int m = 0; m < kPPT; ++m) {
+        for (int m = 0; m < nslot; ++m) {
             const int k = base + m * kThreads + tid;
             int out_cell = -1;
             T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
@@ -609,7 +623,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
                 atomicAdd(g + a.nr + 1, (double)c11);
             }
         }
-        ck = ck_next;
+        cl = ck_next;
+        cw = cw_next;
     }
     __syncthreads();
     for (int k = tid; k < PIC_NCOUNT; k += blockDim.x)
