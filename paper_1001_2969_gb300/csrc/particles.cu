@@ -343,24 +343,24 @@ constexpr int kThreads = 256;
 // shared-memory atomics of a warp are serialised
 constexpr int kEedfCopies = 8;
 
-// The fused particle pass (Sec. 2.1 merged cycle).  Each block works on
-// chunks of kChunk particles of the cell-sorted input, claimed from a counter.  Lanes of a warp hold
+// The fused particle pass (Sec. 2.1 merged cycle).  Each warp works on
+// units of 32 kPPT particles of the cell-sorted input, claimed from a counter.  Lanes of a warp hold
 // consecutive particles, so their output cells come in runs; each run's
 // deposit is summed across its lanes and its first lane adds it to the four
 // nodes with global reductions (fire-and-forget, resolved in L2).  A
 // shared-memory window of the chunk's nodes needs atomics that conflict
 // between runs and warps and costs more instructions than it saves.
-// PF: the chunk's particles come into shared memory by cp.async a chunk at
+// PF: the unit's particles come into shared memory by cp.async a unit at
 // a time, ahead of their use (for latency-bound passes)
-// PPT: particles per thread in a chunk (kThreads * PPT particles)
+// PPT: particles per thread in a unit (32 * PPT particles per warp)
 // XYZ: the global X-Y-Z pusher (a_theta carried; a.xyz set)
 template <typename T, bool PF, int kPPT, bool XYZ>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepArgs<T> a) {
-    constexpr int kChunk = kThreads * kPPT;
+    constexpr int kChunk = kThreads * kPPT;  // the block's staging slots
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using V = typename V4<T>::type;
-    // the chunk's particles, fetched into shared memory ahead of their use
-    // (PF): [kPPT][kThreads] of q0, q1, id, cell
+    // the warps' current units' particles, fetched into shared memory ahead
+    // of their use (PF): [kPPT][kThreads] of q0, q1, id, cell
     V *st_q0 = reinterpret_cast<V *>(smem_raw);
     V *st_q1 = st_q0 + kChunk;
     uint64_t *st_id = reinterpret_cast<uint64_t *>(st_q1 + kChunk);
@@ -380,251 +380,299 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_step(StepA
     __syncthreads();  // tallies and EEDF cleared before any thread adds to them
     const int n = *a.n_alive;
     const int nmain = *a.n_main_src;
-    const int nchunks = (n + kChunk - 1) / kChunk;
-    // work is claimed from a counter, the next claim made while the current
-    // one is worked on: blocks that meet costly chunks (many collisions)
-    // take fewer.  The prefetching shapes claim chunks of kChunk particles;
-    // the direct-load shapes claim slots of kThreads particles, kPPT at a
-    // time until the last 2 x (blocks x kPPT) slots, then one at a time, so
-    // the pass ends within about one slot's time
-    const int nunits = PF ? nchunks : (n + kThreads - 1) / kThreads;
-    const int tail = PF ? nunits : nunits - 2 * (int)gridDim.x * kPPT;
-    __shared__ int s_claim, s_want;
-    if (tid == 0) {
-        const int w = PF ? 1 : (tail > 0 ? kPPT : 1);
-        s_claim = atomicAdd(a.chunk_next, w);
-        s_want = w;
-    }
-    __syncthreads();
-    int cl = s_claim, cw = s_want;
-    // this thread's perm entries of its next chunk, read a chunk ahead
-    int pn[kPPT];
-    if (PF) {
-#pragma unroll
-        for (int m = 0; m < kPPT; ++m) {
-            const int k = cl * kChunk + m * kThreads + tid;
-            pn[m] = k < n ? a.perm[k] : 0;
+    // the prefetching shapes' copy of a particle (source index pidx) into
+    // the staging slot, by cp.async
+    auto fetch = [&](int pidx, int slot) {
+        const bool from_main = pidx < nmain;
+        const PBuf<T> &src = from_main ? a.src_main : a.src_births;
+        const int si = from_main ? pidx : pidx - nmain;
+        for (int h = 0; h < (int)(sizeof(V) / 16); ++h) {
+            cpa16(reinterpret_cast<char *>(st_q0 + slot) + 16 * h,
+                  reinterpret_cast<const char *>(src.q0 + si) + 16 * h);
+            cpa16(reinterpret_cast<char *>(st_q1 + slot) + 16 * h,
+                  reinterpret_cast<const char *>(src.q1 + si) + 16 * h);
         }
-    }
-    while (cl < nunits) {
-        const int base = PF ? cl * kChunk : cl * kThreads;
-        const int nslot = PF ? kPPT : min(cw, nunits - cl);
-        const int end = min(base + nslot * kThreads, n);
-        __syncthreads();  // every thread has read s_claim
-        if (tid == 0) {
-            const int w = PF ? 1 : (cl + cw >= tail ? 1 : kPPT);
-            s_claim = atomicAdd(a.chunk_next, w);
-            s_want = w;
+        cpa8(st_id + slot, src.id + si);
+        cpa4(st_cell + slot, src.cell + si);
+        if (XYZ) {
+            if (sizeof(T) == 8)
+                cpa8(st_at + slot, src.at + si);
+            else
+                cpa4(st_at + slot, src.at + si);
         }
-        __syncthreads();
-        const int ck_next = s_claim, cw_next = s_want;
-        // request the chunk's particles, then read the next chunk's perm
-        // entries; a thread fills and reads only its own slots, so chunks
-        // need no barrier
-        if (PF) {
-#pragma unroll
-            for (int m = 0; m < kPPT; ++m) {
-                const int k = base + m * kThreads + tid;
-                if (k < end) {
-                    const int pidx = pn[m];
-                    const bool from_main = pidx < nmain;
-                    const PBuf<T> &src = from_main ? a.src_main : a.src_births;
-                    const int si = from_main ? pidx : pidx - nmain;
-                    const int slot = m * kThreads + tid;
-                    for (int h = 0; h < (int)(sizeof(V) / 16); ++h) {
-                        cpa16(reinterpret_cast<char *>(st_q0 + slot) + 16 * h,
-                              reinterpret_cast<const char *>(src.q0 + si) + 16 * h);
-                        cpa16(reinterpret_cast<char *>(st_q1 + slot) + 16 * h,
-                              reinterpret_cast<const char *>(src.q1 + si) + 16 * h);
-                    }
-                    cpa8(st_id + slot, src.id + si);
-                    cpa4(st_cell + slot, src.cell + si);
-                    if (XYZ) {
-                        if (sizeof(T) == 8)
-                            cpa8(st_at + slot, src.at + si);
-                        else
-                            cpa4(st_at + slot, src.at + si);
-                    }
+    };
+    // one particle of the pass: the state at sorted position k (read through
+    // the permutation, or staged at slot by fetch), gathered, pushed,
+    // collided, split, pushed again and deposited; every lane of the warp
+    // calls it together (valid false: a lane past the end)
+    auto process = [&](int k, bool valid, int slot) {
+        int out_cell = -1;
+        T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+        if (valid) {
+            PS<T> p;
+            uint64_t id;
+            if (PF) {
+                ld4(st_q0 + slot, p.oz, p.orr, p.vr, p.vt);
+                ld4(st_q1 + slot, p.vz, p.ar, p.az, p.w);
+                decode_cell(st_cell[slot], a.ncz, a.inv_ncz, p.i, p.j);
+                id = st_id[slot];
+                if (XYZ) p.at = st_at[slot];
+            } else {
+                const int pidx = a.perm[k];
+                const bool from_main = pidx < nmain;
+                const PBuf<T> &src = from_main ? a.src_main : a.src_births;
+                const int si = from_main ? pidx : pidx - nmain;
+                p = load_p_fast(src, si, a.ncz, a.inv_ncz);
+                id = src.id[si];
+                if (XYZ) p.at = src.at[si];
+            }
+            // a stored cell outside the mesh (never written by a pass)
+            // is reported and the record dropped, never followed
+            const bool in_mesh = (unsigned)p.i < (unsigned)a.ncz && (unsigned)p.j < (unsigned)a.ncr;
+            if (!in_mesh) p.i = p.j = 0;
+            // gather E at x~ with the deposit's shape factors (Sec. 2.4)
+            T s0, s1;
+            shape_r(a.weighting, p.j, p.orr, s0, s1);
+            const T z0 = (T)1 - p.oz, z1 = p.oz;
+            const auto *Ep = a.E + (size_t)p.i * a.nr + p.j;
+            const auto e00 = Ep[0], e01 = Ep[1], e10 = Ep[a.nr], e11 = Ep[a.nr + 1];
+            const T Ez = z0 * (s0 * e00.x + s1 * e01.x) + z1 * (s0 * e10.x + s1 * e11.x);
+            const T Er = z0 * (s0 * e00.y + s1 * e01.y) + z1 * (s0 * e10.y + s1 * e11.y);
+            // final push (Sec. 2.1 finalpush, Sec. 2.3 in r-z)
+            p.oz += a.kz * Ez;
+            carry(p.oz, p.i);
+            const T ro = p.orr + a.kr * Er;
+            const T fl = m_floor(ro);
+            int jn = p.j + (int)fl;
+            bool axis = false;
+            if (jn < 0) {  // through the axis: |r|, |v_r|, |a_r|
+                const T rr = -((T)p.j + ro);
+                const T f2 = m_floor(rr);
+                jn = (int)f2;
+                p.orr = rr - f2;
+                axis = true;
+            } else {
+                p.orr = ro - fl;
+            }
+            p.j = jn;
+            p.vz += a.kv * Ez;
+            p.vr += a.kv * Er;
+            p.az = (T)0.5 * (a.ka * Ez + p.az);
+            p.ar = (T)0.5 * (a.ka * Er + p.ar);
+            if (XYZ) p.at = (T)0.5 * p.at;  // no E_theta
+            if (axis) {
+                if (XYZ) {  // through the axis to the opposite azimuth
+                    p.vr = -p.vr;
+                    p.ar = -p.ar;
+                    p.vt = -p.vt;
+                    p.at = -p.at;
+                } else {  // |v_r|, |a_r| (Sec. 2.3)
+                    p.vr = m_abs(p.vr);
+                    p.ar = m_abs(p.ar);
                 }
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            const int nb = ck_next * kChunk;
-#pragma unroll
-            for (int m = 0; m < kPPT; ++m) {
-                const int k = nb + m * kThreads + tid;
-                pn[m] = k < n ? a.perm[k] : 0;
+            bool alive = true;
+            // one test for all: a NaN or infinity anywhere makes the sum
+            // non-finite (the values are far below overflow)
+            if (!in_mesh || !m_finite(p.oz + p.orr + p.vr + p.vt + p.vz + p.w)) {
+                atomicOr(&a.ds->status, ST_NAN);
+                alive = false;
             }
-        }
-        // each thread reads back only the slots it requested itself
-        if (PF) asm volatile("cp.async.wait_group 0;" ::: "memory");
-#pragma unroll 1
-        for (int m = 0; m < nslot; ++m) {
-            const int k = base + m * kThreads + tid;
-            int out_cell = -1;
-            T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
-            if (k < end) {
-                PS<T> p;
-                uint64_t id;
-                if (PF) {
-                    const int slot = m * kThreads + tid;
-                    ld4(st_q0 + slot, p.oz, p.orr, p.vr, p.vt);
-                    ld4(st_q1 + slot, p.vz, p.ar, p.az, p.w);
-                    decode_cell(st_cell[slot], a.ncz, a.inv_ncz, p.i, p.j);
-                    id = st_id[slot];
-                    if (XYZ) p.at = st_at[slot];
-                } else {
-                    const int pidx = a.perm[k];
-                    const bool from_main = pidx < nmain;
-                    const PBuf<T> &src = from_main ? a.src_main : a.src_births;
-                    const int si = from_main ? pidx : pidx - nmain;
-                    p = load_p_fast(src, si, a.ncz, a.inv_ncz);
-                    id = src.id[si];
-                    if (XYZ) p.at = src.at[si];
+            int wall = alive ? wall_of(p.i, p.oz, p.j, a.nz, a.nr) : -1;
+            if (wall >= 0) {
+                atomicAdd(&bt.cnt[PIC_C_ABS + a.s * 3 + wall], 1ull);
+                atomicAdd(&bt.q[wall], (double)p.w * a.qch[a.s]);
+                alive = false;
+            }
+            if (alive) {
+                collide(a, &bt, id, step, p);
+                if (a.eedf) {
+                    const T Ek = a.half_m_e * (p.vr * p.vr + p.vt * p.vt + p.vz * p.vz);
+                    const T x = Ek * a.eedf_scale;
+                    if (x >= (T)0 && x < (T)a.eedf_bins)
+                        atomicAdd(&s_eedf[(int)x * kEedfCopies + (lane & (kEedfCopies - 1))], p.w);
                 }
-                // a stored cell outside the mesh (never written by a pass)
-                // is reported and the record dropped, never followed
-                const bool in_mesh = (unsigned)p.i < (unsigned)a.ncz && (unsigned)p.j < (unsigned)a.ncr;
-                if (!in_mesh) p.i = p.j = 0;
-                // gather E at x~ with the deposit's shape factors (Sec. 2.4)
-                T s0, s1;
-                shape_r(a.weighting, p.j, p.orr, s0, s1);
-                const T z0 = (T)1 - p.oz, z1 = p.oz;
-                const auto *Ep = a.E + (size_t)p.i * a.nr + p.j;
-                const auto e00 = Ep[0], e01 = Ep[1], e10 = Ep[a.nr], e11 = Ep[a.nr + 1];
-                const T Ez = z0 * (s0 * e00.x + s1 * e01.x) + z1 * (s0 * e10.x + s1 * e11.x);
-                const T Er = z0 * (s0 * e00.y + s1 * e01.y) + z1 * (s0 * e10.y + s1 * e11.y);
-                // final push (Sec. 2.1 finalpush, Sec. 2.3 in r-z)
-                p.oz += a.kz * Ez;
-                carry(p.oz, p.i);
-                const T ro = p.orr + a.kr * Er;
-                const T fl = m_floor(ro);
-                int jn = p.j + (int)fl;
-                bool axis = false;
-                if (jn < 0) {  // through the axis: |r|, |v_r|, |a_r|
-                    const T rr = -((T)p.j + ro);
-                    const T f2 = m_floor(rr);
-                    jn = (int)f2;
-                    p.orr = rr - f2;
-                    axis = true;
-                } else {
-                    p.orr = ro - fl;
-                }
-                p.j = jn;
-                p.vz += a.kv * Ez;
-                p.vr += a.kv * Er;
-                p.az = (T)0.5 * (a.ka * Ez + p.az);
-                p.ar = (T)0.5 * (a.ka * Er + p.ar);
-                if (XYZ) p.at = (T)0.5 * p.at;  // no E_theta
-                if (axis) {
-                    if (XYZ) {  // through the axis to the opposite azimuth
-                        p.vr = -p.vr;
-                        p.ar = -p.ar;
-                        p.vt = -p.vt;
-                        p.at = -p.at;
-                    } else {  // |v_r|, |a_r| (Sec. 2.3)
-                        p.vr = m_abs(p.vr);
-                        p.ar = m_abs(p.ar);
+                if (do_split) {  // weight-conserving split (Sec. 2.2)
+                    const T wr_ = a.w_ref[p.j];
+                    if (p.w > wr_) {
+                        T Nf = m_floor(p.w / wr_);
+                        if (Nf > (T)kSplitNMax) Nf = (T)kSplitNMax;
+                        int Nc = (int)Nf;
+                        T rem = p.w - Nf * wr_;
+                        if (!(rem > (T)0)) {
+                            Nc -= 1;
+                            rem = p.w - (T)Nc * wr_;
+                        }
+                        if (Nc > 0) {
+                            atomicAdd(&bt.cnt[PIC_C_SPLITS + a.s], 1ull);
+                            PS<T> cp = p;
+                            cp.w = wr_;
+                            p.w = rem;
+                            for (int c = 0; c < Nc; ++c) emit_birth(a, &bt, a.s, a.s, id, 2 + c, cp);
+                        }
                     }
                 }
-                bool alive = true;
-                // one test for all: a NaN or infinity anywhere makes the sum
-                // non-finite (the values are far below overflow)
-                if (!in_mesh || !m_finite(p.oz + p.orr + p.vr + p.vt + p.vz + p.w)) {
-                    atomicOr(&a.ds->status, ST_NAN);
-                    alive = false;
-                }
-                int wall = alive ? wall_of(p.i, p.oz, p.j, a.nz, a.nr) : -1;
+                if (XYZ)
+                    first_push_xyz(a, p);
+                else
+                    first_push(a, p);
+                wall = wall_of(p.i, p.oz, p.j, a.nz, a.nr);
                 if (wall >= 0) {
                     atomicAdd(&bt.cnt[PIC_C_ABS + a.s * 3 + wall], 1ull);
                     atomicAdd(&bt.q[wall], (double)p.w * a.qch[a.s]);
                     alive = false;
                 }
-                if (alive) {
-                    collide(a, &bt, id, step, p);
-                    if (a.eedf) {
-                        const T Ek = a.half_m_e * (p.vr * p.vr + p.vt * p.vt + p.vz * p.vz);
-                        const T x = Ek * a.eedf_scale;
-                        if (x >= (T)0 && x < (T)a.eedf_bins)
-                            atomicAdd(&s_eedf[(int)x * kEedfCopies + (lane & (kEedfCopies - 1))], p.w);
-                    }
-                    if (do_split) {  // weight-conserving split (Sec. 2.2)
-                        const T wr_ = a.w_ref[p.j];
-                        if (p.w > wr_) {
-                            T Nf = m_floor(p.w / wr_);
-                            if (Nf > (T)kSplitNMax) Nf = (T)kSplitNMax;
-                            int Nc = (int)Nf;
-                            T rem = p.w - Nf * wr_;
-                            if (!(rem > (T)0)) {
-                                Nc -= 1;
-                                rem = p.w - (T)Nc * wr_;
-                            }
-                            if (Nc > 0) {
-                                atomicAdd(&bt.cnt[PIC_C_SPLITS + a.s], 1ull);
-                                PS<T> cp = p;
-                                cp.w = wr_;
-                                p.w = rem;
-                                for (int c = 0; c < Nc; ++c) emit_birth(a, &bt, a.s, a.s, id, 2 + c, cp);
-                            }
-                        }
-                    }
-                    if (XYZ)
-                        first_push_xyz(a, p);
-                    else
-                        first_push(a, p);
-                    wall = wall_of(p.i, p.oz, p.j, a.nz, a.nr);
-                    if (wall >= 0) {
-                        atomicAdd(&bt.cnt[PIC_C_ABS + a.s * 3 + wall], 1ull);
-                        atomicAdd(&bt.q[wall], (double)p.w * a.qch[a.s]);
-                        alive = false;
-                    }
-                }
-                if (alive) {
-                    out_cell = p.j * a.ncz + p.i;
-                    // deposit weights at the new x~ (Sec. 2.4)
-                    T r0, r1;
-                    shape_r(a.weighting, p.j, p.orr, r0, r1);
-                    const T y0 = (T)1 - p.oz, y1 = p.oz;
-                    c00 = p.w * y0 * r0;
-                    c01 = p.w * y0 * r1;
-                    c10 = p.w * y1 * r0;
-                    c11 = p.w * y1 * r1;
-                }
-                store_p(a.dst_main, k, p, out_cell, id);
-                if (XYZ) a.dst_main.at[k] = p.at;
             }
-            // runs of lanes with one output cell: sum each run into its first
-            // lane, which makes the four deposit reductions and the histogram count
-            const int cprev = __shfl_up_sync(0xffffffffu, out_cell, 1);
-            const bool head = lane == 0 || cprev != out_cell;
-            const unsigned heads = __ballot_sync(0xffffffffu, head);
-            const unsigned above = heads & ~((2u << lane) - 1u);
-            const int rend = above ? __ffs(above) - 1 : 32;
+            if (alive) {
+                out_cell = p.j * a.ncz + p.i;
+                // deposit weights at the new x~ (Sec. 2.4)
+                T r0, r1;
+                shape_r(a.weighting, p.j, p.orr, r0, r1);
+                const T y0 = (T)1 - p.oz, y1 = p.oz;
+                c00 = p.w * y0 * r0;
+                c01 = p.w * y0 * r1;
+                c10 = p.w * y1 * r0;
+                c11 = p.w * y1 * r1;
+            }
+            store_p(a.dst_main, k, p, out_cell, id);
+            if (XYZ) a.dst_main.at[k] = p.at;
+        }
+        // runs of lanes with one output cell: sum each run into its first
+        // lane, which makes the four deposit reductions and the histogram count
+        const int cprev = __shfl_up_sync(0xffffffffu, out_cell, 1);
+        const bool head = lane == 0 || cprev != out_cell;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const unsigned above = heads & ~((2u << lane) - 1u);
+        const int rend = above ? __ffs(above) - 1 : 32;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const T t00 = __shfl_down_sync(0xffffffffu, c00, d);
-                const T t01 = __shfl_down_sync(0xffffffffu, c01, d);
-                const T t10 = __shfl_down_sync(0xffffffffu, c10, d);
-                const T t11 = __shfl_down_sync(0xffffffffu, c11, d);
-                if (lane + d < rend) {
-                    c00 += t00;
-                    c01 += t01;
-                    c10 += t10;
-                    c11 += t11;
-                }
-            }
-            if (head && out_cell >= 0) {
-                atomicAdd(a.counts[a.s] + out_cell, rend - lane);
-                int ci, cj;
-                decode_cell(out_cell, a.ncz, a.inv_ncz, ci, cj);
-                double *g = a.N[a.s] + (size_t)ci * a.nr + cj;
-                atomicAdd(g, (double)c00);
-                atomicAdd(g + 1, (double)c01);
-                atomicAdd(g + a.nr, (double)c10);
-                atomicAdd(g + a.nr + 1, (double)c11);
+        for (int d = 1; d < 32; d <<= 1) {
+            const T t00 = __shfl_down_sync(0xffffffffu, c00, d);
+            const T t01 = __shfl_down_sync(0xffffffffu, c01, d);
+            const T t10 = __shfl_down_sync(0xffffffffu, c10, d);
+            const T t11 = __shfl_down_sync(0xffffffffu, c11, d);
+            if (lane + d < rend) {
+                c00 += t00;
+                c01 += t01;
+                c10 += t10;
+                c11 += t11;
             }
         }
-        cl = ck_next;
-        cw = cw_next;
+        if (head && out_cell >= 0) {
+            atomicAdd(a.counts[a.s] + out_cell, rend - lane);
+            int ci, cj;
+            decode_cell(out_cell, a.ncz, a.inv_ncz, ci, cj);
+            double *g = a.N[a.s] + (size_t)ci * a.nr + cj;
+            atomicAdd(g, (double)c00);
+            atomicAdd(g + 1, (double)c01);
+            atomicAdd(g + a.nr, (double)c10);
+            atomicAdd(g + a.nr + 1, (double)c11);
+        }
+    };
+    // Work is claimed from a counter in slots of 32 consecutive particles.
+    // The direct-load shapes, while the pass is far from its end, claim a
+    // block's kPPT x kThreads particles at a time (its warps load
+    // neighbouring particles together, whose sources lie together: faster
+    // at 1e7 particles and more).  Otherwise each warp claims on its own,
+    // up to kPPT slots, shrinking to one slot over the last 2 x (warps x
+    // kPPT) slots (guided self-scheduling): no warp waits for another of its
+    // block, and the pass ends within about one slot's time.  A unit's
+    // width follows the latest claim its claimer knows of (the counter only
+    // grows, so a width is never too small).  The next claim is made while
+    // the current unit is worked on; the prefetching shapes claim two ahead
+    // and read the next unit's perm entries early.
+    const int nslots = (n + 31) >> 5;
+    const int twice_warps = 2 * (int)gridDim.x * (kThreads / 32);
+    constexpr int kBlockSlots = kPPT * (kThreads / 32);
+    const int bulk_end = nslots - twice_warps * kPPT;  // block claims start before it
+    auto width = [&](int at) { return max(1, min(kPPT, (nslots - at) / twice_warps)); };
+    int pn[kPPT];  // this thread's perm entries of its next unit
+    // the next unit's perm entries: a block unit's slot m is kThreads
+    // particles on from its slot m-1, a warp unit's 32 (only its w slots)
+    auto perm_ahead = [&](int c, int w, bool blk_unit) {
+#pragma unroll
+        for (int m = 0; m < kPPT; ++m) {
+            const int k = c * 32 + (blk_unit ? m * kThreads + tid : m * 32 + lane);
+            pn[m] = (blk_unit || m < w) && k < n ? a.perm[k] : 0;
+        }
+    };
+    __shared__ int s_claim;
+    bool blk = !PF && bulk_end > 0;  // block claims (block-uniform)
+    int cl, cw, cn = 0, cnw = 0;
+    // a warp's first claims (two for the prefetching shapes)
+    auto warp_start = [&]() {
+        int x = 0, y = 0;
+        cw = cnw = width(max(bulk_end, 0));
+        if (lane == 0) {
+            x = atomicAdd(a.chunk_next, cw);
+            if (PF) y = atomicAdd(a.chunk_next, cnw);
+        }
+        cl = __shfl_sync(0xffffffffu, x, 0);
+        if (PF) cn = __shfl_sync(0xffffffffu, y, 0);
+    };
+    if (blk) {
+        if (tid == 0) s_claim = atomicAdd(a.chunk_next, kBlockSlots);
+        __syncthreads();
+        cl = s_claim;
+        cw = kBlockSlots;
+    } else {
+        warp_start();
+    }
+    if (PF) perm_ahead(cl, cw, blk);
+    for (;;) {
+        if (cl >= nslots) {
+            if (!blk) break;
+            blk = false;  // the block's last unit is done: the rest warp by warp
+            warp_start();
+            if (PF) perm_ahead(cl, cw, false);
+            continue;
+        }
+        const int stride = blk ? kThreads : 32, off = blk ? tid : lane;
+        const int base = cl * 32;
+        const int nslot = blk ? kPPT : min(cw, nslots - cl);
+        const int end = min(base + (blk ? kBlockSlots : nslot) * 32, n);
+        int claim = 0, w;
+        if (blk) {
+            const bool more = cl + kBlockSlots < bulk_end;  // block-uniform
+            __syncthreads();  // every thread has read s_claim
+            if (tid == 0 && more) s_claim = atomicAdd(a.chunk_next, kBlockSlots);
+            __syncthreads();
+            claim = more ? s_claim : nslots;
+            w = kBlockSlots;
+        } else {
+            w = width(PF ? cn + cnw : cl + cw);
+            if (lane == 0) claim = atomicAdd(a.chunk_next, w);
+        }
+        // request the unit's particles, then read the next unit's perm
+        // entries; a thread fills and reads only its own slots
+        if (PF) {
+#pragma unroll
+            for (int m = 0; m < kPPT; ++m) {
+                const int k = base + m * stride + off;
+                if (k < end) fetch(pn[m], m * kThreads + tid);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (blk)
+                perm_ahead(claim, w, true);
+            else
+                perm_ahead(cn, cnw, false);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+#pragma unroll 1
+        for (int m = 0; m < nslot; ++m) {
+            const int k = base + m * stride + off;
+            process(k, k < end, m * kThreads + tid);
+        }
+        if (blk) {
+            cl = claim;
+        } else if (PF) {
+            cl = cn;
+            cw = cnw;
+            cn = __shfl_sync(0xffffffffu, claim, 0);
+            cnw = w;
+        } else {
+            cl = __shfl_sync(0xffffffffu, claim, 0);
+            cw = w;
+        }
     }
     __syncthreads();
     for (int k = tid; k < PIC_NCOUNT; k += blockDim.x)
