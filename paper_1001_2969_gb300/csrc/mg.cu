@@ -424,11 +424,22 @@ __device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double
                                            const SolveLayout &lay, double tol, int max_cycles,
                                            const StepCtl *sctl, const int bid, const int nbk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const MGFast &m = *mp;
-    MGCtl *ctl = m.ctl;
     if (sctl && sctl->halt) return;  // an earlier failure of this step
-    const int n = nr - 1, nz0 = m.nz[0], ng = nz0 * nr, L = m.nlev - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+    // the level table in shared memory: every grid barrier's acquire drops
+    // L1, and a table read from L2 before each level's loads would put an L2
+    // round trip in front of every phase
+    __shared__ __align__(16) MGFast s_m;
+    {
+        static_assert(sizeof(MGFast) % 8 == 0, "the level table is copied in 8-byte words");
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(mp);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_m);
+        for (int k = tid; k < (int)(sizeof(MGFast) / 8); k += nt) dst[k] = src[k];
+        __syncthreads();
+    }
+    const MGFast &m = s_m;
+    MGCtl *ctl = m.ctl;
+    const int n = nr - 1, nz0 = m.nz[0], ng = nz0 * nr, L = m.nlev - 1;
     constexpr int NW = kLine * M;  // unknowns of a line with its padding
     const bool mixed = sizeof(Tv) == 4;
     Tv *delta = mixed ? (Tv *)m.u32[0] : (Tv *)m.u64[0];  // level-0 correction (zero on the boundary)
@@ -441,6 +452,7 @@ __device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double
     const bool in_group = bid < G;
     __shared__ unsigned long long s_r[32], s_b[32];
     __shared__ double s_dot[4][32];
+    __shared__ double s_sum[4];
     // the mixed path accelerates its refinement by flexible GCR(1) (the
     // Krylov vectors are allocated for it); the FP64 path runs the paper's
     // plain V(0,1) iteration
@@ -543,9 +555,18 @@ __device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double
                 double a[4] = {0.0, 0.0, 0.0, 0.0};  // r.w, w.w, w.wp, r.wp
                 for (int t = bid; t < ntile; t += nbk) {
                     const int j0 = t * tw;
-                    for (int e = tid; e < sw * nz0; e += nt) {
-                        const int c = e % sw - 1, i = e / sw, j = j0 + c;
-                        S[(size_t)(c + 1) * nz0 + i] = (j >= 0 && j < nr) ? (double)delta[(size_t)i * nr + j] : 0.0;
+                    for (int e0 = tid; e0 < sw * nz0; e0 += kU * nt) {
+                        Tv dv[kU];
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int e = e0 + u * nt, c = e % sw - 1, i = e / sw, j = j0 + c;
+                            dv[u] = (e < sw * nz0 && j >= 0 && j < nr) ? delta[(size_t)i * nr + j] : (Tv)0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < kU; ++u) {
+                            const int e = e0 + u * nt, c = e % sw - 1, i = e / sw;
+                            if (e < sw * nz0) S[(size_t)(c + 1) * nz0 + i] = (double)dv[u];
+                        }
                     }
                     __syncthreads();
                     // batches of kU nodes per thread, loads first
@@ -598,25 +619,29 @@ __device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double
                     leave(false);
                     return;
                 }
-                // every block sums the partial products in block order: the
-                // same step length everywhere
-                if (warp == 0) {
-                    double v[4] = {0.0, 0.0, 0.0, 0.0};
-                    for (int b = lane; b < nbk; b += 32)
-#pragma unroll
-                        for (int d = 0; d < 4; ++d) v[d] += m.kpart[(size_t)b * 4 + d];
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        for (int o = 16; o > 0; o >>= 1) v[d] += __shfl_xor_sync(0xffffffffu, v[d], o);
-                        if (lane == 0) s_dot[d][0] = v[d];
+                // every block sums the partial products in the same fixed
+                // order (the same step length everywhere), all its threads
+                // loading at once: thread t takes entries t, t + nt, ... of
+                // product t % 4 (nt is a multiple of 32)
+                {
+                    double v = 0.0;
+#pragma unroll 4
+                    for (int e = tid; e < 4 * nbk; e += nt) v += m.kpart[e];
+                    for (int o = 4; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane < 4) s_dot[lane][warp] = v;
+                    __syncthreads();
+                    if (tid < 4) {
+                        double t = 0.0;
+                        for (int q = 0; q < (nt >> 5); ++q) t += s_dot[tid][q];
+                        s_sum[tid] = t;
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
-                const double beta = kc > 0.0 ? s_dot[2][0] / kc : 0.0;
-                const double den = s_dot[1][0] - beta * s_dot[2][0];
-                const double alpha = den > 0.0 ? (s_dot[0][0] - beta * s_dot[3][0]) / den : 1.0;
+                const double beta = kc > 0.0 ? s_sum[2] / kc : 0.0;
+                const double den = s_sum[1] - beta * s_sum[2];
+                const double alpha = den > 0.0 ? (s_sum[0] - beta * s_sum[3]) / den : 1.0;
                 kc = den > 0.0 ? den : 0.0;
-                __syncthreads();  // s_dot is rewritten by the next cycle
+                __syncthreads();  // s_sum is rewritten by the next cycle
                 for (int t = bid; t < ntile; t += nbk) {
                     const int j0 = t * tw;
                     for (int e0 = tid; e0 < tw * (nz0 - 2); e0 += kU * nt) {
