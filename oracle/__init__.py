@@ -73,6 +73,7 @@ class OrcConfig(C.Structure):
         ("circuit_C", C.c_double),
         ("pusher", C.c_int32),
         ("ion_subcycle", C.c_int32),
+        ("mg_guess", C.c_int32),
     ]
 
 
@@ -202,6 +203,7 @@ class Oracle:
         c.circuit_C = float(cfg.get("circuit_C", 0.0))
         c.pusher = {"local": 0, "xyz": 1}[cfg.get("pusher", "local")]
         c.ion_subcycle = int(cfg.get("ion_subcycle", 1))
+        c.mg_guess = {"previous": 0, "linear": 1}[cfg.get("mg_guess", "linear")]
         if capacity is None:
             capacity = max(int(1.5 * max(sp["capacity"] for sp in cfg["species"])), 64)
         self.capacity = capacity

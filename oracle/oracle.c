@@ -56,6 +56,7 @@ struct orc_state {
     double qpass[ORC_Q_NCOUNT]; /* absorbed charge of the last particle pass */
     /* external circuit: superposition parts of phi and the circuit state */
     double *phiP, *phiL, *zero;
+    double *phi_prev; /* the potential of the step before phi's (mg_guess) */
     double circ_V, circ_Q, circ_Qc;
     /* births of the current pass */
     orc_birth *b;
@@ -412,6 +413,7 @@ orc_state *orc_create(const orc_config *cfg, int64_t capacity) {
     st->rho = xmalloc(ng * sizeof(double));
     st->chi = xmalloc(ng * sizeof(double));
     st->phi = xmalloc(ng * sizeof(double));
+    st->phi_prev = xmalloc(ng * sizeof(double)); /* zero, like phi */
     st->Ez = xmalloc(ng * sizeof(double));
     st->Er = xmalloc(ng * sizeof(double));
     st->phiP = xmalloc(ng * sizeof(double));
@@ -451,6 +453,7 @@ void orc_destroy(orc_state *st) {
     free(st->rho);
     free(st->chi);
     free(st->phi);
+    free(st->phi_prev);
     free(st->Ez);
     free(st->Er);
     free(st->phiP);
@@ -680,6 +683,9 @@ void orc_set_grid(orc_state *st, int which, const double *in) {
     default: return;
     }
     memcpy(dst, in, ng * sizeof(double));
+    /* a potential set from outside has no history: the next extrapolation
+     * starts from it unchanged */
+    if (which == 4) memcpy(st->phi_prev, in, ng * sizeof(double));
 }
 
 /* ------------------------------------------------------------------ */
@@ -1567,8 +1573,21 @@ void orc_step(orc_state *st, int nsteps, int *last_cycles, double *last_res) {
         double res = 0.0;
         if (st->c.circuit_C > 0.0)
             circuit_solve(st, orc_voltage(st, t), V, &cyc, &res);
-        else
+        else {
+            if (st->c.mg_guess == 1) {
+                /* w_0 of Algorithm 1: phi^n + (phi^n - phi^(n-1)) on the
+                 * interior nodes, the potential extrapolated linearly in
+                 * time (the boundary values are set by the solve) */
+                int nz = st->c.nz, nr = st->c.nr;
+                for (int i = 1; i < nz - 1; ++i)
+                    for (int j = 0; j < nr - 1; ++j) {
+                        double now = st->phi[IDX(i, j)];
+                        st->phi[IDX(i, j)] = 2.0 * now - st->phi_prev[IDX(i, j)];
+                        st->phi_prev[IDX(i, j)] = now;
+                    }
+            }
             orc_solve(st, orc_voltage(st, t), st->c.mg_tol, st->c.mg_max_cycles, &cyc, &res);
+        }
         if (last_cycles) *last_cycles = cyc;
         if (last_res) *last_res = res;
         orc_efield(st);

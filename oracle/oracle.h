@@ -94,6 +94,12 @@ typedef struct {
     /* ion subcycling (Sec. 2.7): ions move in every K-th pass only, with
      * dt_i = K dt; 0 or 1 moves them every pass */
     int32_t ion_subcycle;
+    /* starting value w_0 of a timestep's V-cycles (Algorithm 1 leaves it
+     * open): 0 the last step's potential, 1 the linear extrapolation
+     * 2 phi^n - phi^(n-1) from the last two steps on the interior nodes
+     * (plain solves only; the circuit's two solves start from their last
+     * solutions) */
+    int32_t mg_guess;
 } orc_config;
 
 typedef struct orc_state orc_state;

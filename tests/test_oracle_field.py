@@ -192,3 +192,58 @@ def test_efield_differences():
     assert np.all(Er[:, 0] == 0)  # symmetry axis
     dr = R / 10
     assert np.all(np.abs(Er[:, -1] - (-2 * b * R)) <= abs(b) * dr * 1.0001)  # first order
+
+
+def _laplace_run(guess, steps):
+    """c1 with no particles (no charge, no susceptibility): the potential is
+    V(t) times one fixed Laplace solution.  The source is a sine far below its
+    first quarter period (2 pi f t < 1e-7 over the run), so V(t_n) is linear in
+    n to about 1e-21 of its size."""
+    cfg = W.scaled(W.config("c1", precision="fp64", mg_guess=guess, mg_tol=1e-10), 0)
+    cfg["rf"] = dict(amp=[1e8], freq=[1.0], phase=[0.0])
+    o = Oracle(cfg)
+    cyc, phi = [], []
+    for _ in range(steps):
+        c, _ = o.step(1)
+        cyc.append(c)
+        phi.append(o.grid("phi"))
+    return cfg, o, cyc, phi
+
+
+def test_linear_start_is_the_next_solution_for_a_voltage_linear_in_time():
+    """Algorithm 1's starting value w_0 (Sec. 2.5) taken as 2 phi^n - phi^(n-1):
+    for phi(t) = V(t) phi_1 with V linear in t the extrapolated start is the next
+    step's solution up to the last two solves' residual errors, so from the third
+    step on at most one V-cycle is needed; started from phi^n (the previous
+    step's potential) every step needs several.  A sign or index slip in the
+    extrapolation (phi^(n-1) - 2 phi^n, or phi^n twice) fails the first claim;
+    both starts must reach the same potential within the solve tolerance."""
+    steps = 8
+    _, _, cyc_lin, phi_lin = _laplace_run("linear", steps)
+    _, _, cyc_prev, phi_prev = _laplace_run("previous", steps)
+    assert max(cyc_lin[2:]) <= 1, cyc_lin
+    assert min(cyc_prev[2:]) >= 4, cyc_prev
+    for a, b in zip(phi_lin, phi_prev):
+        assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
+    # the potential is V(t) phi_1: each step's is the first one scaled by n
+    for n, p in enumerate(phi_prev, start=1):
+        assert np.abs(p - n * phi_prev[0]).max() <= 1e-8 * np.abs(p).max()
+
+
+def test_linear_start_matches_previous_on_the_first_step_and_after_a_set_potential():
+    """With no history (a fresh state, or a potential set from outside) the
+    extrapolated start is phi^n itself: the first step is bit for bit the one
+    started from the previous potential, with the same cycle count."""
+    cfg = W.scaled(W.config("c1", precision="fp64"), 2000)
+    runs = {}
+    for guess in ("linear", "previous"):
+        o = Oracle(dict(cfg, mg_guess=guess))
+        o.load()
+        c1, _ = o.step(1)
+        p1 = o.grid("phi")
+        o.set_grid("phi", p1)  # no history after this
+        c2, _ = o.step(1)
+        runs[guess] = (c1, p1, c2, o.grid("phi"))
+    a, b = runs["linear"], runs["previous"]
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    assert a[2] == b[2] and np.array_equal(a[3], b[3])
