@@ -41,6 +41,9 @@ typedef enum pic_status {
 enum { PIC_FP64 = 0, PIC_MIXED = 1 };
 enum { PIC_WEIGHT_ZR2 = 0, PIC_WEIGHT_ZR = 1 };
 enum { PIC_CHI_MAX = 0, PIC_CHI_MEAN = 1 };
+/* starting value of each timestep's solve (pic_config.mg_guess) */
+enum { PIC_GUESS_PREVIOUS = 0, PIC_GUESS_LINEAR = 1 };
+
 /* pusher (Sec. 2.3): the local X-Y frame with a_theta dropped (the paper's
  * choice for its 2D runs), or the global X-Y-Z form, which carries a_theta */
 enum { PIC_PUSH_LOCAL = 0, PIC_PUSH_XYZ = 1 };
@@ -146,6 +149,13 @@ typedef struct pic_config {
      * 0 or 1: no subcycling.  split_every must be a multiple of K.  Not
      * with pic_batch_init or pic_window (PIC_ERR_ARG). */
     int32_t ion_subcycle;
+    /* starting value w_0 of each timestep's V-cycles (Algorithm 1 leaves it
+     * open): PIC_GUESS_PREVIOUS the last step's potential, PIC_GUESS_LINEAR
+     * 2 phi^n - phi^(n-1) on the interior nodes, extrapolated from the last
+     * two steps (the first step after init or pic_load without history
+     * starts from phi^n).  With the external circuit its two solves start
+     * from their previous solutions either way. */
+    int32_t mg_guess;
 } pic_config;
 
 typedef struct pic_handle pic_handle;

@@ -297,9 +297,13 @@ __device__ __forceinline__ void warp_line_solve(const Ts *__restrict__ F, Ts *Bs
     Bs[(M - 1) * kRow + p] = I;
 }
 
-// right-hand side rho A_j dz / eps0 and the Dirichlet data of phi
+// right-hand side rho A_j dz / eps0 and the Dirichlet data of phi; with
+// phi_prev (a warm solve) the interior starts from 2 phi - phi_prev, the
+// linear extrapolation in time of the last two steps' potentials, and
+// phi_prev takes the last step's
 __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, double *phi, const double *phi_zL,
-                         double V_arg, int nz, int nr, int cold, const StepCtl *ctl, int v_from_ctl) {
+                         double V_arg, int nz, int nr, int cold, const StepCtl *ctl, int v_from_ctl,
+                         double *phi_prev) {
     const MGFast &m = *mp;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nz * nr || (ctl && ctl->halt)) return;
@@ -320,8 +324,14 @@ __global__ void k_rhs_bc(const MGFast *__restrict__ mp, const double *rho, doubl
         p = phi_zL ? phi_zL[j] : 0.0;
     else if (j == nr - 1)
         p = 0.0;
-    else
-        p = cold ? 0.0 : phi[k];
+    else if (cold)
+        p = 0.0;
+    else if (phi_prev) {
+        const double t = phi[k];
+        p = 2.0 * t - phi_prev[k];
+        phi_prev[k] = t;
+    } else
+        p = phi[k];
     phi[k] = p;
     // the solve alternates between phi and a copy (both carry the boundary
     // values); the level-0 correction starts at zero (and stays zero on the
@@ -1224,7 +1234,8 @@ bool solve_job(const FieldDims &fd, MGFast &m, double *phi, bool mixed, double t
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
-                  bool v_from_ctl, bool setup, cudaEvent_t at_solve, bool wide, SolveJob *defer) {
+                  bool v_from_ctl, bool setup, cudaEvent_t at_solve, bool wide, SolveJob *defer,
+                  double *phi_prev) {
     const int nz = fd.nz, nr = fd.nr, n = nr - 1, ng = nz * nr;
     const int M = line_chunk(n);
     const int nlev = m.nlev;
@@ -1262,7 +1273,7 @@ int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const doubl
     }
     }
     k_rhs_bc<<<(ng + 255) / 256, 256, 0, st>>>(mp, rho, phi, phi_zL, V, nz, nr, warm ? 0 : 1, sctl,
-                                               v_from_ctl ? 1 : 0);
+                                               v_from_ctl ? 1 : 0, warm ? phi_prev : nullptr);
     ++L;
     // (k_rhs_bc also copies phi to its alternate, clears the level-0
     // correction and the solve's control block)

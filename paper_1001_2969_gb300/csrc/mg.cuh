@@ -110,11 +110,15 @@ void mg_fast_geometry(const MGFast &m, int nr, double dr, std::vector<double> &o
 // defer (narrow solves of a batch): the set-up is enqueued, the solve itself
 // is described in *defer and left to mg_multi_launch; its end (the report to
 // sctl) is then mg_solve_done's.
+// phi_prev (warm solves only, optional): the potential of the step before
+// phi's; the V-cycles then start from 2 phi - phi_prev on the interior, and
+// phi_prev takes phi's values (the starting value w_0 of Algorithm 1,
+// extrapolated linearly in time).
 int mg_fast_solve(const FieldDims &fd, MGFast &m, const double *rho, const double *chi, double V,
                   const double *phi_zL, double *phi, bool warm, bool mixed, double tol,
                   int max_cycles, double *rel_res, int *launches, StepCtl *sctl, cudaStream_t st,
                   bool v_from_ctl = true, bool setup = true, cudaEvent_t at_solve = nullptr,
-                  bool wide = true, SolveJob *defer = nullptr);
+                  bool wide = true, SolveJob *defer = nullptr, double *phi_prev = nullptr);
 
 // the launch shape of one reactor's solve (host only); false: not launchable
 bool solve_job(const FieldDims &fd, MGFast &m, double *phi, bool mixed, double tol, int max_cycles,

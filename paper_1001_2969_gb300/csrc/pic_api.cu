@@ -94,6 +94,7 @@ struct pic_handle {
     bool has_phiL = false;
     // external circuit: the two superposition parts of phi and an empty charge grid
     double *phi_P = nullptr, *phi_L = nullptr, *zero_grid = nullptr;
+    double *phi_prev = nullptr;  // the potential of the step before phi's (mg_guess)
     double *m_acc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     double *eedf = nullptr;
     double *tmp_grid[3] = {nullptr, nullptr, nullptr};
@@ -263,6 +264,8 @@ pic_status validate(const pic_config *c, std::string &why) {
     if (c->mg_max_cycles < 1) return bad("mg_max_cycles must be >= 1");
     if (c->pusher != PIC_PUSH_LOCAL && c->pusher != PIC_PUSH_XYZ) return bad("pusher must be PIC_PUSH_LOCAL or PIC_PUSH_XYZ");
     if (c->ion_subcycle < 0 || c->ion_subcycle > 1024) return bad("ion_subcycle must be in [0, 1024]");
+    if (c->mg_guess != PIC_GUESS_PREVIOUS && c->mg_guess != PIC_GUESS_LINEAR)
+        return bad("mg_guess must be PIC_GUESS_PREVIOUS or PIC_GUESS_LINEAR");
     if (c->ion_subcycle > 1 && c->split_every % c->ion_subcycle != 0)
         return bad("split_every must be a multiple of ion_subcycle");
     if (!(c->circuit_C >= 0.0) || !std::isfinite(c->circuit_C))
@@ -583,6 +586,7 @@ void setup_device(pic_handle *h) {
     h->rho = (double *)dalloc(h, gb);
     h->chi = (double *)dalloc(h, gb);
     h->phi = (double *)dalloc(h, gb);
+    h->phi_prev = (double *)dalloc(h, gb);
     h->Ez = (double *)dalloc(h, gb);
     h->Er = (double *)dalloc(h, gb);
     h->V = (double *)dalloc(h, gb);
@@ -601,6 +605,7 @@ void setup_device(pic_handle *h) {
     h->eedf = (double *)dalloc(h, (size_t)std::max(1, h->cfg.eedf_bins) * sizeof(double));
     for (int s = 0; s < 2; ++s) cudaMemsetAsync(h->N[s], 0, gb, h->st);
     cudaMemsetAsync(h->phi, 0, gb, h->st);
+    cudaMemsetAsync(h->phi_prev, 0, gb, h->st);  // = phi: the first step starts from phi
     cudaMemsetAsync(h->Ez, 0, gb, h->st);
     cudaMemsetAsync(h->Er, 0, gb, h->st);
     cudaMemsetAsync(h->rho, 0, gb, h->st);
@@ -903,7 +908,8 @@ void one_step(pic_handle *h, cudaStream_t sb, bool mv, int part = 0, SolveJob *j
         } else {
             mg_fast_solve(fd, h->mgf, h->rho, h->chi, 0.0, h->has_phiL ? h->phiL_d : nullptr, h->phi,
                           true, h->mixed, h->cfg.mg_tol, h->cfg.mg_max_cycles, nullptr, &L, h->sctl, st, true,
-                          true, fork, !h->in_batch, part == 1 ? job : nullptr);
+                          true, fork, !h->in_batch, part == 1 ? job : nullptr,
+                          h->cfg.mg_guess == PIC_GUESS_LINEAR ? h->phi_prev : nullptr);
             if (part == 1) {
                 h->launches += L;
                 return;
@@ -2108,7 +2114,7 @@ pic_status pic_merge(pic_handle *h, int32_t s, double frac, double dv, int64_t *
     return PIC_OK;
 }
 
-static const uint64_t kCkptMagic = 0x50494352475a3031ull;  // "PICRGZ01"
+static const uint64_t kCkptMagic = 0x50494352475a3032ull;  // "PICRGZ02"
 
 pic_status pic_save(pic_handle *h, const char *path) {
     if (!h || !path) return PIC_ERR_ARG;
@@ -2124,7 +2130,7 @@ pic_status pic_save(pic_handle *h, const char *path) {
     fwrite(hdr, sizeof(hdr), 1, f);
     fwrite(ids, sizeof(ids), 1, f);
     std::vector<double> g((size_t)h->ng);
-    for (double *src : {h->phi, h->N[0], h->N[1]}) {
+    for (double *src : {h->phi, h->phi_prev, h->N[0], h->N[1]}) {
         cudaMemcpy(g.data(), src, g.size() * 8, cudaMemcpyDeviceToHost);
         fwrite(g.data(), 8, g.size(), f);
     }
@@ -2187,9 +2193,9 @@ pic_status pic_load(pic_handle *h, const char *path) {
         fclose(f);
         return fail(h, PIC_ERR_ARG, "checkpoint does not match this handle");
     }
-    std::vector<double> g((size_t)h->ng), N0((size_t)h->ng), N1((size_t)h->ng);
-    bool ok = fread(g.data(), 8, g.size(), f) == g.size() && fread(N0.data(), 8, N0.size(), f) == N0.size() &&
-              fread(N1.data(), 8, N1.size(), f) == N1.size();
+    std::vector<double> g((size_t)h->ng), gp((size_t)h->ng), N0((size_t)h->ng), N1((size_t)h->ng);
+    bool ok = fread(g.data(), 8, g.size(), f) == g.size() && fread(gp.data(), 8, gp.size(), f) == gp.size() &&
+              fread(N0.data(), 8, N0.size(), f) == N0.size() && fread(N1.data(), 8, N1.size(), f) == N1.size();
     pic_status st = ok ? PIC_OK : fail(h, PIC_ERR_ARG, "truncated checkpoint");
     for (int s = 0; s < 2 && st == PIC_OK; ++s) {
         int64_t n = 0;
@@ -2246,6 +2252,7 @@ pic_status pic_load(pic_handle *h, const char *path) {
     h->sp[1].next_id = ids[1];
     push_ctl(h);
     cudaMemcpy(h->phi, g.data(), g.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(h->phi_prev, gp.data(), gp.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(h->N[0], N0.data(), N0.size() * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(h->N[1], N1.data(), N1.size() * 8, cudaMemcpyHostToDevice);
     return cuda_check(h, "load");

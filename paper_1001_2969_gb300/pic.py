@@ -66,7 +66,7 @@ class pic_config(C.Structure):
                 ("eedf_bins", C.c_int32), ("eedf_emax_eV", C.c_double), ("load", C.c_int32),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p), ("circuit_C", C.c_double), ("pusher", C.c_int32),
-                ("ion_subcycle", C.c_int32)]
+                ("ion_subcycle", C.c_int32), ("mg_guess", C.c_int32)]
 
 
 class pic_particles_view(C.Structure):
@@ -257,6 +257,7 @@ def pic_init(cfg: dict, load: bool = True, stream=None, torch_memory: bool = Tru
     c.circuit_C = float(cfg.get("circuit_C", 0.0))
     c.pusher = {"local": 0, "xyz": 1}[cfg.get("pusher", "local")]
     c.ion_subcycle = int(cfg.get("ion_subcycle", 1))
+    c.mg_guess = {"previous": 0, "linear": 1}[cfg.get("mg_guess", "linear")]
     ptr = C.c_void_p()
     st = L.pic_init(C.byref(c), C.byref(ptr))
     if st != PIC_OK:

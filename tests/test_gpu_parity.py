@@ -280,12 +280,18 @@ def test_tiny_and_empty_inputs(pic, prec):
     assert list(pic.pic_get_counts(h)["n_alive"]) == [0, 0]
 
 
-def test_multi_step_parity_fp64(pic):
-    cfg = W.scaled(W.config("c1", precision="fp64"), 20_000)
+@pytest.mark.parametrize("guess", ["linear", "previous"])
+def test_multi_step_parity_fp64(pic, guess):
+    """Five steps: the FP64 path runs the oracle's V-cycle iterates, from the
+    same starting value (the last potential, or its linear extrapolation from
+    the last two steps), so the cycle counts agree step by step."""
+    cfg = W.scaled(W.config("c1", precision="fp64", mg_guess=guess), 20_000)
     h, o = make_pair(pic, cfg)
     K = 5
-    pic.pic_step(h, K)
-    o.step(K)
+    ocyc = 0
+    for _ in range(K):
+        pic.pic_step(h, 1)
+        ocyc += o.step(1)[0]
     f = pic.pic_get_fields(h)
     for name in ("phi", "Ez", "Er"):
         assert nerr(f[name], o.grid(name)) < 1e-11, name
@@ -298,6 +304,7 @@ def test_multi_step_parity_fp64(pic):
     m = pic.pic_moments(h)
     oc, _ = o.counters()
     _counters_match(m["counters"], oc, "fp64")
+    assert int(m["counters"][pic.PIC_C_MGCYC]) == ocyc
     om = o.moments()
     for k in ("ne", "ni", "phi", "Ez", "Er"):
         assert nerr(m[k], om[k]) < 1e-10, k
