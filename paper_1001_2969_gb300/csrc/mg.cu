@@ -463,6 +463,7 @@ __device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double
     __shared__ unsigned long long s_r[32], s_b[32];
     __shared__ double s_dot[4][32];
     __shared__ double s_sum[4];
+    __shared__ double s_ab[3];  // the GCR step's beta, alpha and |q|^2
     // the mixed path accelerates its refinement by flexible GCR(1) (the
     // Krylov vectors are allocated for it); the FP64 path runs the paper's
     // plain V(0,1) iteration
@@ -614,10 +615,20 @@ __device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double
                     }
                     __syncthreads();  // S is reused by the next tile
                 }
-#pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    for (int o = 16; o > 0; o >>= 1) a[d] += __shfl_xor_sync(0xffffffffu, a[d], o);
-                    if (lane == 0) s_dot[d][warp] = a[d];
+                // the warp's four sums with few FP64 additions (the pipe is
+                // narrow): halves of the warp trade the products they do not
+                // keep (16 apart: 0, 1 stay low, 2, 3 high; 8 apart: one
+                // product per quarter), then each quarter sums its own;
+                // product 2 (lane >> 4) + ((lane >> 3) & 1) ends in the
+                // quarter's lanes
+                {
+                    const bool hi = lane >= 16, q1 = (lane & 8) != 0;
+                    const double s0 = __shfl_xor_sync(0xffffffffu, hi ? a[0] : a[2], 16);
+                    const double s1 = __shfl_xor_sync(0xffffffffu, hi ? a[1] : a[3], 16);
+                    const double b0 = (hi ? a[2] : a[0]) + s0, b1 = (hi ? a[3] : a[1]) + s1;
+                    double c = (q1 ? b1 : b0) + __shfl_xor_sync(0xffffffffu, q1 ? b0 : b1, 8);
+                    for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                    if ((lane & 7) == 0) s_dot[2 * (lane >> 4) + ((lane >> 3) & 1)][warp] = c;
                 }
                 __syncthreads();
                 if (tid < 4) {
@@ -646,12 +657,20 @@ __device__ __forceinline__ void solve_body(const MGFast *__restrict__ mp, double
                         s_sum[tid] = t;
                     }
                     __syncthreads();
+                    // the step's scalars by one thread: GB300's FP64 pipe is
+                    // narrow, and every thread dividing cost microseconds
+                    if (tid == 0) {
+                        const double beta = kc > 0.0 ? s_sum[2] / kc : 0.0;
+                        const double den = s_sum[1] - beta * s_sum[2];
+                        s_ab[0] = beta;
+                        s_ab[1] = den > 0.0 ? (s_sum[0] - beta * s_sum[3]) / den : 1.0;
+                        s_ab[2] = den > 0.0 ? den : 0.0;
+                    }
+                    __syncthreads();
                 }
-                const double beta = kc > 0.0 ? s_sum[2] / kc : 0.0;
-                const double den = s_sum[1] - beta * s_sum[2];
-                const double alpha = den > 0.0 ? (s_sum[0] - beta * s_sum[3]) / den : 1.0;
-                kc = den > 0.0 ? den : 0.0;
-                __syncthreads();  // s_sum is rewritten by the next cycle
+                const double beta = s_ab[0], alpha = s_ab[1];
+                kc = s_ab[2];
+                __syncthreads();  // s_sum and s_ab are rewritten by the next cycle
                 for (int t = bid; t < ntile; t += nbk) {
                     const int j0 = t * tw;
                     for (int e0 = tid; e0 < tw * (nz0 - 2); e0 += kU * nt) {
