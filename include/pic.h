@@ -152,9 +152,9 @@ typedef struct pic_config {
     /* starting value w_0 of each timestep's V-cycles (Algorithm 1 leaves it
      * open): PIC_GUESS_PREVIOUS the last step's potential, PIC_GUESS_LINEAR
      * 2 phi^n - phi^(n-1) on the interior nodes, extrapolated from the last
-     * two steps (the first step after init or pic_load without history
-     * starts from phi^n).  With the external circuit its two solves start
-     * from their previous solutions either way. */
+     * two steps.  phi^(n-1) starts equal to phi (zero) at init, so the first
+     * step starts from phi^n; checkpoints carry it.  With the external circuit
+     * its two solves start from their previous solutions either way. */
     int32_t mg_guess;
 } pic_config;
 
@@ -385,8 +385,12 @@ pic_status pic_set_id_stride(pic_handle *h, const uint64_t *next_id, uint64_t st
 /* pic_get_counts -- particles alive per species, steps taken, next ids. */
 pic_status pic_get_counts(pic_handle *h, int64_t *n_alive, int64_t *step, uint64_t *next_id);
 
-/* pic_save / pic_load -- checkpoint: particles, phi, step, ids, counters.
- * Resuming is bit-exact because every draw is keyed by (id, step). */
+/* pic_save / pic_load -- checkpoint: particles, phi and the step before's
+ * phi (the solve's extrapolated start), the deposit, step, ids, and the
+ * circuit state when there is one.  Resuming is bit-exact because every
+ * draw is keyed by (id, step).  pic_load rejects (PIC_ERR_ARG) a file of
+ * another mesh, pusher, subcycling or circuit setting, and one written in
+ * an earlier format. */
 /*
  * pic_get_circuit -- state of the external circuit after the last step:
  * out[0] electrode voltage V (V), out[1] electrode charge Q (C), out[2]
